@@ -1,0 +1,24 @@
+"""Shared pytest setup: the ``gpu`` marker and repo-root imports.
+
+Tests marked ``gpu`` need a CUDA device and the compiled CUDA library; the
+rest run on any CPU (``-m "not gpu"``).
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled sm_103a library")
+
+
+@pytest.fixture(scope="session")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle

@@ -1,0 +1,192 @@
+"""Pins of the oracle's preprocess, binning and forward rendering.
+
+Closed forms (Eq. 1-2 for one and two splats, the EWA covariance of an
+isotropic / axis-aligned / off-axis Gaussian), invariants of Eq. 1 (zero
+opacity gives the background, weights plus final transmittance sum to one,
+alpha never exceeds 0.99, T never drops below 1e-4) and a brute-force
+per-tile enumeration of the binning.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_01199_gb300 import scenegen
+
+Y00 = 0.5 / np.sqrt(np.pi)  # textbook real SH of degree 0
+
+
+def _one(mean, log_scale, quat=(1, 0, 0, 0), logit=0.0, rgb=(0.8, 0.5, 0.2)):
+    sh = np.array([[(np.array(rgb) - 0.5) / Y00]])
+    return {"mean": np.array([mean], np.float64), "log_scale": np.array([log_scale], np.float64),
+            "quat": np.array([quat], np.float64), "logit": np.array([logit], np.float64),
+            "sh": sh, "sh_degree": 0}
+
+
+def _cat(*scenes):
+    out = {k: np.concatenate([s[k] for s in scenes]) for k in ("mean", "log_scale", "quat", "logit", "sh")}
+    out["sh_degree"] = 0
+    return out
+
+
+def _sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def test_single_isotropic_gaussian_closed_form(orc):
+    W = H = 64
+    f = 64.0
+    cam = scenegen.pinhole_camera(W, H, f, bg=(0.1, 0.2, 0.3))
+    z, s = 3.0, 0.05
+    q = np.random.default_rng(0).standard_normal(4)
+    sc = _one([0.0, 0.0, z], [np.log(s)] * 3, quat=q, logit=0.7)
+    r = orc.render_scene(sc, cam, (16, 16))
+    sp = r["splats"]
+    sig2 = (f * s / z) ** 2 + 0.3  # EWA: J = f/z I on the axis, plus the 0.3 low-pass
+    np.testing.assert_allclose(sp["conic"][0], [1 / sig2, 0.0, 1 / sig2], rtol=1e-13, atol=1e-15)
+    assert sp["radius"][0] == int(np.ceil(3 * np.sqrt(sig2)))
+    np.testing.assert_allclose(sp["uv"][0], [W / 2, H / 2])
+    np.testing.assert_allclose(sp["depth"][0], z)
+    # Eq. 1 with one splat: I = c a + (1 - a) bg, a = min(0.99, o G)
+    o = _sigmoid(0.7)
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    G = np.exp(-((px - W / 2) ** 2 + (py - H / 2) ** 2) / (2 * sig2))
+    a = np.minimum(0.99, o * G)
+    rad = sp["radius"][0]
+    x0, x1 = int(np.floor((W / 2 - rad) / 16)), int(np.floor((W / 2 + rad) / 16)) + 1
+    inrect = (px // 16 >= x0) & (px // 16 < x1) & (py // 16 >= x0) & (py // 16 < x1)
+    keep = (a >= 1 / 255) & inrect
+    a = np.where(keep, a, 0.0)
+    rgb = np.array([0.8, 0.5, 0.2])
+    bg = np.array([0.1, 0.2, 0.3])
+    expect = rgb[:, None, None] * a + (1 - a) * bg[:, None, None]
+    np.testing.assert_allclose(r["image"], expect, atol=1e-14)
+    np.testing.assert_allclose(r["T"], 1 - a, atol=1e-14)
+    np.testing.assert_array_equal(r["last"], keep.astype(np.int32))
+
+
+def test_axis_aligned_and_off_axis_covariance(orc):
+    W, H, f = 128, 96, 100.0
+    cam = scenegen.pinhole_camera(W, H, f)
+    sx, sy, sz = 0.02, 0.05, 0.3
+    # on the axis, identity rotation: diag((f sx/z)^2, (f sy/z)^2) + 0.3
+    z = 4.0
+    sp = orc.preprocess(_one([0, 0, z], np.log([sx, sy, sz])), cam)
+    a, c = (f * sx / z) ** 2 + 0.3, (f * sy / z) ** 2 + 0.3
+    np.testing.assert_allclose(sp["conic"][0], [1 / a, 0, 1 / c], rtol=1e-13, atol=1e-16)
+    # off axis at (x, 0, z): row 0 of J is (f/z, 0, -f x / z^2), so the
+    # depth extent leaks into the screen x variance
+    x = 0.5
+    sp = orc.preprocess(_one([x, 0, z], np.log([sx, sy, sz])), cam)
+    a = (f / z) ** 2 * sx ** 2 + (f * x / z ** 2) ** 2 * sz ** 2 + 0.3
+    c = (f / z) ** 2 * sy ** 2 + 0.3
+    np.testing.assert_allclose(sp["conic"][0], [1 / a, 0, 1 / c], rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(sp["uv"][0], [f * x / z + W / 2, H / 2], rtol=1e-14)
+    # a 90-degree rotation about z swaps the screen axes
+    q = [np.cos(np.pi / 4), 0, 0, np.sin(np.pi / 4)]
+    sp = orc.preprocess(_one([0, 0, z], np.log([sx, sy, sz]), quat=q), cam)
+    a, c = (f * sy / z) ** 2 + 0.3, (f * sx / z) ** 2 + 0.3
+    np.testing.assert_allclose(sp["conic"][0], [1 / a, 0, 1 / c], rtol=1e-12, atol=1e-12)
+
+
+def test_near_plane_and_offscreen_cull(orc):
+    cam = scenegen.pinhole_camera(64, 64, 64.0)
+    sc = _cat(_one([0, 0, 0.1], [-3] * 3), _one([0, 0, -2], [-3] * 3), _one([50, 0, 3], [-3] * 3),
+              _one([0, 0, 3], [-3] * 3))
+    sp = orc.preprocess(sc, cam)
+    np.testing.assert_array_equal(sp["radius"] > 0, [False, False, False, True])
+
+
+def test_two_splats_over_operator_and_order_invariance(orc):
+    W = H = 32
+    cam = scenegen.pinhole_camera(W, H, 32.0, bg=(0.0, 0.0, 0.0))
+    front = _one([0, 0, 2.0], [np.log(0.1)] * 3, logit=0.3, rgb=(1.0, 0.0, 0.0))
+    back = _one([0, 0, 3.0], [np.log(0.15)] * 3, logit=-0.2, rgb=(0.0, 0.0, 1.0))
+    r1 = orc.render_scene(_cat(front, back), cam)
+    r2 = orc.render_scene(_cat(back, front), cam)
+    np.testing.assert_array_equal(r1["image"], r2["image"])
+    sp = r1["splats"]
+    px = py = W / 2 + 0.5  # pixel (16, 16)
+    al = []
+    for j in range(2):
+        dx, dy = sp["uv"][j, 0] - px, sp["uv"][j, 1] - py
+        A, B, C = sp["conic"][j]
+        al.append(min(0.99, sp["opacity"][j] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)))
+    expect = np.array([1, 0, 0]) * al[0] + np.array([0, 0, 1]) * al[1] * (1 - al[0])
+    np.testing.assert_allclose(r1["image"][:, 16, 16], expect, atol=1e-15)
+    np.testing.assert_allclose(r1["T"][16, 16], (1 - al[0]) * (1 - al[1]), atol=1e-15)
+
+
+def test_zero_opacity_gives_background(orc):
+    d = scenegen.uniform_box_scene(512, 1, 5, 64, 64, focal=64.0)
+    sc, cam = d["scene"], dict(d["camera"], bg=np.array([0.1, 0.2, 0.3], np.float32))
+    sc = dict(sc, logit=np.full_like(sc["logit"], -30.0))
+    r = orc.render_scene(sc, cam)
+    bg = np.array([0.1, 0.2, 0.3], np.float32).astype(np.float64)
+    np.testing.assert_array_equal(r["image"], np.broadcast_to(bg[:, None, None], r["image"].shape))
+    assert (r["last"] == 0).all()
+
+
+def test_weights_sum_with_final_transmittance(orc):
+    d = scenegen.uniform_box_scene(2048, 0, 6, 64, 64, focal=64.0)
+    sc = dict(d["scene"])
+    sc["sh"] = np.full_like(sc["sh"], 0.5 / Y00)  # every colour = 1
+    sc["log_scale"] = sc["log_scale"] + 1.0
+    r = orc.render_scene(sc, d["camera"])
+    # bg = 0 and c = 1:  I = sum_k a_k T_k = 1 - T_final
+    np.testing.assert_allclose(r["image"][0] + r["T"], 1.0, atol=1e-13)
+    assert r["T"].min() >= 1e-4
+    assert (r["last"] > 0).mean() > 0.5
+
+
+def test_opaque_splat_is_clamped(orc):
+    cam = scenegen.pinhole_camera(32, 32, 32.0, bg=(0.5, 0.5, 0.5))
+    # sigma^2 = (32 * 0.5 / 2)^2 + 0.3; the pixel centre 0.5 px off the mean on
+    # both axes has G = exp(-0.5 / (2 sigma^2)) > 0.996, so o G > 0.99 clamps
+    sc = _one([0, 0, 2.0], [np.log(0.5)] * 3, logit=40.0, rgb=(0.9, 0.1, 0.3))
+    r = orc.render_scene(sc, cam)
+    expect = 0.99 * np.array([0.9, 0.1, 0.3]) + 0.01 * 0.5
+    np.testing.assert_allclose(r["image"][:, 16, 16], expect, rtol=1e-6)
+    assert r["image"].max() <= 0.99 * 0.9 + 0.01 * 0.5 + 1e-15
+
+
+def test_stop_rule_excludes_the_crossing_splat(orc):
+    # 3 identical opaque splats stacked: after two, T = 1e-4 exactly would be
+    # crossed by the third, which must then not be composited.
+    cam = scenegen.pinhole_camera(16, 16, 16.0)
+    # scale 1 at z ~ 2 with f = 16: sigma^2 ~ 64, so o G > 0.99 at pixel (8, 8)
+    sc = _cat(*[_one([0, 0, 2.0 + 0.1 * k], [0.0] * 3, logit=40.0, rgb=(1, 1, 1)) for k in range(3)])
+    r = orc.render_scene(sc, cam, (16, 16))
+    # centre pixel: a = 0.99, T after two = 1e-4 (not < 1e-4): composited;
+    # the third would give 1e-6 < 1e-4: stop without it.
+    c = r["image"][0, 8, 8]
+    assert r["last"][8, 8] == 2
+    np.testing.assert_allclose(c, 0.99 + 0.99 * 0.01, rtol=1e-6)
+    assert r["T"][8, 8] >= 1e-4
+
+
+def _rect_f32(u, v, r, tw, th, gx, gy):
+    u, v, r = np.float32(u), np.float32(v), np.float32(r)
+    x0 = np.floor((u - r) / np.float32(tw)); x1 = np.floor((u + r) / np.float32(tw)) + np.float32(1)
+    y0 = np.floor((v - r) / np.float32(th)); y1 = np.floor((v + r) / np.float32(th)) + np.float32(1)
+    cl = lambda a, g: int(min(max(a, 0), g))
+    return cl(x0, gx), cl(y0, gy), cl(x1, gx), cl(y1, gy)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_binning_matches_brute_force(orc, tile):
+    W, H = 100, 70
+    s = scenegen.random_splats(400, 3, W, H, max_radius=25)
+    s["radius"][::17] = 0  # culled splats
+    vals, ranges, P = orc.bin_splats(s["u"], s["v"], s["radius"], s["depth"], W, H, tile)
+    gx, gy = (W + tile[0] - 1) // tile[0], (H + tile[1] - 1) // tile[1]
+    rects = [_rect_f32(s["u"][i], s["v"][i], s["radius"][i], tile[0], tile[1], gx, gy)
+             for i in range(400)]
+    total = 0
+    for t in range(gx * gy):
+        tx, ty = t % gx, t // gx
+        members = [i for i in range(400) if s["radius"][i] > 0 and rects[i][0] <= tx < rects[i][2]
+                   and rects[i][1] <= ty < rects[i][3]]
+        members.sort(key=lambda i: (float(s["depth"][i]), i))  # depth, then index (stable)
+        a, b = ranges[t]
+        assert list(vals[a:b]) == members
+        total += len(members)
+    assert total == P
