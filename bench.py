@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the LiteGS training-step hot path on GB300.
+
+Workload (default): 3,000,000 Gaussians of SH degree 3 from the uniform-box
+generator (means in [-1,1]^3 four units in front of the camera, log-scales
+N(-3.5, 0.5), opacity logits N(0, 1), seed 2), one 1297 x 840 pinhole camera
+(fx = fy = 1297), 16 x 16 tiles, L1 loss against a uniform random target.
+One step = the whole hot path a1..a10: Morton re-sort of parameters and Adam
+moments, cluster cull + compaction, preprocess, binning + sort, forward
+rasterisation, L1 loss gradient, backward rasterisation with the
+opacity-gradient moments, variance metric, fused preprocess backward + Adam.
+
+Metric: training iterations per second (whole job; N GPUs run N independent
+replicas, weak scaling). Inputs stay resident (the 2.1 GB parameter + moment
+state and the target exceed the 129 MB L2, so no flush is needed).
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload instead (see cpu_step_sample()).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd iters/s @3M Gaussians 1.1MP (plain vs mixed); served render p50/p99 ms"
+UNIT = "iters/s"
+N_GAUSS = 3_000_000
+SH_DEG = 3
+SEED = 2
+W_IMG, H_IMG = 1297, 840
+TILE = (16, 16)
+WORKLOAD = ("3M Gaussians SH3 uniform-box scene (seed 2), 1297x840 camera fx=fy=1297, 16x16 tiles, "
+            "full training step a1-a10 (Morton re-sort + cull/compact + preprocess + bin sort + "
+            "raster fwd + L1 + raster bwd + variance + fused preprocess-bwd/Adam)")
+
+
+def make_workload(seed_offset: int = 0, n: int | None = None):
+    from paper_2503_01199_gb300 import scenegen
+    return scenegen.uniform_box_scene(n or N_GAUSS, SH_DEG, SEED + seed_offset, W_IMG, H_IMG,
+                                      focal=float(W_IMG))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        rows = [r.split(", ") for r in self.lines if r.count(",") >= 9]
+        if self.bus_id:
+            mine = [r for r in rows if self.bus_id.endswith(r[1].lower()[-12:]) or
+                    r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[6 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def traffic_record() -> dict:
+    """ncu DRAM bytes per launch of kernels, from profiles/traffic.json, with
+    the library build they were captured on (stale entries read as null)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2503_01199_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+STAGES = ["a1_morton", "a2_cull", "a3_preprocess", "a4_bin_sort", "a5_raster_fwd", "a6_loss",
+          "a7_raster_bwd", "a8_variance", "a9a10_bwd_adam"]
+
+
+def run_gpu(args) -> dict | None:
+    import torch
+    import torch.distributed as dist
+    from paper_2503_01199_gb300 import binding as B
+    from paper_2503_01199_gb300 import pipeline as PL
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.load()
+    d = make_workload(rank, args.n_gaussians)
+    sc, cam, tgt_np = d["scene"], d["camera"], d["target"]
+    tr = PL.Trainer(sc, W_IMG, H_IMG, PL.StepConfig(tile=TILE, pair_capacity=192_000_000),
+                    device=str(dev))
+    del sc
+    cs = B.camera_struct(cam)
+    target = torch.from_numpy(tgt_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(events=None):
+        def mark(i):
+            if events is not None:
+                events[i].record(stream)
+        mark(0)
+        tr.morton_reorder()
+        mark(1)
+        g = tr.gaussians()
+        B.lgs_cluster_cull_compact(g, cs, tr.cfg.cluster, None, tr.cluster_visible, tr.rowmap,
+                                   tr.d_V, tr.ws_ccc)
+        mark(2)
+        B.lgs_preprocess(g, tr.rowmap, tr.d_V, cs, TILE[0], TILE[1], tr.splats)
+        mark(3)
+        B.lgs_bin_sort(tr.splats, tr.d_V, tr.n, cs, TILE[0], TILE[1], tr.vals, tr.d_P, tr.ranges,
+                       tr.ws_bin)
+        mark(4)
+        B.lgs_raster_fwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.image,
+                         tr.finalT, tr.last)
+        mark(5)
+        B.lgs_loss_l1(tr.image, target, tr.dLdI, tr.loss)
+        mark(6)
+        B.lgs_raster_bwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.finalT, tr.last,
+                         tr.dLdI, tr.gacc)
+        mark(7)
+        B.lgs_opacity_variance(tr.gacc, tr.rowmap, tr.d_V, tr.n, tr.metric)
+        mark(8)
+        tr.step_count += 1
+        B.lgs_preprocess_bwd_adam(tr.gaussians(), tr.m, tr.v, tr.rowmap, tr.d_V, cs, tr.gacc,
+                                  tr.lr, tr.cfg.beta1, tr.cfg.beta2, tr.cfg.eps, tr.step_count)
+        mark(9)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    overflow = B.lgs_get_overflow()
+    if overflow:
+        raise RuntimeError(f"pair capacity too small: {overflow} pairs needed")
+    V = int(tr.d_V.item())
+    P = int(tr.d_P.item())
+    # ---- timed region: device throughput with per-stage events
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except AttributeError:
+        pass
+    clocks = ClockSampler(bus)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.lgs_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = B.lgs_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
+                for i, s in enumerate(STAGES)}
+    # ---- end to end: target from pinned host memory, step, loss back to host
+    pinned = torch.from_numpy(tgt_np).pin_memory()
+    loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        target.copy_(pinned, non_blocking=True)
+        step()
+        loss_host.copy_(tr.loss, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    loss_val = float(loss_host.item())
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    e2e_value = world * args.steps / (e2e_ms / 1e3)
+    # ---- roofline of the dominant kernel
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    npl = B.num_planes(SH_DEG)
+    kernel_bytes = {
+        "a9a10_bwd_adam": V * (6 * npl * 4 + 48 + 4),   # p, m, v read + write; grad row; map
+        "a3_preprocess": V * (npl * 4 + 4 + 48 + 4 + 4),  # params + map in; record, depth, radius out
+    }
+    single = {s: stage_ms[s] for s in ("a3_preprocess", "a5_raster_fwd", "a7_raster_bwd",
+                                        "a9a10_bwd_adam")}
+    dom = max(kernel_bytes, key=lambda s: stage_ms[s])
+    achieved = kernel_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    tr_rec = traffic_record().get(dom, {})
+    traffic = tr_rec.get("bytes_per_launch") if tr_rec.get("source") == source_digest() else None
+    roofline = {"kernel": {"a9a10_bwd_adam": "k_preprocess_bwd_adam",
+                           "a3_preprocess": "k_preprocess"}[dom],
+                "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "peak_source": "measured" if hbm else "fallback",
+                "frac": round(achieved / (hbm if hbm else 6800.0), 4),
+                "traffic": traffic, "algorithmic_bytes": int(kernel_bytes[dom])}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "sh_degree": SH_DEG,
+                   "resolution": f"{W_IMG}x{H_IMG}", "tile": f"{TILE[0]}x{TILE[1]}",
+                   "parallelism": f"replicas x{world}", "visible_gaussians": V, "pairs": P,
+                   "l2": "inputs larger than L2 (2.1 GB resident state), no flush"},
+        "roofline": roofline,
+        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(tgt_np.nbytes), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "loss": loss_val,
+    }
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def cpu_step_sample(d, row_frac: int = 3, n_blocks: int = 40, seed: int = 0) -> dict:
+    """Time the oracle's step on a bounded sample and scale it to one step.
+
+    Per-Gaussian stages (Morton codes + sort, cluster cull, preprocess,
+    variance, preprocess backward, Adam) run on every row_frac-th Gaussian
+    and are scaled by row_frac. Per-tile stages (binning, forward, loss,
+    backward) run on n_blocks blocks of 4 x 4 tiles drawn from the tile grid,
+    each on exactly its own splats (camera cropped to the block, OpenMP over
+    its 16 tiles), and are scaled by (number of tiles) / (sampled tiles).
+    """
+    import oracle
+    sc, cam, tgt = d["scene"], d["camera"], d["target"]
+    n = sc["mean"].shape[0]
+    rows = np.arange(0, n, row_frac)
+    sub = {k: (np.asarray(v)[rows] if k != "sh_degree" else v) for k, v in sc.items()}
+    t = {}
+
+    def timed(name, fn):
+        a = time.perf_counter()
+        r = fn()
+        t[name] = time.perf_counter() - a
+        return r
+
+    timed("a1", lambda: oracle.morton_reorder(sub))
+    timed("a2", lambda: oracle.cluster_cull(sub, cam, 128))
+    timed("a3", lambda: oracle.preprocess(sub, cam, TILE))
+    # per-tile work needs every splat of a block: project the full scene once
+    # (untimed setup; its cost is counted by the a3 sample above)
+    full = oracle.preprocess(sc, cam, TILE)
+    gx, gy = -(-cam["width"] // TILE[0]), -(-cam["height"] // TILE[1])
+    rect = full["rect"]
+    live = full["radius"] > 0
+    rng = np.random.default_rng(seed)
+    bs = 4
+    tile_time, tiles_done = 0.0, 0
+    for _ in range(n_blocks):
+        bx, by = int(rng.integers(0, gx - bs + 1)), int(rng.integers(0, gy - bs + 1))
+        sel = np.flatnonzero(live & (rect[:, 0] < bx + bs) & (rect[:, 2] > bx) &
+                             (rect[:, 1] < by + bs) & (rect[:, 3] > by))
+        spt = {k: full[k][sel] for k in ("uv", "conic", "opacity", "rgb", "depth", "radius")}
+        spt["uv"] = spt["uv"] - np.array([bx * TILE[0], by * TILE[1]], np.float64)
+        bw_, bh_ = bs * TILE[0], bs * TILE[1]
+        ccam = dict(cam, width=bw_, height=bh_)
+        tg = np.zeros((3, bh_, bw_), np.float32)
+        part = tgt[:, by * TILE[1]:by * TILE[1] + bh_, bx * TILE[0]:bx * TILE[0] + bw_]
+        tg[:, :part.shape[1], :part.shape[2]] = part
+        a = time.perf_counter()
+        vals, ranges, P = oracle.bin_splats(spt["uv"][:, 0], spt["uv"][:, 1], spt["radius"],
+                                            spt["depth"], bw_, bh_, TILE)
+        fw = oracle.render_fwd(spt, vals, ranges, ccam, TILE)
+        L, dL = oracle.l1_loss(fw["image"], tg)
+        oracle.render_bwd(spt, vals, ranges, ccam, dL, TILE)
+        tile_time += time.perf_counter() - a
+        tiles_done += bs * bs
+    g9 = np.random.default_rng(1).standard_normal((rows.size, 9)) * 1e-6
+    timed("a8", lambda: oracle.opacity_variance(np.abs(g9[:, 0]), g9[:, 1],
+                                                np.ones(rows.size, np.int64)))
+    grads = timed("a9", lambda: oracle.preprocess_bwd(sub, cam, g9))
+    planes = oracle.scene_planes(sub)
+    gp = oracle.grad_planes(grads)
+    m, v = np.zeros_like(planes), np.zeros_like(planes)
+    from paper_2503_01199_gb300 import pipeline as PL
+    lr = np.asarray(PL.lr_per_plane(SH_DEG), np.float64)
+    timed("a10", lambda: oracle.adam(planes, gp, m, v, lr, 1, np.arange(rows.size, dtype=np.uint32)))
+    per_row = sum(t.values()) * row_frac
+    per_tile = tile_time / max(1, tiles_done) * (gx * gy)
+    return {"seconds_per_step": per_row + per_tile, "sampled_seconds": sum(t.values()) + tile_time,
+            "row_frac": row_frac, "tiles": tiles_done, "n_tiles": gx * gy}
+
+
+def cpu_baseline(d) -> dict:
+    import oracle
+    oracle.build()
+    r = cpu_step_sample(d)
+    return {"value": round(1.0 / r["seconds_per_step"], 5), "unit": UNIT,
+            "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"oracle step on every {r['row_frac']}th Gaussian (per-Gaussian stages, "
+                       f"x{r['row_frac']}) plus {r['tiles']} of {r['n_tiles']} tiles in 4x4-tile "
+                       f"blocks (binning, forward, loss, backward, x{r['n_tiles']}/{r['tiles']}); "
+                       f"{r['sampled_seconds']:.1f} s of CPU work")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    d = make_workload()
+    for _ in range(args.warmup):
+        cpu_step_sample(d, row_frac=600, n_blocks=1)
+    secs = []
+    samp = None
+    for k in range(args.steps):
+        r = cpu_step_sample(d, row_frac=300, n_blocks=1, seed=k)
+        secs.append(r["seconds_per_step"])
+        samp = r
+    value = 1.0 / float(np.mean(secs))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(secs)), 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "sh_degree": SH_DEG,
+                      "resolution": f"{W_IMG}x{H_IMG}", "tile": f"{TILE[0]}x{TILE[1]}"},
+           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": oracle.threads(),
+                            "kind": "oracle",
+                            "sample": (f"each step: oracle on every {samp['row_frac']}th Gaussian "
+                                       f"and {samp['tiles']} tiles, scaled to the full step")},
+           "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-gaussians", type=int, default=None,
+                    help="smaller scene for profiling captures (not a bench line)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    args.warmup = max(args.warmup, 3)
+    out = run_gpu(args)
+    if out is None:
+        return
+    if args.n_gaussians:
+        out["config"]["n_gaussians"] = args.n_gaussians
+        out["config"]["workload"] = "profiling case: " + out["config"]["workload"].replace(
+            "3M Gaussians", f"{args.n_gaussians} Gaussians")
+    if out["n_gpus"] == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(make_workload())
+    else:
+        out["cpu_baseline"] = None
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,293 @@
+/*
+ * lgs.h -- C ABI of a GB300 (sm_103a) implementation of the training-step hot
+ * path of LiteGS (arXiv 2503.01199): the tile-based differentiable Gaussian
+ * rasterizer with its Cluster-Cull-Compact data path, per-Gaussian gradient
+ * reduction, opacity-gradient variance statistic and sparse Adam update.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* or documented as "device" are device pointers owned
+ *     by the caller. The library never allocates, frees or retains them.
+ *     Scratch memory comes from a caller-supplied workspace whose size is
+ *     given by the matching *_workspace_size() query. Host structs (camera,
+ *     Gaussian descriptor, splat descriptor) are read during the call only.
+ *   - Float arrays must be 16-byte aligned; plane strides are in elements
+ *     and must be multiples of 4.
+ *   - Every call only enqueues work on `stream` (a cudaStream_t; 0 is the
+ *     legacy default stream) and returns without synchronising, so a
+ *     sequence of calls can be captured in a CUDA graph. Counts that are only
+ *     known on the device (the number of visible Gaussians V, the number of
+ *     tile/splat pairs P) stay on the device; kernels are sized by the host
+ *     bound (n, capacity) and read the device count.
+ *   - Return value: LGS_OK, LGS_ERR_INVALID_ARG (null or misaligned pointer,
+ *     bad size, unsupported option; nothing was enqueued), LGS_ERR_CUDA (a
+ *     launch failed; see lgs_last_cuda_error()), LGS_ERR_CAPACITY (only from
+ *     lgs_get_overflow()).
+ *
+ * Gaussian parameters (Sec. 3: g_i = {p, Sigma, c, o}) are stored as planes
+ * of float32, plane k of Gaussian i at data[k * stride + i]:
+ *   0..2   centre p (world x, y, z)
+ *   3..5   log of the per-axis scale (Sigma = R S S^T R^T, S = diag(exp(.)))
+ *   6..9   rotation quaternion (w, x, y, z), any non-zero length
+ *   10     opacity logit (o = sigmoid(logit))
+ *   11..   colour coefficients c_i: SH coefficient k, channel ch at plane
+ *          11 + 3k + ch, k < (sh_degree + 1)^2 (real SH, l-major, m = -l..l)
+ * so a Gaussian has 11 + 3 (deg + 1)^2 planes: 14 at degree 0, 59 at 3.
+ *
+ * Projected splat record (Sec. 3: {x, y, Sigma^screen, c, o}), 12 floats per
+ * visible Gaussian j, 48-byte aligned rows of `rec`:
+ *   rec[12 j + 0..8] = u, v, A, B, C, o, r, g, b
+ * where (u, v) is the screen centre in pixels, (A, B, C) the inverse 2D
+ * covariance [[A, B], [B, C]] used in the exponent of Eq. 2, o the opacity
+ * and (r, g, b) the colour. Slots 9..11 are reserved. depth[j] is the
+ * camera-space z, radius[j] the integer screen radius (0 = culled).
+ *
+ * Pixel (x, y) is sampled at its centre (x + 0.5, y + 0.5). Images are
+ * planar float32 [3][height][width].
+ */
+#ifndef LGS_H
+#define LGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lgs_status;
+#define LGS_OK 0
+#define LGS_ERR_INVALID_ARG 1
+#define LGS_ERR_CAPACITY 2
+#define LGS_ERR_CUDA 3
+#define LGS_ERR_TIMEOUT 4
+
+typedef void *lgs_stream; /* cudaStream_t */
+
+/* Number of parameter planes of a Gaussian of the given SH degree. */
+#define LGS_NUM_PLANES(deg) (11 + 3 * ((deg) + 1) * ((deg) + 1))
+#define LGS_MAX_PLANES 59
+#define LGS_SPLAT_FLOATS 12
+#define LGS_GRAD_FLOATS 16
+
+/* Pinhole camera. R is the row-major world-to-camera rotation, t the
+ * translation (camera = R world + t); the camera looks along +z. */
+typedef struct lgs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear; /* Gaussians with camera z <= znear are culled */
+    float bg[3]; /* background colour composited behind the last splat */
+} lgs_camera;
+
+/* Gaussian parameter planes (see above). Device memory. */
+typedef struct lgs_gaussians {
+    float *data;
+    int64_t n;      /* number of Gaussians */
+    int64_t stride; /* plane stride in floats, >= n, multiple of 4 */
+    int32_t sh_degree; /* 0..3 */
+    int32_t reserved;
+} lgs_gaussians;
+
+/* Projected splats, indexed by compacted index j < V. Device memory. */
+typedef struct lgs_splats {
+    float *rec;       /* [capacity][12] */
+    float *depth;     /* [capacity]     */
+    int32_t *radius;  /* [capacity]     */
+    int64_t capacity; /* rows available; must be >= the V it is used with */
+} lgs_splats;
+
+/* Library version string and the CUDA error of the last failed launch. */
+const char *lgs_version(void);
+int32_t lgs_last_cuda_error(void);
+
+/* Number of kernels this library has launched in this process (all
+ * devices, all threads); for accounting, e.g. launches per training step. */
+uint64_t lgs_kernel_launches(void);
+
+/* ------------------------------------------------------------------------
+ * a1. Morton re-sort (Sec. 3.2.1). Computes the 64-bit Morton code of every
+ * centre (planes 0..2 of src): centres normalised to [0,1]^3 by their
+ * bounding box (a degenerate axis maps to 0), scaled by 2^21 - 1 and
+ * truncated in single precision, bits interleaved x, y, z from the least
+ * significant bit (the paper's printed shifts 2k, 2k+1, 2k+2 are read as
+ * 3k, 3k+1, 3k+2). Sorts the codes stably (ties keep the input order) and
+ * gathers all n_planes planes of src into dst in that order:
+ *   dst[k * stride + i] = src[k * stride + perm[i]].
+ * src and dst must not overlap; plane count may include optimiser moments
+ * stored as further planes with the same stride.
+ * Outputs (device, nullable): codes_out[i] = sorted code, perm_out[i] = row
+ * of src that landed in row i.
+ * ---------------------------------------------------------------------- */
+size_t lgs_morton_workspace_size(int64_t n);
+lgs_status lgs_morton_reorder(const float *src, float *dst, int64_t n, int64_t stride,
+                              int32_t n_planes, uint64_t *codes_out, uint32_t *perm_out,
+                              void *workspace, size_t workspace_bytes, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a2. Cluster-Cull-Compact (Sec. 3.2.2, App. A.3 figure). Rows are grouped
+ * into clusters of cluster_size consecutive rows (the last may be partial).
+ * Each cluster's axis-aligned box bounds its centres widened by 3 x the
+ * largest scale of each Gaussian; a cluster is culled when its box lies
+ * entirely outside one of five planes: the near plane z = znear and the four
+ * side planes through the camera centre at 1.3 x the half field of view
+ * (the paper names view-frustum culling of cluster AABBs; the planes and the
+ * widening are this library's reading). Visible clusters are compacted in
+ * increasing order: map[j] is the row of compacted index j, and
+ * *d_num_visible = V, the total rows of visible clusters.
+ * Outputs (device): map [n] (rows >= V undefined), d_num_visible [1];
+ * optional aabb [ceil(n / cluster_size)][6] (min xyz, max xyz) and
+ * cluster_visible [ceil(n / cluster_size)] (0/1).
+ * The paper copies visible rows into a contiguous buffer; here the map is
+ * the compaction (kernels read cluster-contiguous rows through it), and
+ * lgs_compact_gather() performs the physical copy when one is wanted.
+ * ---------------------------------------------------------------------- */
+size_t lgs_ccc_workspace_size(int64_t n, int32_t cluster_size);
+lgs_status lgs_cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *cam,
+                                    int32_t cluster_size, float *aabb_out,
+                                    uint32_t *cluster_visible_out, uint32_t *map_out,
+                                    int32_t *d_num_visible, void *workspace,
+                                    size_t workspace_bytes, lgs_stream stream);
+
+/* dst[k * dst_stride + j] = src[k * src_stride + map[j]] for j < V (device). */
+lgs_status lgs_compact_gather(const float *src, int64_t src_stride, float *dst,
+                              int64_t dst_stride, int32_t n_planes, const uint32_t *map,
+                              const int32_t *d_num_visible, int64_t max_rows,
+                              lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a3. Preprocess (Sec. 3: the projected primitive {x, y, Sigma^screen, c,
+ * o}; the paper inherits the projection from 3DGS). For compacted index
+ * j < V, row i = map[j] (map NULL: i = j, d_num_visible NULL: V = g->n):
+ *   camera-space centre t = R p + T; culled if t.z <= znear;
+ *   Sigma = R(q) diag(exp(2 s)) R(q)^T;
+ *   J = [[fx/z, 0, -fx x'/z^2], [0, fy/z, -fy y'/z^2]] with x', y' the
+ *   centre clamped to 1.3 x the half field of view;
+ *   Sigma2D = J R Sigma R^T J^T + 0.3 I; (A, B, C) = inverse of Sigma2D;
+ *   (u, v) = (fx x/z + cx, fy y/z + cy);
+ *   radius = ceil(3 sqrt(lambda_max)), lambda_max = m + sqrt(max(0.1, m^2 - det)),
+ *   m = trace/2; culled (radius 0) if its tile rectangle is empty;
+ *   colour = max(0, sum_k c_k Y_k(dir) + 0.5), dir = (p - camera centre)/|.|;
+ *   o = sigmoid(logit).
+ * Writes out->rec, out->depth, out->radius rows j < V.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_preprocess(const lgs_gaussians *g, const uint32_t *map,
+                          const int32_t *d_num_visible, const lgs_camera *cam, int32_t tile_w,
+                          int32_t tile_h, const lgs_splats *out, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a4. Tile binning and sort (Sec. 3.1 "tile-based method"; Eq. 1 requires
+ * each tile's splats in depth order s(i)). A splat is listed in every tile
+ * whose pixel square meets [u - r, u + r] x [v - r, v + r]:
+ *   x0 = floor((u - r) / tile_w), x1 = floor((u + r) / tile_w) + 1 (same in
+ *   y), clamped to the tile grid, computed in single precision.
+ * Each tile's list is in increasing depth; equal depths keep increasing
+ * compacted index (a stable sort of the key (tile << 32 | depth bits)).
+ * Outputs (device): vals[P] = compacted splat index of each pair, grouped by
+ * tile; tile_ranges[2 t], [2 t + 1] = begin, end of tile t (row-major tile
+ * id t = ty * grid_w + tx); *d_num_pairs = P.
+ * If P > pair_capacity only the first pair_capacity pairs are written, the
+ * device overflow flag is raised and lgs_get_overflow() reports the size
+ * needed; the image is then incomplete.
+ * ---------------------------------------------------------------------- */
+size_t lgs_bin_sort_workspace_size(int64_t max_splats, int64_t pair_capacity, int32_t n_tiles);
+lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int64_t max_splats,
+                        const lgs_camera *cam, int32_t tile_w, int32_t tile_h, uint32_t *vals,
+                        int64_t pair_capacity, int64_t *d_num_pairs, uint32_t *tile_ranges,
+                        void *workspace, size_t workspace_bytes, lgs_stream stream);
+
+/* Synchronises the device, returns LGS_ERR_CAPACITY and the largest pair
+ * count seen if some lgs_bin_sort overflowed since the last query (and
+ * clears the flag), else LGS_OK with *needed = 0. */
+lgs_status lgs_get_overflow(int64_t *needed);
+
+/* ------------------------------------------------------------------------
+ * a5. Forward rasterisation (Eq. 1-2, Alg. 1). Per pixel, front to back
+ * over its tile's list: alpha = min(0.99, o exp(-0.5 (A dx^2 + C dy^2) -
+ * B dx dy)) with (dx, dy) = (u, v) - pixel centre; alpha < 1/255 is skipped;
+ * if T (1 - alpha) < 1e-4 the pixel stops without this splat; otherwise
+ * colour += c alpha T and T *= 1 - alpha. image = colour + T bg.
+ * Outputs (device): image [3][H][W]; final_T [H][W]; last_contrib [H][W] =
+ * 1 + position within the tile list of the last composited splat (0: none).
+ * tile_w x tile_h must be 16 x 16.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
+                          const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
+                          int32_t tile_h, float *image, float *final_T, int32_t *last_contrib,
+                          lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a6. L1 photometric loss (the paper does not state its loss; this is the
+ * L1 term of 3DGS): loss = mean |image - target| over n values,
+ * dL_dimage = sign(image - target) / n (sign(0) = 0). *d_loss (device) is
+ * overwritten.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float *dL_dimage,
+                       float *d_loss, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a7. Backward rasterisation with per-Gaussian reduction (Eq. 3; App. A.1
+ * Eq. 4-6) and opacity-gradient moments (Sec. 3.3). Per pixel the included
+ * splats are revisited back to front from last_contrib, the transmittance
+ * recovered as T / (1 - alpha) from final_T, and
+ *   dL/dc = alpha T dL/dI,
+ *   dL/dalpha = T (c - acc) . dL/dI - T_final bg . dL/dI / (1 - alpha),
+ * acc = colour composited behind. Per splat the per-pixel terms are summed
+ * within the tile before one atomic add per value per tile.
+ * grad_acc (device) [max_splats][16] floats, row j:
+ *   0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 do (activated opacity), 6..8 dr dg db,
+ *   9 S = sum of (dL/do per pixel)^2, 10 M = sum of dL/do per pixel,
+ *   11 C = count of included fragments as uint32, 12..15 zero.
+ * accumulate = 0 zeroes rows j < max_splats first; 1 adds to them.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
+                          const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
+                          int32_t tile_h, const float *final_T, const int32_t *last_contrib,
+                          const float *dL_dimage, float *grad_acc, int64_t max_splats,
+                          int32_t accumulate, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a8. Densification metric (Sec. 3.3): C Var = S - M^2 / C (0 if C = 0) for
+ * compacted j < V, written to metric[map[j]] (map NULL: metric[j]).
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,
+                                const int32_t *d_num_visible, int64_t max_rows, float *metric,
+                                lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a9. Preprocess backward: the chain rule through a3 from grad_acc rows
+ * 0..8 to the parameter planes. For j < V, writes plane k, row map[j] of
+ * grad_planes (stride g->stride, LGS_NUM_PLANES(deg) planes); other rows are
+ * not touched. Every clamp passes zero gradient while active.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_preprocess_bwd(const lgs_gaussians *g, const uint32_t *map,
+                              const int32_t *d_num_visible, const lgs_camera *cam,
+                              const float *grad_acc, float *grad_planes, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a10. Adam on visible rows only (Sec. 3.2.3: sparse update at cluster
+ * granularity on contiguous blocks). For j < V, row i = map[j], plane k:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p -= lr[k] (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * lr is a host array of n_planes (<= 64) learning rates. Rows of culled
+ * clusters are not touched.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, int64_t stride,
+                         int32_t n_planes, const float *lr, float beta1, float beta2, float eps,
+                         int32_t step, const uint32_t *map, const int32_t *d_num_visible,
+                         int64_t max_rows, lgs_stream stream);
+
+/* a9 + a10 in one pass: the gradient of each parameter is computed and
+ * applied at once, without a gradient buffer. m and v are planes with the
+ * stride of g; g->data is updated in place. Same results as lgs_preprocess_bwd
+ * followed by lgs_adam_step up to rounding. */
+lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
+                                   const uint32_t *map, const int32_t *d_num_visible,
+                                   const lgs_camera *cam, const float *grad_acc,
+                                   const float *lr, float beta1, float beta2, float eps,
+                                   int32_t step, lgs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGS_H */

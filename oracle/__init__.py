@@ -12,13 +12,15 @@ on first use and converts numpy arrays in and out.
 
 Thresholds that a single-precision kernel may decide differently from this
 double-precision code are reported rather than hidden:
-  * preprocess ``flags`` bit0: radius or tile rectangle within rounding of a
-    boundary; bit1: the near-plane test within rounding;
+  * preprocess ``flags`` bit0: the radius within rounding of a step; bit1:
+    the near-plane test within rounding; bit2: the tile rectangle's edges
+    within rounding of a tile boundary;
   * render ``pixflags`` bit0: an alpha (1/255) or transmittance (1e-4) test
-    within a relative 1e-4 of its threshold; bit1: two included splats whose
-    depths differ by less than a relative 2e-6 (their order may flip);
+    within a relative margin of its threshold (set_margins(): 2e-4 by
+    default); bit1: two included splats whose depths differ by less than a
+    relative 2e-6 (their order may flip);
   * render-backward ``sflags`` bit0: a fragment in a flagged pixel; bit1: a
-    fragment with o*G within 1e-4 of the 0.99 clamp.
+    fragment with o*G within the alpha margin of the 0.99 clamp.
 Parity tests compare exactly where no flag is set and count the flagged.
 
 Every function here is pinned by the CPU tests in ``tests/test_oracle_*.py``
@@ -28,6 +30,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import shutil
 import subprocess
 from pathlib import Path
@@ -49,7 +52,9 @@ def build(force: bool = False) -> Path:
     """Compile lgs_oracle.c into oracle/_build/liblgs_oracle.so (gcc, -O2)."""
     global OMP
     _OUT.parent.mkdir(exist_ok=True)
-    if not force and _OUT.exists() and _OUT.stat().st_mtime >= _SRC.stat().st_mtime:
+    machine = _OUT.parent / "machine.txt"
+    if (not force and _OUT.exists() and _OUT.stat().st_mtime >= _SRC.stat().st_mtime
+            and machine.exists() and machine.read_text().strip() == platform.machine()):
         OMP = (_OUT.parent / "omp").exists()
         return _OUT
     cc = shutil.which("gcc") or shutil.which("cc")
@@ -64,6 +69,7 @@ def build(force: bool = False) -> Path:
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
     os.replace(tmp, _OUT)
+    machine.write_text(platform.machine())
     flag = _OUT.parent / "omp"
     if omp:
         flag.write_text("1")
@@ -82,6 +88,7 @@ def lib():
         i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         sig = {
             "or_version": (i32, []),
+            "or_set_margins": (None, [f64] * 5),
             "or_sh_basis_spherical": (None, [i32, P, P]),
             "or_sh_basis_cartesian": (None, [i32, P, P, P]),
             "or_preprocess": (None, [i64, i32, P, P, P, P, P, P, i32, i32, P, P, P, P, P, P, P, P]),
@@ -103,6 +110,25 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+MARGINS_END_TO_END = (2e-4, 2e-4, 2e-3, 1e-5, 5e-7)
+MARGINS_SHARED_SPLATS = (2e-5, 2e-4, 2e-3, 1e-5, 0.0)
+
+
+def set_margins(alpha: float, T: float, px: float, radius: float, depth: float) -> None:
+    """Flag margins (relative for alpha, T, radius, depth; pixels for px).
+
+    A single-precision kernel computes alpha = o exp(power) with a relative
+    error of a few 1e-6 when it reads the same float32 splats
+    (MARGINS_SHARED_SPLATS), and of a few 1e-5 when it also projected them
+    itself (MARGINS_END_TO_END, the default: the screen centre carries a
+    1e-5 px rounding that the exponent's slope of ~3 / sigma amplifies).
+    Depths: with shared float32 depths both sides order equal keys by the
+    same stable rule (margin 0 disables the flag); a kernel that computes
+    the depth itself is within a few ulps (5e-7 relative).
+    """
+    lib().or_set_margins(alpha, T, px, radius, depth)
 
 
 def threads() -> int:
@@ -322,11 +348,10 @@ def scene_planes(scene: dict) -> np.ndarray:
     """Stack a scene into planes [11 + 3K, N]: mean(3), log-scale(3),
     quat(4), logit, then SH coefficient k channel c at 11 + 3k + c."""
     n = scene["mean"].shape[0]
-    return np.concatenate([np.asarray(scene["mean"], np.float64).T,
-                           np.asarray(scene["log_scale"], np.float64).T,
-                           np.asarray(scene["quat"], np.float64).T,
-                           np.asarray(scene["logit"], np.float64)[None],
-                           np.asarray(scene["sh"], np.float64).reshape(n, -1).T])
+    return np.ascontiguousarray(np.concatenate([
+        np.asarray(scene["mean"], np.float64).T, np.asarray(scene["log_scale"], np.float64).T,
+        np.asarray(scene["quat"], np.float64).T, np.asarray(scene["logit"], np.float64)[None],
+        np.asarray(scene["sh"], np.float64).reshape(n, -1).T]))
 
 
 def planes_scene(planes: np.ndarray, sh_degree: int) -> dict:
@@ -338,8 +363,8 @@ def planes_scene(planes: np.ndarray, sh_degree: int) -> dict:
 
 def grad_planes(g: dict) -> np.ndarray:
     n = g["mean"].shape[0]
-    return np.concatenate([g["mean"].T, g["log_scale"].T, g["quat"].T, g["logit"][None],
-                           g["sh"].reshape(n, -1).T])
+    return np.ascontiguousarray(np.concatenate([g["mean"].T, g["log_scale"].T, g["quat"].T,
+                                                g["logit"][None], g["sh"].reshape(n, -1).T]))
 
 
 # --------------------------------------------------------------------------

@@ -40,12 +40,21 @@
 
 /* Relative margins below which a double-precision decision is reported as
  * too close to its threshold for a single-precision kernel to be expected
- * to take the same branch (see the header of oracle/__init__.py). */
-#define OR_MARGIN_ALPHA 1e-4
-#define OR_MARGIN_T 1e-4
-#define OR_MARGIN_PX 2e-3
-#define OR_MARGIN_RADIUS 1e-5
-#define OR_MARGIN_DEPTH 2e-6
+ * to take the same branch (see the header of oracle/__init__.py). They only
+ * set the flags; no result depends on them. */
+static double OR_MARGIN_ALPHA = 2e-4;
+static double OR_MARGIN_T = 2e-4;
+static double OR_MARGIN_PX = 2e-3;
+static double OR_MARGIN_RADIUS = 1e-5;
+static double OR_MARGIN_DEPTH = 2e-6;
+
+void or_set_margins(double alpha, double T, double px, double radius, double depth) {
+    OR_MARGIN_ALPHA = alpha;
+    OR_MARGIN_T = T;
+    OR_MARGIN_PX = px;
+    OR_MARGIN_RADIUS = radius;
+    OR_MARGIN_DEPTH = depth;
+}
 
 int or_version(void) { return 1; }
 
@@ -337,8 +346,9 @@ static int frac_near_int(double x, double margin) {
     return f < margin || f > 1.0 - margin;
 }
 
-/* flags bit0: radius or tile rectangle within rounding of a boundary;
- *       bit1: near-plane test within rounding of its threshold. */
+/* flags bit0: 3 sqrt(lambda_max) within rounding of an integer (radius);
+ *       bit1: near-plane test within rounding of its threshold;
+ *       bit2: u -+ r or v -+ r within rounding of a tile boundary. */
 void or_preprocess(int64_t n, int deg, const double *mean, const double *log_scale,
                    const double *quat, const double *logit, const double *sh, const double *camv,
                    int tw, int th, double *uv, double *conic, double *depth, double *opacity,
@@ -361,7 +371,7 @@ void or_preprocess(int64_t n, int deg, const double *mean, const double *log_sca
             double m = OR_MARGIN_PX / tw;
             if (frac_near_int((g.u - g.radius) / tw, m) || frac_near_int((g.u + g.radius) / tw, m) ||
                 frac_near_int((g.v - g.radius) / th, m) || frac_near_int((g.v + g.radius) / th, m))
-                f |= 1;
+                f |= 4;
         }
         flags[i] = f;
         if (g.culled) {
@@ -590,7 +600,7 @@ static int64_t walk_pixel(double pxc, double pyc, const double *uv, const double
         double Tn = T * (1.0 - a);
         if (fabs(Tn - OR_T_MIN) < OR_MARGIN_T * OR_T_MIN) *pf |= 1;
         if (Tn < OR_T_MIN) { if (h) *h = fnv(*h, (uint64_t)k | (1ULL << 62)); break; }
-        if (prev_depth >= 0.0 && fabs(depth[j] - prev_depth) <= OR_MARGIN_DEPTH * depth[j]) *pf |= 2;
+        if (prev_depth >= 0.0 && fabs(depth[j] - prev_depth) < OR_MARGIN_DEPTH * depth[j]) *pf |= 2;
         prev_depth = depth[j];
         if (fr) {
             fr[nin].pos = k; fr[nin].j = j; fr[nin].G = G; fr[nin].a = a; fr[nin].T = T;

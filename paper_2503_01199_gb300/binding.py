@@ -1,0 +1,294 @@
+"""Thin Python binding of liblgs (include/lgs.h): the same entry points,
+taking torch CUDA tensors and marshalling them to pointers, sizes and the
+current CUDA stream. Every step runs in the library's kernels; nothing here
+computes. There is no fallback: if the library cannot be loaded or CUDA is
+not available, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LGS_OK, LGS_ERR_INVALID_ARG, LGS_ERR_CAPACITY, LGS_ERR_CUDA, LGS_ERR_TIMEOUT = 0, 1, 2, 3, 4
+SPLAT_FLOATS = 12
+GRAD_FLOATS = 16
+MAX_PLANES = 59
+
+ENTRY_POINTS = (
+    "lgs_version", "lgs_last_cuda_error", "lgs_kernel_launches", "lgs_morton_workspace_size", "lgs_morton_reorder",
+    "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_compact_gather", "lgs_preprocess",
+    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_raster_fwd",
+    "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
+    "lgs_adam_step", "lgs_preprocess_bwd_adam",
+)
+
+
+def num_planes(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+class LgsCamera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("znear", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class LgsGaussians(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int64),
+                ("sh_degree", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class LgsSplats(ctypes.Structure):
+    _fields_ = [("rec", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("radius", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64)]
+
+
+class LgsError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblgs.so (building it if needed). Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    path = library_path()
+    if not path.exists():
+        raise LgsError(f"liblgs.so not found at {path}; run paper_2503_01199_gb300/build.py")
+    L = ctypes.CDLL(str(path))
+    P, i32, i64, f32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    sig = {
+        "lgs_version": (ctypes.c_char_p, []),
+        "lgs_last_cuda_error": (i32, []),
+        "lgs_kernel_launches": (ctypes.c_uint64, []),
+        "lgs_morton_workspace_size": (sz, [i64]),
+        "lgs_morton_reorder": (i32, [P, P, i64, i64, i32, P, P, P, sz, P]),
+        "lgs_ccc_workspace_size": (sz, [i64, i32]),
+        "lgs_cluster_cull_compact": (i32, [P, P, i32, P, P, P, P, P, sz, P]),
+        "lgs_compact_gather": (i32, [P, i64, P, i64, i32, P, P, i64, P]),
+        "lgs_preprocess": (i32, [P, P, P, P, i32, i32, P, P]),
+        "lgs_bin_sort_workspace_size": (sz, [i64, i64, i32]),
+        "lgs_bin_sort": (i32, [P, P, i64, P, i32, i32, P, i64, P, P, P, sz, P]),
+        "lgs_get_overflow": (i32, [P]),
+        "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, P, P, P, P]),
+        "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
+        "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, P, P, P, P, i64, i32, P]),
+        "lgs_opacity_variance": (i32, [P, P, P, i64, P, P]),
+        "lgs_preprocess_bwd": (i32, [P, P, P, P, P, P, P]),
+        "lgs_adam_step": (i32, [P, P, P, P, i64, i32, P, f32, f32, f32, i32, P, P, i64, P]),
+        "lgs_preprocess_bwd_adam": (i32, [P, P, P, P, P, P, P, P, f32, f32, f32, i32, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != LGS_OK:
+        err = _lib.lgs_last_cuda_error() if _lib is not None else 0
+        names = {1: "LGS_ERR_INVALID_ARG", 2: "LGS_ERR_CAPACITY", 3: "LGS_ERR_CUDA", 4: "LGS_ERR_TIMEOUT"}
+        raise LgsError(f"{what} failed: {names.get(status, status)} (cuda error {err})")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if t.numel() and not t.is_cuda:
+        raise LgsError("liblgs takes CUDA tensors only")
+    if not t.is_contiguous():
+        raise LgsError("liblgs takes contiguous tensors only")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------------
+# descriptors
+# --------------------------------------------------------------------------
+def camera_struct(cam: dict) -> LgsCamera:
+    c = LgsCamera()
+    R = [float(x) for x in np.asarray(cam["R"]).reshape(9)]
+    t = [float(x) for x in np.asarray(cam["t"]).reshape(3)]
+    bg = [float(x) for x in np.asarray(cam["bg"]).reshape(3)]
+    c.R[:] = R
+    c.t[:] = t
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.znear = float(cam["znear"])
+    c.bg[:] = bg
+    return c
+
+
+def gaussians_struct(planes: torch.Tensor, n: int, sh_degree: int) -> LgsGaussians:
+    """planes: float32 CUDA tensor [>= num_planes, stride]."""
+    g = LgsGaussians()
+    g.data = _ptr(planes)
+    g.n = int(n)
+    g.stride = int(planes.shape[-1])
+    g.sh_degree = int(sh_degree)
+    return g
+
+
+def splats_struct(rec: torch.Tensor, depth: torch.Tensor, radius: torch.Tensor) -> LgsSplats:
+    s = LgsSplats()
+    s.rec, s.depth, s.radius = _ptr(rec), _ptr(depth), _ptr(radius)
+    s.capacity = int(depth.shape[0])
+    return s
+
+
+# --------------------------------------------------------------------------
+# entry points
+# --------------------------------------------------------------------------
+def lgs_version() -> str:
+    return load().lgs_version().decode()
+
+
+def lgs_kernel_launches() -> int:
+    return int(load().lgs_kernel_launches())
+
+
+def lgs_morton_workspace_size(n: int) -> int:
+    return int(load().lgs_morton_workspace_size(n))
+
+
+def lgs_morton_reorder(src, dst, n, n_planes, codes_out, perm_out, workspace, stream=None):
+    L = load()
+    _check(L.lgs_morton_reorder(_ptr(src), _ptr(dst), n, src.shape[-1], n_planes, _ptr(codes_out),
+                                _ptr(perm_out), _ptr(workspace), workspace.numel(),
+                                _stream(stream)), "lgs_morton_reorder")
+
+
+def lgs_ccc_workspace_size(n: int, cluster_size: int) -> int:
+    return int(load().lgs_ccc_workspace_size(n, cluster_size))
+
+
+def lgs_cluster_cull_compact(g: LgsGaussians, cam: LgsCamera, cluster_size, aabb_out,
+                             cluster_visible_out, map_out, d_num_visible, workspace, stream=None):
+    L = load()
+    _check(L.lgs_cluster_cull_compact(ctypes.byref(g), ctypes.byref(cam), cluster_size,
+                                      _ptr(aabb_out), _ptr(cluster_visible_out), _ptr(map_out),
+                                      _ptr(d_num_visible), _ptr(workspace), workspace.numel(),
+                                      _stream(stream)), "lgs_cluster_cull_compact")
+
+
+def lgs_compact_gather(src, dst, n_planes, map_, d_num_visible, max_rows, stream=None):
+    L = load()
+    _check(L.lgs_compact_gather(_ptr(src), src.shape[-1], _ptr(dst), dst.shape[-1], n_planes,
+                                _ptr(map_), _ptr(d_num_visible), max_rows, _stream(stream)),
+           "lgs_compact_gather")
+
+
+def lgs_preprocess(g: LgsGaussians, map_, d_num_visible, cam: LgsCamera, tile_w, tile_h,
+                   out: LgsSplats, stream=None):
+    L = load()
+    _check(L.lgs_preprocess(ctypes.byref(g), _ptr(map_), _ptr(d_num_visible), ctypes.byref(cam),
+                            tile_w, tile_h, ctypes.byref(out), _stream(stream)), "lgs_preprocess")
+
+
+def lgs_bin_sort_workspace_size(max_splats: int, pair_capacity: int, n_tiles: int) -> int:
+    return int(load().lgs_bin_sort_workspace_size(max_splats, pair_capacity, n_tiles))
+
+
+def lgs_bin_sort(sp: LgsSplats, d_num_visible, max_splats, cam: LgsCamera, tile_w, tile_h, vals,
+                 d_num_pairs, tile_ranges, workspace, stream=None):
+    L = load()
+    _check(L.lgs_bin_sort(ctypes.byref(sp), _ptr(d_num_visible), max_splats, ctypes.byref(cam),
+                          tile_w, tile_h, _ptr(vals), vals.numel(), _ptr(d_num_pairs),
+                          _ptr(tile_ranges), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "lgs_bin_sort")
+
+
+def lgs_get_overflow() -> int:
+    """Returns the pair count needed by an overflowed lgs_bin_sort (0 if none)."""
+    L = load()
+    needed = ctypes.c_int64(0)
+    st = L.lgs_get_overflow(ctypes.byref(needed))
+    if st not in (LGS_OK, LGS_ERR_CAPACITY):
+        _check(st, "lgs_get_overflow")
+    return int(needed.value)
+
+
+def lgs_raster_fwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h, image,
+                   final_T, last_contrib, stream=None):
+    L = load()
+    _check(L.lgs_raster_fwd(ctypes.byref(sp), _ptr(vals), _ptr(tile_ranges), ctypes.byref(cam),
+                            tile_w, tile_h, _ptr(image), _ptr(final_T), _ptr(last_contrib),
+                            _stream(stream)), "lgs_raster_fwd")
+
+
+def lgs_loss_l1(image, target, dL_dimage, d_loss, stream=None):
+    L = load()
+    _check(L.lgs_loss_l1(_ptr(image), _ptr(target), image.numel(), _ptr(dL_dimage), _ptr(d_loss),
+                         _stream(stream)), "lgs_loss_l1")
+
+
+def lgs_raster_bwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h, final_T,
+                   last_contrib, dL_dimage, grad_acc, accumulate=False, stream=None):
+    L = load()
+    _check(L.lgs_raster_bwd(ctypes.byref(sp), _ptr(vals), _ptr(tile_ranges), ctypes.byref(cam),
+                            tile_w, tile_h, _ptr(final_T), _ptr(last_contrib), _ptr(dL_dimage),
+                            _ptr(grad_acc), grad_acc.shape[0], int(bool(accumulate)),
+                            _stream(stream)), "lgs_raster_bwd")
+
+
+def lgs_opacity_variance(grad_acc, map_, d_num_visible, max_rows, metric, stream=None):
+    L = load()
+    _check(L.lgs_opacity_variance(_ptr(grad_acc), _ptr(map_), _ptr(d_num_visible), max_rows,
+                                  _ptr(metric), _stream(stream)), "lgs_opacity_variance")
+
+
+def lgs_preprocess_bwd(g: LgsGaussians, map_, d_num_visible, cam: LgsCamera, grad_acc,
+                       grad_planes, stream=None):
+    L = load()
+    _check(L.lgs_preprocess_bwd(ctypes.byref(g), _ptr(map_), _ptr(d_num_visible),
+                                ctypes.byref(cam), _ptr(grad_acc), _ptr(grad_planes),
+                                _stream(stream)), "lgs_preprocess_bwd")
+
+
+def _lr_array(lr) -> ctypes.Array:
+    vals = [float(x) for x in lr]
+    arr = (ctypes.c_float * len(vals))(*vals)
+    return arr
+
+
+def lgs_adam_step(params, grads, m, v, n_planes, lr, beta1, beta2, eps, step, map_,
+                  d_num_visible, max_rows, stream=None):
+    L = load()
+    arr = _lr_array(lr)
+    _check(L.lgs_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.shape[-1],
+                           n_planes, arr, beta1, beta2, eps, step, _ptr(map_),
+                           _ptr(d_num_visible), max_rows, _stream(stream)), "lgs_adam_step")
+
+
+def lgs_preprocess_bwd_adam(g: LgsGaussians, m, v, map_, d_num_visible, cam: LgsCamera, grad_acc,
+                            lr, beta1, beta2, eps, step, stream=None):
+    L = load()
+    arr = _lr_array(lr)
+    _check(L.lgs_preprocess_bwd_adam(ctypes.byref(g), _ptr(m), _ptr(v), _ptr(map_),
+                                     _ptr(d_num_visible), ctypes.byref(cam), _ptr(grad_acc), arr,
+                                     beta1, beta2, eps, step, _stream(stream)),
+           "lgs_preprocess_bwd_adam")

@@ -1,0 +1,259 @@
+// extern "C" entry points of liblgs (declared in include/lgs.h): argument
+// checks, then the kernels of the other translation units.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+
+#include "lgs_internal.cuh"
+
+namespace lgs {
+
+// implemented in the other translation units
+size_t morton_workspace_size(int64_t n);
+lgs_status morton_reorder(const float *src, float *dst, int64_t n, int64_t stride, int n_planes,
+                          uint64_t *codes_out, uint32_t *perm_out, void *ws, cudaStream_t s);
+size_t ccc_workspace_size(int64_t n, int cs);
+lgs_status cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *cam, int cs,
+                                float *aabb_out, uint32_t *vis_out, uint32_t *map, int32_t *d_V,
+                                void *ws, cudaStream_t s);
+lgs_status compact_gather(const float *src, int64_t src_stride, float *dst, int64_t dst_stride,
+                          int n_planes, const uint32_t *map, const int32_t *d_V, int64_t max_rows,
+                          cudaStream_t s);
+lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
+                      const lgs_camera *cam, int tw, int th, const lgs_splats *out, cudaStream_t s);
+lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
+                          const lgs_camera *cam, const float *gacc, float *gout, cudaStream_t s);
+lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
+                               const int32_t *d_V, const lgs_camera *cam, const float *gacc,
+                               const float *lr, float b1, float b2, float eps, int step,
+                               cudaStream_t s);
+lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t stride, int np,
+                     const float *lr, float b1, float b2, float eps, int step, const uint32_t *map,
+                     const int32_t *d_V, int64_t max_rows, cudaStream_t s);
+size_t bin_sort_workspace_size(int64_t maxV, int64_t cap, int ntiles);
+lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, const lgs_camera *cam,
+                    int tw, int th, uint32_t *vals, int64_t cap, int64_t *d_P, uint32_t *ranges,
+                    void *ws, cudaStream_t s);
+lgs_status get_overflow(int64_t *needed);
+lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
+                      const lgs_camera *cam, int tw, int th, float *image, float *finalT,
+                      int32_t *last, cudaStream_t s);
+lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
+                      const lgs_camera *cam, int tw, int th, const float *finalT,
+                      const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
+                      int accumulate, cudaStream_t s);
+lgs_status loss_l1(const float *img, const float *tgt, int64_t n, float *g, float *loss,
+                   cudaStream_t s);
+lgs_status opacity_variance(const float *gacc, const uint32_t *map, const int32_t *d_V,
+                            int64_t max_rows, float *out, cudaStream_t s);
+
+namespace {
+thread_local int32_t t_last_error = 0;
+int g_sms[64] = {0};
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_cuda_error(cudaError_t e) { t_last_error = (int32_t)e; }
+
+lgs_status check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return LGS_ERR_CUDA;
+    }
+    return LGS_OK;
+}
+
+int num_sms() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!g_sms[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = n > 0 ? n : 1;
+    }
+    return g_sms[dev];
+}
+
+}  // namespace lgs
+
+using namespace lgs;
+
+namespace {
+
+bool bad_camera(const lgs_camera *c) {
+    return !c || c->width <= 0 || c->height <= 0 || !(c->fx > 0.f) || !(c->fy > 0.f) ||
+           !(c->znear > 0.f);
+}
+
+bool bad_gaussians(const lgs_gaussians *g) {
+    return !g || !g->data || g->n < 0 || g->n > 0x7fffffffLL || g->stride < g->n ||
+           (g->stride & 3) || g->sh_degree < 0 || g->sh_degree > 3 || !aligned16(g->data);
+}
+
+bool bad_splats(const lgs_splats *s, int64_t rows) {
+    return !s || !s->rec || !s->depth || !s->radius || s->capacity < rows || !aligned16(s->rec);
+}
+
+bool bad_tiles(const lgs_camera *c, int tw, int th) {
+    if (tw <= 0 || th <= 0) return true;
+    const int64_t n = ceil_div(c->width, tw) * ceil_div(c->height, th);
+    return n > 65536;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lgs_version(void) { return "lgs 0.1 (sm_103a)"; }
+
+int32_t lgs_last_cuda_error(void) { return t_last_error; }
+
+uint64_t lgs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+size_t lgs_morton_workspace_size(int64_t n) { return morton_workspace_size(n < 0 ? 0 : n); }
+
+lgs_status lgs_morton_reorder(const float *src, float *dst, int64_t n, int64_t stride,
+                              int32_t n_planes, uint64_t *codes_out, uint32_t *perm_out,
+                              void *workspace, size_t workspace_bytes, lgs_stream stream) {
+    if (!src || !dst || n <= 0 || n > 0x7fffffffLL || stride < n || (stride & 3) || n_planes < 3 ||
+        !aligned16(src) || !aligned16(dst) || src == dst || !workspace ||
+        workspace_bytes < morton_workspace_size(n))
+        return LGS_ERR_INVALID_ARG;
+    return morton_reorder(src, dst, n, stride, n_planes, codes_out, perm_out, workspace,
+                          as_stream(stream));
+}
+
+size_t lgs_ccc_workspace_size(int64_t n, int32_t cluster_size) {
+    return cluster_size > 0 ? ccc_workspace_size(n < 0 ? 0 : n, cluster_size) : 0;
+}
+
+lgs_status lgs_cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *cam,
+                                    int32_t cluster_size, float *aabb_out,
+                                    uint32_t *cluster_visible_out, uint32_t *map_out,
+                                    int32_t *d_num_visible, void *workspace,
+                                    size_t workspace_bytes, lgs_stream stream) {
+    if (bad_gaussians(g) || bad_camera(cam) || cluster_size <= 0 || !map_out || !d_num_visible ||
+        g->n == 0 || !workspace || workspace_bytes < ccc_workspace_size(g->n, cluster_size))
+        return LGS_ERR_INVALID_ARG;
+    return cluster_cull_compact(g, cam, cluster_size, aabb_out, cluster_visible_out, map_out,
+                                d_num_visible, workspace, as_stream(stream));
+}
+
+lgs_status lgs_compact_gather(const float *src, int64_t src_stride, float *dst,
+                              int64_t dst_stride, int32_t n_planes, const uint32_t *map,
+                              const int32_t *d_num_visible, int64_t max_rows,
+                              lgs_stream stream) {
+    if (!src || !dst || !map || n_planes <= 0 || max_rows < 0 || src_stride <= 0 ||
+        dst_stride < max_rows)
+        return LGS_ERR_INVALID_ARG;
+    return compact_gather(src, src_stride, dst, dst_stride, n_planes, map, d_num_visible, max_rows,
+                          as_stream(stream));
+}
+
+lgs_status lgs_preprocess(const lgs_gaussians *g, const uint32_t *map,
+                          const int32_t *d_num_visible, const lgs_camera *cam, int32_t tile_w,
+                          int32_t tile_h, const lgs_splats *out, lgs_stream stream) {
+    if (bad_gaussians(g) || bad_camera(cam) || bad_splats(out, g ? g->n : 0) ||
+        bad_tiles(cam, tile_w, tile_h))
+        return LGS_ERR_INVALID_ARG;
+    if (g->n == 0) return LGS_OK;
+    return preprocess(g, map, d_num_visible, cam, tile_w, tile_h, out, as_stream(stream));
+}
+
+size_t lgs_bin_sort_workspace_size(int64_t max_splats, int64_t pair_capacity, int32_t n_tiles) {
+    if (max_splats < 0 || pair_capacity < 0) return 0;
+    return bin_sort_workspace_size(max_splats, pair_capacity, n_tiles);
+}
+
+lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int64_t max_splats,
+                        const lgs_camera *cam, int32_t tile_w, int32_t tile_h, uint32_t *vals,
+                        int64_t pair_capacity, int64_t *d_num_pairs, uint32_t *tile_ranges,
+                        void *workspace, size_t workspace_bytes, lgs_stream stream) {
+    if (bad_camera(cam) || bad_splats(sp, max_splats) || bad_tiles(cam, tile_w, tile_h) ||
+        !vals || !d_num_pairs || !tile_ranges || max_splats <= 0 || max_splats > 0x7fffffffLL ||
+        pair_capacity <= 0 || pair_capacity > 0xffffffffLL || !workspace ||
+        workspace_bytes < bin_sort_workspace_size(max_splats, pair_capacity, 0))
+        return LGS_ERR_INVALID_ARG;
+    return bin_sort(sp, d_num_visible, max_splats, cam, tile_w, tile_h, vals, pair_capacity,
+                    d_num_pairs, tile_ranges, workspace, as_stream(stream));
+}
+
+lgs_status lgs_get_overflow(int64_t *needed) { return get_overflow(needed); }
+
+lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
+                          const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
+                          int32_t tile_h, float *image, float *final_T, int32_t *last_contrib,
+                          lgs_stream stream) {
+    if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !image || !final_T ||
+        !last_contrib || bad_tiles(cam, tile_w, tile_h))
+        return LGS_ERR_INVALID_ARG;
+    return raster_fwd(sp, vals, tile_ranges, cam, tile_w, tile_h, image, final_T, last_contrib,
+                      as_stream(stream));
+}
+
+lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float *dL_dimage,
+                       float *d_loss, lgs_stream stream) {
+    if (!image || !target || !dL_dimage || !d_loss || n <= 0) return LGS_ERR_INVALID_ARG;
+    return loss_l1(image, target, n, dL_dimage, d_loss, as_stream(stream));
+}
+
+lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
+                          const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
+                          int32_t tile_h, const float *final_T, const int32_t *last_contrib,
+                          const float *dL_dimage, float *grad_acc, int64_t max_splats,
+                          int32_t accumulate, lgs_stream stream) {
+    if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !final_T ||
+        !last_contrib || !dL_dimage || !grad_acc || !aligned16(grad_acc) || max_splats < 0 ||
+        bad_tiles(cam, tile_w, tile_h))
+        return LGS_ERR_INVALID_ARG;
+    return raster_bwd(sp, vals, tile_ranges, cam, tile_w, tile_h, final_T, last_contrib, dL_dimage,
+                      grad_acc, max_splats, accumulate, as_stream(stream));
+}
+
+lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,
+                                const int32_t *d_num_visible, int64_t max_rows, float *metric,
+                                lgs_stream stream) {
+    if (!grad_acc || !metric || max_rows < 0) return LGS_ERR_INVALID_ARG;
+    return opacity_variance(grad_acc, map, d_num_visible, max_rows, metric, as_stream(stream));
+}
+
+lgs_status lgs_preprocess_bwd(const lgs_gaussians *g, const uint32_t *map,
+                              const int32_t *d_num_visible, const lgs_camera *cam,
+                              const float *grad_acc, float *grad_planes, lgs_stream stream) {
+    if (bad_gaussians(g) || bad_camera(cam) || !grad_acc || !grad_planes || !aligned16(grad_acc))
+        return LGS_ERR_INVALID_ARG;
+    if (g->n == 0) return LGS_OK;
+    return preprocess_bwd(g, map, d_num_visible, cam, grad_acc, grad_planes, as_stream(stream));
+}
+
+lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, int64_t stride,
+                         int32_t n_planes, const float *lr, float beta1, float beta2, float eps,
+                         int32_t step, const uint32_t *map, const int32_t *d_num_visible,
+                         int64_t max_rows, lgs_stream stream) {
+    if (!params || !grads || !m || !v || !lr || n_planes <= 0 || n_planes > 64 || step < 1 ||
+        max_rows < 0 || stride < max_rows)
+        return LGS_ERR_INVALID_ARG;
+    if (max_rows == 0) return LGS_OK;
+    return adam_step(params, grads, m, v, stride, n_planes, lr, beta1, beta2, eps, step, map,
+                     d_num_visible, max_rows, as_stream(stream));
+}
+
+lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
+                                   const uint32_t *map, const int32_t *d_num_visible,
+                                   const lgs_camera *cam, const float *grad_acc,
+                                   const float *lr, float beta1, float beta2, float eps,
+                                   int32_t step, lgs_stream stream) {
+    if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||
+        !aligned16(grad_acc))
+        return LGS_ERR_INVALID_ARG;
+    if (g->n == 0) return LGS_OK;
+    return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, grad_acc, lr, beta1, beta2, eps,
+                               step, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the CUDA translation units of liblgs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgs.h"
+
+namespace lgs {
+
+constexpr int kWarp = 32;
+
+// Last CUDA error seen by a launch (for lgs_last_cuda_error()).
+void set_cuda_error(cudaError_t e);
+
+// Check the launch just made; map failures to LGS_ERR_CUDA.
+lgs_status check_launch();
+
+// Count one kernel launch of this library (reported by lgs_kernel_launches()).
+void count_launch();
+
+inline cudaStream_t as_stream(lgs_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Grid for a grid-stride loop over `n` items with `threads` per block.
+inline unsigned grid_for(int64_t n, int threads, int per_sm = 8) {
+    int64_t blocks = ceil_div(n > 0 ? n : 1, threads);
+    int64_t cap = (int64_t)num_sms() * per_sm;
+    return (unsigned)(blocks < cap ? blocks : cap);
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int load_count(const int32_t *d_count, int64_t fallback) {
+    return d_count ? *d_count : (int)fallback;
+}
+
+// Order-preserving map of floats to unsigned ints (for atomic min / max).
+__device__ __forceinline__ uint32_t float_to_ordered(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t b) {
+    return __uint_as_float((b & 0x80000000u) ? (b & 0x7fffffffu) : ~b);
+}
+
+// Tile rectangle of a splat: tiles whose pixel square meets
+// [u - r, u + r] x [v - r, v + r], end-exclusive, clamped to the grid.
+// Single precision with explicit rounding so that every caller (and any
+// reference) obtains the same integers.
+__device__ __forceinline__ int4 tile_rect(float u, float v, float r, int tw, int th, int gx,
+                                          int gy) {
+    float x0 = floorf(__fdiv_rn(__fsub_rn(u, r), (float)tw));
+    float x1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(u, r), (float)tw)), 1.0f);
+    float y0 = floorf(__fdiv_rn(__fsub_rn(v, r), (float)th));
+    float y1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(v, r), (float)th)), 1.0f);
+    x0 = fminf(fmaxf(x0, 0.0f), (float)gx);
+    x1 = fminf(fmaxf(x1, 0.0f), (float)gx);
+    y0 = fminf(fmaxf(y0, 0.0f), (float)gy);
+    y1 = fminf(fmaxf(y1, 0.0f), (float)gy);
+    return make_int4((int)x0, (int)y0, (int)x1, (int)y1);
+}
+
+// ---------------------------------------------------------------------------
+// host-side building blocks implemented in sort.cu
+// ---------------------------------------------------------------------------
+
+// Workspace bytes for a stable LSD radix sort of up to n (key, u32 value)
+// pairs with `key_bytes`-byte keys (ping-pong buffers plus histograms).
+size_t radix_sort_workspace(int64_t n, int key_bytes);
+
+// Stable LSD radix sort of (key, value) pairs over the low `bits` bits of
+// the key. The count is *d_n (device; NULL means n_max). The pairs start in
+// (keys[0], vals[0]); keys[1] / vals[1] are the alternate buffers. Returns
+// the index (0 or 1) of the buffers holding the result in *out_buf.
+// `scratch` holds the histograms (radix_hist_bytes()).
+size_t radix_hist_bytes();
+lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
+                          const int32_t *d_n32, int bits, void *scratch, int *out_buf,
+                          cudaStream_t s);
+lgs_status radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
+                          const int32_t *d_n32, int bits, void *scratch, int *out_buf,
+                          cudaStream_t s);
+lgs_status radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
+                          const int32_t *d_n32, int bits, void *scratch, int *out_buf,
+                          cudaStream_t s);
+
+// Number of passes the sort makes for `bits` key bits.
+int radix_passes(int bits);
+
+// Exclusive scan of n_max u32 values (count *d_n32 if given) into 64-bit
+// offsets; *d_total receives the sum. `scratch` of scan_scratch_bytes().
+size_t scan_scratch_bytes();
+lgs_status exclusive_scan_u32_to_u64(const uint32_t *in, uint64_t *out, int64_t n_max,
+                                     const int32_t *d_n32, int64_t *d_total, void *scratch,
+                                     cudaStream_t s);
+
+}  // namespace lgs

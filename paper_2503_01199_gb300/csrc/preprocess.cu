@@ -1,0 +1,526 @@
+// Preprocess (3D Gaussian -> projected splat, Sec. 3) and its backward, plus
+// the fused backward + Adam step on visible rows (Sec. 3.2.3).
+//
+// One thread per compacted Gaussian j; row = map[j]. Parameter planes are
+// read with unit stride across the warp: a visible cluster is a run of
+// consecutive rows, so reads through the map stay coalesced.
+#include <cuda_runtime.h>
+
+#include "lgs_internal.cuh"
+
+namespace lgs {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr float kLowPass = 0.3f;
+constexpr float kClampFov = 1.3f;
+
+// ---------------------------------------------------------------------------
+// real spherical harmonics up to degree 3 as Cartesian polynomials on the
+// unit sphere: Y_l^{+-m} = sqrt2 K_l^m (-1)^m P_l^(m)(z) {Re, Im}(x + i y)^m,
+// K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), P_l^(m) the m-th derivative of
+// the Legendre polynomial. Constants are evaluated at compile time.
+// ---------------------------------------------------------------------------
+constexpr double c_sqrt(double x) {
+    double r = x > 1.0 ? x : 1.0;
+    for (int i = 0; i < 64; ++i) r = 0.5 * (r + x / r);
+    return r;
+}
+constexpr double c_fact(int k) { return k <= 1 ? 1.0 : k * c_fact(k - 1); }
+constexpr double c_pi = 3.14159265358979323846;
+constexpr double shK(int l, int m) {
+    return c_sqrt((2.0 * l + 1.0) / (4.0 * c_pi) * c_fact(l - m) / c_fact(l + m));
+}
+constexpr double c_sqrt2 = c_sqrt(2.0);
+
+constexpr float Y0 = (float)shK(0, 0);
+constexpr float Y1 = (float)shK(1, 0);                   // = sqrt2 K_1^1
+constexpr float Y20 = (float)shK(2, 0);                  // (3z^2 - 1)/2
+constexpr float Y21 = (float)(-3.0 * c_sqrt2 * shK(2, 1));  // z {x, y}
+constexpr float Y22 = (float)(3.0 * c_sqrt2 * shK(2, 2));   // {x^2 - y^2, 2xy}
+constexpr float Y30 = (float)shK(3, 0);                  // (5z^3 - 3z)/2
+constexpr float Y31 = (float)(-0.5 * c_sqrt2 * shK(3, 1));  // (15z^2 - 3) {x, y}
+constexpr float Y32 = (float)(15.0 * c_sqrt2 * shK(3, 2));  // z {x^2 - y^2, 2xy}
+constexpr float Y33 = (float)(-15.0 * c_sqrt2 * shK(3, 3)); // {x^3 - 3xy^2, 3x^2 y - y^3}
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y) {
+    Y[0] = Y0;
+    if (deg < 1) return;
+    Y[1] = -Y1 * y;
+    Y[2] = Y1 * z;
+    Y[3] = -Y1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z, xy = x * y;
+    Y[4] = Y22 * 2.0f * xy;
+    Y[5] = Y21 * z * y;
+    Y[6] = Y20 * 0.5f * (3.0f * zz - 1.0f);
+    Y[7] = Y21 * z * x;
+    Y[8] = Y22 * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = Y33 * (3.0f * xx * y - yy * y);
+    Y[10] = Y32 * z * 2.0f * xy;
+    Y[11] = Y31 * (15.0f * zz - 3.0f) * y;
+    Y[12] = Y30 * 0.5f * (5.0f * zz * z - 3.0f * z);
+    Y[13] = Y31 * (15.0f * zz - 3.0f) * x;
+    Y[14] = Y32 * z * (xx - yy);
+    Y[15] = Y33 * (xx * x - 3.0f * x * yy);
+}
+
+// g += sum_k w_k grad Y_k  (gradient of the polynomial extension)
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, const float *w,
+                                              float &gx, float &gy, float &gz) {
+    if (deg < 1) return;
+    gy += -Y1 * w[1];
+    gz += Y1 * w[2];
+    gx += -Y1 * w[3];
+    if (deg < 2) return;
+    gx += Y22 * 2.0f * y * w[4];
+    gy += Y22 * 2.0f * x * w[4];
+    gy += Y21 * z * w[5];
+    gz += Y21 * y * w[5];
+    gz += Y20 * 3.0f * z * w[6];
+    gx += Y21 * z * w[7];
+    gz += Y21 * x * w[7];
+    gx += Y22 * 2.0f * x * w[8];
+    gy += -Y22 * 2.0f * y * w[8];
+    if (deg < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx += Y33 * 6.0f * x * y * w[9];
+    gy += Y33 * (3.0f * xx - 3.0f * yy) * w[9];
+    gx += Y32 * 2.0f * y * z * w[10];
+    gy += Y32 * 2.0f * x * z * w[10];
+    gz += Y32 * 2.0f * x * y * w[10];
+    gy += Y31 * (15.0f * zz - 3.0f) * w[11];
+    gz += Y31 * 30.0f * y * z * w[11];
+    gz += Y30 * 0.5f * (15.0f * zz - 3.0f) * w[12];
+    gx += Y31 * (15.0f * zz - 3.0f) * w[13];
+    gz += Y31 * 30.0f * x * z * w[13];
+    gx += Y32 * 2.0f * x * z * w[14];
+    gy += -Y32 * 2.0f * y * z * w[14];
+    gz += Y32 * (xx - yy) * w[14];
+    gx += Y33 * (3.0f * xx - 3.0f * yy) * w[15];
+    gy += -Y33 * 6.0f * x * y * w[15];
+}
+
+// Everything the forward computes for one Gaussian, kept for the backward.
+struct Fwd {
+    bool culled;
+    float px, py, pz;        // camera-space centre
+    float s[3];              // scales
+    float qn[4], qinv;       // unit quaternion, 1/|q|
+    float Rq[9];             // rotation of q
+    float Sg[6];             // 3D covariance xx xy xz yy yz zz
+    float tx, ty;            // clamped centre used by J
+    int clx, cly;
+    float Tm[6];             // J R_cam (2 x 3)
+    float a, b, c;           // projected covariance incl. low-pass
+    float det, A, B, C;      // inverse (conic)
+    float u, v;
+    int radius;
+    float dir[3], dinv;      // view direction and 1/|p - centre|
+    float raw[3], rgb[3];
+    float o;
+};
+
+struct Cam {
+    float R[9], t[3], fx, fy, cx, cy, znear, cc[3], limx, limy;
+    int W, H, tw, th, gx, gy;
+};
+
+Cam make_cam(const lgs_camera *c, int tw, int th) {
+    Cam k;
+    for (int i = 0; i < 9; ++i) k.R[i] = c->R[i];
+    for (int i = 0; i < 3; ++i) k.t[i] = c->t[i];
+    k.fx = c->fx; k.fy = c->fy; k.cx = c->cx; k.cy = c->cy; k.znear = c->znear;
+    for (int i = 0; i < 3; ++i)
+        k.cc[i] = -(c->R[i] * c->t[0] + c->R[3 + i] * c->t[1] + c->R[6 + i] * c->t[2]);
+    k.limx = kClampFov * c->width / (2.0f * c->fx);
+    k.limy = kClampFov * c->height / (2.0f * c->fy);
+    k.W = c->width; k.H = c->height; k.tw = tw; k.th = th;
+    k.gx = (int)ceil_div(c->width, tw);
+    k.gy = (int)ceil_div(c->height, th);
+    return k;
+}
+
+__device__ __forceinline__ void forward(const Cam &K, const float *__restrict__ P, int64_t stride,
+                                        int64_t row, int deg, Fwd &f, float *sh_out /* nullable */) {
+    const float mx = P[0 * stride + row], my = P[1 * stride + row], mz = P[2 * stride + row];
+    f.px = K.R[0] * mx + K.R[1] * my + K.R[2] * mz + K.t[0];
+    f.py = K.R[3] * mx + K.R[4] * my + K.R[5] * mz + K.t[1];
+    f.pz = K.R[6] * mx + K.R[7] * my + K.R[8] * mz + K.t[2];
+    f.culled = !(f.pz > K.znear);
+    if (f.culled) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f.s[k] = expf(P[(3 + k) * stride + row]);
+    float q0 = P[6 * stride + row], q1 = P[7 * stride + row], q2 = P[8 * stride + row],
+          q3 = P[9 * stride + row];
+    const float qlen = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    f.qinv = 1.0f / qlen;
+    q0 *= f.qinv; q1 *= f.qinv; q2 *= f.qinv; q3 *= f.qinv;
+    f.qn[0] = q0; f.qn[1] = q1; f.qn[2] = q2; f.qn[3] = q3;
+    float *R = f.Rq;
+    R[0] = 1.f - 2.f * (q2 * q2 + q3 * q3); R[1] = 2.f * (q1 * q2 - q0 * q3); R[2] = 2.f * (q1 * q3 + q0 * q2);
+    R[3] = 2.f * (q1 * q2 + q0 * q3); R[4] = 1.f - 2.f * (q1 * q1 + q3 * q3); R[5] = 2.f * (q2 * q3 - q0 * q1);
+    R[6] = 2.f * (q1 * q3 - q0 * q2); R[7] = 2.f * (q2 * q3 + q0 * q1); R[8] = 1.f - 2.f * (q1 * q1 + q2 * q2);
+    // Sigma = sum_k s_k^2 r_k r_k^T with r_k the columns of Rq
+    const float s0 = f.s[0] * f.s[0], s1 = f.s[1] * f.s[1], s2 = f.s[2] * f.s[2];
+    f.Sg[0] = R[0] * R[0] * s0 + R[1] * R[1] * s1 + R[2] * R[2] * s2;
+    f.Sg[1] = R[0] * R[3] * s0 + R[1] * R[4] * s1 + R[2] * R[5] * s2;
+    f.Sg[2] = R[0] * R[6] * s0 + R[1] * R[7] * s1 + R[2] * R[8] * s2;
+    f.Sg[3] = R[3] * R[3] * s0 + R[4] * R[4] * s1 + R[5] * R[5] * s2;
+    f.Sg[4] = R[3] * R[6] * s0 + R[4] * R[7] * s1 + R[5] * R[8] * s2;
+    f.Sg[5] = R[6] * R[6] * s0 + R[7] * R[7] * s1 + R[8] * R[8] * s2;
+    // EWA Jacobian at the clamped centre
+    const float z = f.pz, iz = 1.0f / z;
+    const float xz = f.px * iz, yz = f.py * iz;
+    f.clx = xz < -K.limx ? -1 : (xz > K.limx ? 1 : 0);
+    f.cly = yz < -K.limy ? -1 : (yz > K.limy ? 1 : 0);
+    f.tx = f.clx ? f.clx * K.limx * z : f.px;
+    f.ty = f.cly ? f.cly * K.limy * z : f.py;
+    const float j00 = K.fx * iz, j02 = -K.fx * f.tx * iz * iz;
+    const float j11 = K.fy * iz, j12 = -K.fy * f.ty * iz * iz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        f.Tm[k] = j00 * K.R[k] + j02 * K.R[6 + k];
+        f.Tm[3 + k] = j11 * K.R[3 + k] + j12 * K.R[6 + k];
+    }
+    // S2 = Tm Sigma Tm^T
+    const float *S = f.Sg;
+    float w0[3], w1[3];  // Sigma Tm^T columns
+    w0[0] = S[0] * f.Tm[0] + S[1] * f.Tm[1] + S[2] * f.Tm[2];
+    w0[1] = S[1] * f.Tm[0] + S[3] * f.Tm[1] + S[4] * f.Tm[2];
+    w0[2] = S[2] * f.Tm[0] + S[4] * f.Tm[1] + S[5] * f.Tm[2];
+    w1[0] = S[0] * f.Tm[3] + S[1] * f.Tm[4] + S[2] * f.Tm[5];
+    w1[1] = S[1] * f.Tm[3] + S[3] * f.Tm[4] + S[4] * f.Tm[5];
+    w1[2] = S[2] * f.Tm[3] + S[4] * f.Tm[4] + S[5] * f.Tm[5];
+    f.a = f.Tm[0] * w0[0] + f.Tm[1] * w0[1] + f.Tm[2] * w0[2] + kLowPass;
+    f.b = f.Tm[3] * w0[0] + f.Tm[4] * w0[1] + f.Tm[5] * w0[2];
+    f.c = f.Tm[3] * w1[0] + f.Tm[4] * w1[1] + f.Tm[5] * w1[2] + kLowPass;
+    f.det = f.a * f.c - f.b * f.b;
+    if (!(f.det > 0.0f)) { f.culled = true; return; }
+    const float idet = 1.0f / f.det;
+    f.A = f.c * idet;
+    f.B = -f.b * idet;
+    f.C = f.a * idet;
+    f.u = K.fx * f.px * iz + K.cx;
+    f.v = K.fy * f.py * iz + K.cy;
+    const float mid = 0.5f * (f.a + f.c);
+    const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - f.det));
+    f.radius = (int)ceilf(3.0f * sqrtf(lam));
+    const int4 rc = tile_rect(f.u, f.v, (float)f.radius, K.tw, K.th, K.gx, K.gy);
+    if (rc.z <= rc.x || rc.w <= rc.y) { f.culled = true; return; }
+    // colour
+    const float dx = mx - K.cc[0], dy = my - K.cc[1], dz = mz - K.cc[2];
+    const float dl = sqrtf(dx * dx + dy * dy + dz * dz);
+    f.dinv = 1.0f / dl;
+    f.dir[0] = dx * f.dinv; f.dir[1] = dy * f.dinv; f.dir[2] = dz * f.dinv;
+    float Y[16];
+    sh_basis(deg, f.dir[0], f.dir[1], f.dir[2], Y);
+    const int K2 = (deg + 1) * (deg + 1);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) f.raw[ch] = 0.5f;
+    for (int k = 0; k < K2; ++k) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float c = P[(11 + 3 * k + ch) * stride + row];
+            if (sh_out) sh_out[3 * k + ch] = c;
+            f.raw[ch] += c * Y[k];
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) f.rgb[ch] = fmaxf(f.raw[ch], 0.0f);
+    f.o = 1.0f / (1.0f + expf(-P[10 * stride + row]));
+}
+
+__global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict__ P, int64_t stride,
+                                                        int64_t n, int deg,
+                                                        const uint32_t *__restrict__ map,
+                                                        const int32_t *d_V, Cam K,
+                                                        float *__restrict__ rec,
+                                                        float *__restrict__ depth,
+                                                        int32_t *__restrict__ radius) {
+    const int64_t V = load_count(d_V, n);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = map ? map[j] : j;
+        Fwd f;
+        forward(K, P, stride, row, deg, f, nullptr);
+        float4 *r4 = reinterpret_cast<float4 *>(rec + 12 * j);
+        if (f.culled) {
+            r4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            r4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            depth[j] = 0.0f;
+            radius[j] = 0;
+            continue;
+        }
+        r4[0] = make_float4(f.u, f.v, f.A, f.B);
+        r4[1] = make_float4(f.C, f.o, f.rgb[0], f.rgb[1]);
+        r4[2] = make_float4(f.rgb[2], 0.f, 0.f, 0.f);
+        depth[j] = f.pz;
+        radius[j] = f.radius;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward: gradient of every parameter plane for one Gaussian. `emit(k, g)`
+// receives plane k's gradient (planes in the order of lgs.h).
+// ---------------------------------------------------------------------------
+template <typename Emit>
+__device__ __forceinline__ void backward(const Cam &K, const float *__restrict__ P, int64_t stride,
+                                         int64_t row, int deg, const float *__restrict__ g16,
+                                         Emit emit) {
+    Fwd f;
+    float sh[48];
+    forward(K, P, stride, row, deg, f, sh);
+    const int K2 = (deg + 1) * (deg + 1);
+    if (f.culled) {
+        for (int k = 0; k < 11 + 3 * K2; ++k) emit(k, 0.0f);
+        return;
+    }
+    const float4 ga = reinterpret_cast<const float4 *>(g16)[0];
+    const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
+    const float4 gc = reinterpret_cast<const float4 *>(g16)[2];
+    const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, go = gb.y;
+    const float grgb[3] = {f.raw[0] > 0.f ? gb.z : 0.f, f.raw[1] > 0.f ? gb.w : 0.f,
+                           f.raw[2] > 0.f ? gc.x : 0.f};
+    // ---- colour: SH coefficients and view direction
+    float Y[16];
+    sh_basis(deg, f.dir[0], f.dir[1], f.dir[2], Y);
+    float wk[16];
+    for (int k = 0; k < K2; ++k) {
+        wk[k] = grgb[0] * sh[3 * k] + grgb[1] * sh[3 * k + 1] + grgb[2] * sh[3 * k + 2];
+    }
+    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+    sh_basis_grad(deg, f.dir[0], f.dir[1], f.dir[2], wk, gdx, gdy, gdz);
+    const float dd = gdx * f.dir[0] + gdy * f.dir[1] + gdz * f.dir[2];
+    float gm[3] = {(gdx - f.dir[0] * dd) * f.dinv, (gdy - f.dir[1] * dd) * f.dinv,
+                   (gdz - f.dir[2] * dd) * f.dinv};
+    // ---- conic -> projected covariance: dS2 = -Q dQ Q, B used twice
+    const float hB = 0.5f * gB;
+    const float t00 = f.A * gA + f.B * hB, t01 = f.A * hB + f.B * gC;
+    const float t10 = f.B * gA + f.C * hB, t11 = f.B * hB + f.C * gC;
+    const float s00 = -(t00 * f.A + t01 * f.B);
+    const float s01 = -(t00 * f.B + t01 * f.C);
+    const float s11 = -(t10 * f.B + t11 * f.C);
+    // ---- S2 = Tm Sigma Tm^T:  dSigma = Tm^T dS2 Tm,  dTm = 2 dS2 Tm Sigma
+    const float *T = f.Tm;
+    float gS[6];  // symmetric xx xy xz yy yz zz; off-diagonals hold d/dSigma_ij (one side)
+    {
+        // M = dS2 Tm (2 x 3)
+        float M0[3], M1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            M0[k] = s00 * T[k] + s01 * T[3 + k];
+            M1[k] = s01 * T[k] + s11 * T[3 + k];
+        }
+        gS[0] = T[0] * M0[0] + T[3] * M1[0];
+        gS[1] = T[0] * M0[1] + T[3] * M1[1];
+        gS[2] = T[0] * M0[2] + T[3] * M1[2];
+        gS[3] = T[1] * M0[1] + T[4] * M1[1];
+        gS[4] = T[1] * M0[2] + T[4] * M1[2];
+        gS[5] = T[2] * M0[2] + T[5] * M1[2];
+    }
+    float gT[6];
+    {
+        const float *S = f.Sg;
+        // Tm Sigma (2 x 3)
+        float U0[3], U1[3];
+        U0[0] = T[0] * S[0] + T[1] * S[1] + T[2] * S[2];
+        U0[1] = T[0] * S[1] + T[1] * S[3] + T[2] * S[4];
+        U0[2] = T[0] * S[2] + T[1] * S[4] + T[2] * S[5];
+        U1[0] = T[3] * S[0] + T[4] * S[1] + T[5] * S[2];
+        U1[1] = T[3] * S[1] + T[4] * S[3] + T[5] * S[4];
+        U1[2] = T[3] * S[2] + T[4] * S[4] + T[5] * S[5];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gT[k] = 2.f * (s00 * U0[k] + s01 * U1[k]);
+            gT[3 + k] = 2.f * (s01 * U0[k] + s11 * U1[k]);
+        }
+    }
+    // ---- Tm = J R_cam:  dJ = dTm R_cam^T (only J00, J02, J11, J12 are free)
+    const float gJ00 = gT[0] * K.R[0] + gT[1] * K.R[1] + gT[2] * K.R[2];
+    const float gJ02 = gT[0] * K.R[6] + gT[1] * K.R[7] + gT[2] * K.R[8];
+    const float gJ11 = gT[3] * K.R[3] + gT[4] * K.R[4] + gT[5] * K.R[5];
+    const float gJ12 = gT[3] * K.R[6] + gT[4] * K.R[7] + gT[5] * K.R[8];
+    const float z = f.pz, iz = 1.f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+    float gpx = 0.f, gpy = 0.f, gpz = 0.f;
+    gpz += -K.fx * iz2 * gJ00 - K.fy * iz2 * gJ11;
+    gpz += 2.f * K.fx * f.tx * iz3 * gJ02 + 2.f * K.fy * f.ty * iz3 * gJ12;
+    const float gtx = -K.fx * iz2 * gJ02, gty = -K.fy * iz2 * gJ12;
+    if (f.clx) gpz += gtx * f.clx * K.limx; else gpx += gtx;
+    if (f.cly) gpz += gty * f.cly * K.limy; else gpy += gty;
+    // ---- u, v
+    gpx += gu * K.fx * iz;
+    gpy += gv * K.fy * iz;
+    gpz += -(gu * K.fx * f.px + gv * K.fy * f.py) * iz2;
+    // ---- camera transform
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gm[k] += K.R[k] * gpx + K.R[3 + k] * gpy + K.R[6 + k] * gpz;
+    emit(0, gm[0]);
+    emit(1, gm[1]);
+    emit(2, gm[2]);
+    // ---- Sigma = sum_k s_k^2 r_k r_k^T: dr_k = 2 s_k^2 G r_k, ds_k = 2 s_k r_k^T G r_k
+    // with G the symmetric gradient [[gS0, gS1/2 ..]] -- off-diagonals of gS
+    // count both (i,j) and (j,i) so they are halved into G.
+    const float G00 = gS[0], G11 = gS[3], G22 = gS[5];
+    const float G01 = gS[1], G02 = gS[2], G12 = gS[4];
+    float gR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float r0 = f.Rq[k], r1 = f.Rq[3 + k], r2 = f.Rq[6 + k];
+        const float Gr0 = G00 * r0 + G01 * r1 + G02 * r2;
+        const float Gr1 = G01 * r0 + G11 * r1 + G12 * r2;
+        const float Gr2 = G02 * r0 + G12 * r1 + G22 * r2;
+        const float s2 = f.s[k] * f.s[k];
+        // d/d(log s_k) = s_k d/ds_k = 2 s_k^2 r^T G r
+        emit(3 + k, 2.f * s2 * (r0 * Gr0 + r1 * Gr1 + r2 * Gr2));
+        gR[k] = 2.f * s2 * Gr0;
+        gR[3 + k] = 2.f * s2 * Gr1;
+        gR[6 + k] = 2.f * s2 * Gr2;
+    }
+    // ---- Rq(q): derivative of each entry w.r.t. (w, x, y, z) of the unit q
+    const float w = f.qn[0], x = f.qn[1], y = f.qn[2], zq = f.qn[3];
+    float gq[4];
+    gq[0] = 2.f * (-zq * gR[1] + y * gR[2] + zq * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gq[1] = 2.f * (y * gR[1] + zq * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + zq * gR[6] +
+                   w * gR[7] - 2.f * x * gR[8]);
+    gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + zq * gR[5] - w * gR[6] +
+                   zq * gR[7] - 2.f * y * gR[8]);
+    gq[3] = 2.f * (-2.f * zq * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * zq * gR[4] +
+                   y * gR[5] + x * gR[6] + y * gR[7]);
+    const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * zq;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) emit(6 + k, (gq[k] - f.qn[k] * dq) * f.qinv);
+    emit(10, go * f.o * (1.f - f.o));
+    for (int k = 0; k < K2; ++k) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) emit(11 + 3 * k + ch, grgb[ch] * Y[k]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__restrict__ P,
+                                                            int64_t stride, int64_t n, int deg,
+                                                            const uint32_t *__restrict__ map,
+                                                            const int32_t *d_V, Cam K,
+                                                            const float *__restrict__ gacc,
+                                                            float *__restrict__ gout) {
+    const int64_t V = load_count(d_V, n);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = map ? map[j] : j;
+        backward(K, P, stride, row, deg, gacc + 16 * j,
+                 [&](int k, float g) { gout[k * stride + row] = g; });
+    }
+}
+
+struct AdamArgs {
+    float lr[64];
+    float b1, b2, eps, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
+};
+
+__device__ __forceinline__ void adam_update(float &p, float &m, float &v, float g, float lr,
+                                            const AdamArgs &a) {
+    m = a.b1 * m + (1.f - a.b1) * g;
+    v = a.b2 * v + (1.f - a.b2) * g * g;
+    p -= lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+}
+
+__global__ void __launch_bounds__(kThreads) k_preprocess_bwd_adam(
+    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
+    int64_t n, int deg, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
+    const float *__restrict__ gacc, AdamArgs a) {
+    const int64_t V = load_count(d_V, n);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = map ? map[j] : j;
+        // gradients first (the forward reads the parameters), then the update
+        float g[59];
+        backward(K, P, stride, row, deg, gacc + 16 * j, [&](int k, float x) { g[k] = x; });
+        const int np = 11 + 3 * (deg + 1) * (deg + 1);
+        for (int k = 0; k < np; ++k) {
+            const int64_t i = k * stride + row;
+            float p = P[i], m = Mo[i], v = Vo[i];
+            adam_update(p, m, v, g[k], a.lr[k], a);
+            P[i] = p;
+            Mo[i] = m;
+            Vo[i] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float *__restrict__ G,
+                                             float *__restrict__ Mo, float *__restrict__ Vo,
+                                             int64_t stride, int n_planes,
+                                             const uint32_t *__restrict__ map, const int32_t *d_V,
+                                             int64_t max_rows, AdamArgs a) {
+    const int64_t V = load_count(d_V, max_rows);
+    const int64_t total = V * n_planes;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t / V);
+        const int64_t j = t - (int64_t)k * V;
+        const int64_t row = map ? map[j] : j;
+        const int64_t i = k * stride + row;
+        float p = P[i], m = Mo[i], v = Vo[i];
+        adam_update(p, m, v, G[i], a.lr[k], a);
+        P[i] = p;
+        Mo[i] = m;
+        Vo[i] = v;
+    }
+}
+
+AdamArgs make_adam(const float *lr, int np, float b1, float b2, float eps, int step) {
+    AdamArgs a;
+    for (int k = 0; k < 64; ++k) a.lr[k] = k < np ? lr[k] : 0.f;
+    a.b1 = b1; a.b2 = b2; a.eps = eps;
+    a.c1 = (float)(1.0 / (1.0 - __builtin_pow((double)b1, step)));
+    a.c2 = (float)(1.0 / (1.0 - __builtin_pow((double)b2, step)));
+    return a;
+}
+
+}  // namespace
+
+lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
+                      const lgs_camera *cam, int tw, int th, const lgs_splats *out,
+                      cudaStream_t s) {
+    const Cam K = make_cam(cam, tw, th);
+    count_launch();
+    k_preprocess<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(
+        g->data, g->stride, g->n, g->sh_degree, map, d_V, K, out->rec, out->depth, out->radius);
+    return check_launch();
+}
+
+lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
+                          const lgs_camera *cam, const float *gacc, float *gout, cudaStream_t s) {
+    const Cam K = make_cam(cam, 16, 16);
+    count_launch();
+    k_preprocess_bwd<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(
+        g->data, g->stride, g->n, g->sh_degree, map, d_V, K, gacc, gout);
+    return check_launch();
+}
+
+lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
+                               const int32_t *d_V, const lgs_camera *cam, const float *gacc,
+                               const float *lr, float b1, float b2, float eps, int step,
+                               cudaStream_t s) {
+    const Cam K = make_cam(cam, 16, 16);
+    const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
+    count_launch();
+    k_preprocess_bwd_adam<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(
+        g->data, m, v, g->stride, g->n, g->sh_degree, map, d_V, K, gacc, a);
+    return check_launch();
+}
+
+lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t stride, int np,
+                     const float *lr, float b1, float b2, float eps, int step, const uint32_t *map,
+                     const int32_t *d_V, int64_t max_rows, cudaStream_t s) {
+    const AdamArgs a = make_adam(lr, np, b1, b2, eps, step);
+    count_launch();
+    k_adam<<<grid_for(max_rows * np, 256, 16), 256, 0, s>>>(p, grad, m, v, stride, np, map, d_V,
+                                                           max_rows, a);
+    return check_launch();
+}
+
+}  // namespace lgs

@@ -1,0 +1,200 @@
+"""One training step of the LiteGS rasterizer hot path on one GPU, as a
+sequence of liblgs calls (Sec. 3 pipeline):
+
+  a1 Morton re-sort of parameters and Adam moments        lgs_morton_reorder
+  a2 cluster AABB frustum cull + compaction map           lgs_cluster_cull_compact
+  a3 preprocess (EWA projection, SH colour, opacity)      lgs_preprocess
+  a4 tile binning + depth/tile sort                       lgs_bin_sort
+  a5 forward rasterisation                                lgs_raster_fwd
+  a6 L1 loss gradient                                     lgs_loss_l1
+  a7 backward rasterisation + opacity-gradient moments    lgs_raster_bwd
+  a8 densification metric C Var = S - M^2/C               lgs_opacity_variance
+  a9 preprocess backward + a10 sparse Adam                lgs_preprocess_bwd_adam
+                                                          (or lgs_preprocess_bwd + lgs_adam_step)
+
+torch provides the device buffers and the stream; every step runs in the
+library's kernels. All calls are asynchronous and no count is read back, so
+a step can be captured in a CUDA graph.
+
+Parameters and the two Adam moments live in one buffer of planes
+[3][P][stride] (params, m, v) so that the Morton re-sort permutes all of
+them in one gather; a second buffer of the same shape receives it.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+# Learning rates per parameter group: the common 3DGS set (the paper only
+# says "same learning rates as TamingGS", Sec. 4, without printing them).
+DEFAULT_LR = {"mean": 1.6e-4, "log_scale": 5e-3, "quat": 1e-3, "logit": 5e-2,
+              "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20.0}
+
+
+def lr_per_plane(sh_degree: int, lr: dict | None = None) -> list[float]:
+    lr = dict(DEFAULT_LR, **(lr or {}))
+    k = (sh_degree + 1) ** 2
+    return ([lr["mean"]] * 3 + [lr["log_scale"]] * 3 + [lr["quat"]] * 4 + [lr["logit"]] +
+            [lr["sh_dc"]] * 3 + [lr["sh_rest"]] * 3 * (k - 1))
+
+
+def pack_planes(scene: dict) -> np.ndarray:
+    """Scene dict (scenegen layout) -> float32 planes [P, N] in lgs.h order."""
+    n = scene["mean"].shape[0]
+    return np.ascontiguousarray(np.concatenate([
+        np.asarray(scene["mean"], np.float32).T, np.asarray(scene["log_scale"], np.float32).T,
+        np.asarray(scene["quat"], np.float32).T, np.asarray(scene["logit"], np.float32)[None],
+        np.asarray(scene["sh"], np.float32).reshape(n, -1).T]))
+
+
+def unpack_planes(planes: np.ndarray, sh_degree: int) -> dict:
+    n = planes.shape[1]
+    return {"mean": planes[0:3].T.copy(), "log_scale": planes[3:6].T.copy(),
+            "quat": planes[6:10].T.copy(), "logit": planes[10].copy(),
+            "sh": planes[11:].T.reshape(n, -1, 3).copy(), "sh_degree": sh_degree}
+
+
+def round_up(x: int, m: int) -> int:
+    return (x + m - 1) // m * m
+
+
+@dataclass
+class StepConfig:
+    tile: tuple = (16, 16)
+    cluster: int = 128
+    pair_capacity: int | None = None   # default: 64 pairs per Gaussian, at least 1M
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+    lr: dict = field(default_factory=dict)
+
+
+class Trainer:
+    """Device-resident scene + all step buffers for one camera size."""
+
+    def __init__(self, scene: dict, width: int, height: int, cfg: StepConfig | None = None,
+                 device: str = "cuda"):
+        self.cfg = cfg or StepConfig()
+        self.dev = torch.device(device)
+        self.sh_degree = int(scene["sh_degree"])
+        self.n = int(scene["mean"].shape[0])
+        self.np_ = B.num_planes(self.sh_degree)
+        self.stride = round_up(max(self.n, 1), 128)
+        self.W, self.H = int(width), int(height)
+        tw, th = self.cfg.tile
+        self.gx, self.gy = -(-self.W // tw), -(-self.H // th)
+        self.ntiles = self.gx * self.gy
+        n, dev = self.n, self.dev
+        # [buffer][params, m, v][plane][row]
+        self.state = torch.zeros((2, 3, self.np_, self.stride), dtype=torch.float32, device=dev)
+        self.cur = 0
+        planes = torch.from_numpy(pack_planes(scene))
+        self.state[0, 0, :, :n].copy_(planes.to(dev))
+        self.codes = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.perm = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.ws_morton = torch.empty(B.lgs_morton_workspace_size(n), dtype=torch.uint8, device=dev)
+        ncl = -(-n // self.cfg.cluster)
+        self.ws_ccc = torch.empty(B.lgs_ccc_workspace_size(n, self.cfg.cluster), dtype=torch.uint8,
+                                  device=dev)
+        self.cluster_visible = torch.zeros(ncl, dtype=torch.int32, device=dev)
+        self.rowmap = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.d_V = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.rec = torch.zeros((n, B.SPLAT_FLOATS), dtype=torch.float32, device=dev)
+        self.depth = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.radius = torch.zeros(n, dtype=torch.int32, device=dev)
+        cap = self.cfg.pair_capacity or max(64 * n, 1 << 20)
+        self.cap = int(cap)
+        self.vals = torch.zeros(self.cap, dtype=torch.int32, device=dev)
+        self.d_P = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.ranges = torch.zeros((self.ntiles, 2), dtype=torch.int32, device=dev)
+        self.ws_bin = torch.empty(B.lgs_bin_sort_workspace_size(n, self.cap, self.ntiles),
+                                  dtype=torch.uint8, device=dev)
+        self.image = torch.zeros((3, self.H, self.W), dtype=torch.float32, device=dev)
+        self.finalT = torch.zeros((self.H, self.W), dtype=torch.float32, device=dev)
+        self.last = torch.zeros((self.H, self.W), dtype=torch.int32, device=dev)
+        self.dLdI = torch.zeros_like(self.image)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.gacc = torch.zeros((n, B.GRAD_FLOATS), dtype=torch.float32, device=dev)
+        self.metric = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.grad_planes = None
+        self.lr = lr_per_plane(self.sh_degree, self.cfg.lr)
+        self.step_count = 0
+        self.splats = B.splats_struct(self.rec, self.depth, self.radius)
+
+    # -- views ------------------------------------------------------------
+    @property
+    def params(self) -> torch.Tensor:
+        return self.state[self.cur, 0]
+
+    @property
+    def m(self) -> torch.Tensor:
+        return self.state[self.cur, 1]
+
+    @property
+    def v(self) -> torch.Tensor:
+        return self.state[self.cur, 2]
+
+    def gaussians(self) -> B.LgsGaussians:
+        return B.gaussians_struct(self.params, self.n, self.sh_degree)
+
+    # -- steps ------------------------------------------------------------
+    def morton_reorder(self):
+        """a1: permute params, m and v (3 x P planes) into Morton order."""
+        src = self.state[self.cur].view(3 * self.np_, self.stride)
+        dst = self.state[self.cur ^ 1].view(3 * self.np_, self.stride)
+        B.lgs_morton_reorder(src, dst, self.n, 3 * self.np_, self.codes, self.perm, self.ws_morton)
+        self.cur ^= 1
+
+    def render(self, cam: dict, camst: B.LgsCamera | None = None):
+        """a2..a5 for one camera: cull, preprocess, bin, forward."""
+        cs = camst or B.camera_struct(cam)
+        tw, th = self.cfg.tile
+        g = self.gaussians()
+        B.lgs_cluster_cull_compact(g, cs, self.cfg.cluster, None, self.cluster_visible,
+                                   self.rowmap, self.d_V, self.ws_ccc)
+        B.lgs_preprocess(g, self.rowmap, self.d_V, cs, tw, th, self.splats)
+        B.lgs_bin_sort(self.splats, self.d_V, self.n, cs, tw, th, self.vals, self.d_P,
+                       self.ranges, self.ws_bin)
+        B.lgs_raster_fwd(self.splats, self.vals, self.ranges, cs, tw, th, self.image, self.finalT,
+                         self.last)
+        return cs
+
+    def backward(self, cs: B.LgsCamera, target: torch.Tensor, accumulate=False):
+        """a6..a8: loss gradient, backward rasterisation, variance metric."""
+        tw, th = self.cfg.tile
+        B.lgs_loss_l1(self.image, target, self.dLdI, self.loss)
+        B.lgs_raster_bwd(self.splats, self.vals, self.ranges, cs, tw, th, self.finalT, self.last,
+                         self.dLdI, self.gacc, accumulate=accumulate)
+        B.lgs_opacity_variance(self.gacc, self.rowmap, self.d_V, self.n, self.metric)
+
+    def optimize(self, cs: B.LgsCamera, fused=True):
+        """a9 + a10: preprocess backward and Adam on the visible rows."""
+        self.step_count += 1
+        c = self.cfg
+        g = self.gaussians()
+        if fused:
+            B.lgs_preprocess_bwd_adam(g, self.m, self.v, self.rowmap, self.d_V, cs, self.gacc,
+                                      self.lr, c.beta1, c.beta2, c.eps, self.step_count)
+        else:
+            if self.grad_planes is None:
+                self.grad_planes = torch.zeros((self.np_, self.stride), dtype=torch.float32,
+                                               device=self.dev)
+            B.lgs_preprocess_bwd(g, self.rowmap, self.d_V, cs, self.gacc, self.grad_planes)
+            B.lgs_adam_step(self.params, self.grad_planes, self.m, self.v, self.np_, self.lr,
+                            c.beta1, c.beta2, c.eps, self.step_count, self.rowmap, self.d_V,
+                            self.n)
+
+    def step(self, cam: dict | B.LgsCamera, target: torch.Tensor, reorder: bool = True,
+             fused: bool = True):
+        """One full training step a1..a10."""
+        if reorder:
+            self.morton_reorder()
+        cs = cam if isinstance(cam, B.LgsCamera) else B.camera_struct(cam)
+        self.render(None, cs)
+        self.backward(cs, target)
+        self.optimize(cs, fused=fused)
+        return self.loss

@@ -1,0 +1,205 @@
+"""GPU parity of the whole training step (a1..a10) and of the Adam kernels.
+
+The oracle runs the same step in double precision: Morton re-sort, cluster
+cull, preprocess of the visible rows, binning, forward, L1 loss, backward,
+preprocess backward, variance metric and sparse Adam on the visible rows.
+Integer results (permutation, compaction map, V) must match exactly; the
+image 1e-5 max-abs on pixels no flagged decision touches; gradients,
+moments and the variance metric 1e-3 relative L2. At step 1 Adam moves a
+parameter by +-lr (the sign of its gradient), so parameters are compared
+only where the oracle gradient is clear of rounding.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_01199_gb300 import binding as B
+from paper_2503_01199_gb300 import pipeline as PL
+from paper_2503_01199_gb300 import scenegen
+
+import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    U.need_gpu()
+
+
+def oracle_step(orc, scene, cam, target, tile=(16, 16), step=1, lr=None):
+    codes, perm = orc.morton_reorder(scene)
+    sc = {k: (np.asarray(v, np.float64)[perm] if k != "sh_degree" else v) for k, v in scene.items()}
+    cc = orc.cluster_cull(sc, cam, 128)
+    rows = cc["map"]
+    sub = {k: (v[rows] if k != "sh_degree" else v) for k, v in sc.items()}
+    r = orc.render_scene(sub, cam, tile)
+    L, dL = orc.l1_loss(r["image"], target)
+    bw = orc.render_bwd(r["splats"], r["vals"], r["ranges"], cam, dL, tile)
+    g = orc.grad_planes(orc.preprocess_bwd(sub, cam, bw["grad9"]))
+    n = scene["mean"].shape[0]
+    planes = orc.scene_planes(sc)
+    grads = np.zeros_like(planes)
+    grads[:, rows] = g
+    m, v = np.zeros_like(planes), np.zeros_like(planes)
+    newp = planes.copy()
+    # the kernel receives beta1, beta2 and the rates as float32: use the same values
+    orc.adam(newp, grads, m, v, np.asarray(lr, np.float32).astype(np.float64), step, rows,
+             beta1=float(np.float32(0.9)), beta2=float(np.float32(0.999)),
+             eps=float(np.float32(1e-15)))
+    metric = np.zeros(n)
+    metric[rows] = orc.opacity_variance(bw["S"], bw["M"], bw["C"])
+    # pixels a Gaussian can reach (alpha >= 1/255) in the tiles it may or may
+    # not be listed in, when its radius or tile rectangle is within rounding
+    bad = np.zeros((cam["height"], cam["width"]), bool)
+    tw, th = tile
+    gx, gy = -(-cam["width"] // tw), -(-cam["height"] // th)
+    sp = r["splats"]
+    px, py = np.meshgrid(np.arange(cam["width"]) + 0.5, np.arange(cam["height"]) + 0.5)
+    for i in np.flatnonzero(sp["flags"] & 5):
+        radii = (sp["radius"][i] - 1, sp["radius"][i], sp["radius"][i] + 1) if sp["flags"][i] & 1 \
+            else (sp["radius"][i],)
+        eps = (-2e-3, 2e-3) if sp["flags"][i] & 4 else (0.0,)
+        cands = []
+        for rad in radii:
+            for du in eps:
+                for dv in eps:
+                    u, v = sp["uv"][i, 0] + du, sp["uv"][i, 1] + dv
+                    x0, x1 = np.floor((u - rad) / tw), np.floor((u + rad) / tw) + 1
+                    y0, y1 = np.floor((v - rad) / th), np.floor((v + rad) / th) + 1
+                    cands.append([int(np.clip(a, 0, g)) for a, g in ((x0, gx), (y0, gy), (x1, gx), (y1, gy))])
+        m_all = np.zeros((gy, gx), int)
+        for x0, y0, x1, y1 in cands:
+            m_all[y0:y1, x0:x1] += 1
+        amb = (m_all > 0) & (m_all < len(cands))
+        amb_px = np.kron(amb, np.ones((th, tw), bool))[:cam["height"], :cam["width"]]
+        dx, dy = sp["uv"][i, 0] - px, sp["uv"][i, 1] - py
+        A, Bq, C = sp["conic"][i]
+        reach = sp["opacity"][i] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - Bq * dx * dy) >= 0.999 / 255
+        bad |= amb_px & reach
+    bad |= r["pixflags"] != 0
+    return {"perm": perm, "map": rows, "V": cc["V"], "image": r["image"], "loss": L, "grads": grads,
+            "params": newp, "m": m, "v": v, "metric": metric, "bad": bad, "planes0": planes,
+            "sflags": bw["sflags"], "last": r["last"]}
+
+
+def _run_gpu_step(scene, cam, target, fused, tile=(16, 16)):
+    tr = PL.Trainer(scene, cam["width"], cam["height"], PL.StepConfig(tile=tile))
+    tgt = U.t(target)
+    tr.step(cam, tgt, reorder=True, fused=fused)
+    torch.cuda.synchronize()
+    n = tr.n
+    out = {"perm": tr.perm.cpu().numpy().view(np.uint32), "V": int(tr.d_V.item()),
+           "map": tr.rowmap.cpu().numpy().view(np.uint32)[: int(tr.d_V.item())],
+           "image": tr.image.cpu().numpy(), "loss": float(tr.loss.item()),
+           "params": tr.params.cpu().numpy()[:, :n].astype(np.float64),
+           "m": tr.m.cpu().numpy()[:, :n], "v": tr.v.cpu().numpy()[:, :n],
+           "metric": tr.metric.cpu().numpy(), "last": tr.last.cpu().numpy(), "lr": tr.lr}
+    if not fused:
+        out["grads"] = tr.grad_planes.cpu().numpy()[:, :n]
+    return out
+
+
+@pytest.mark.parametrize("deg", [0, 3])
+def test_full_step_config1(orc, deg):
+    # 4,096 Gaussians, 128 x 128, fx = fy = 128, seed 0, L1 against a uniform target
+    d = scenegen.uniform_box_scene(4096, deg, 0, 128, 128)
+    sc, cam, tgt = d["scene"], d["camera"], d["target"]
+    g = _run_gpu_step(sc, cam, tgt, fused=False)
+    o = oracle_step(orc, sc, cam, tgt, lr=g["lr"])
+    np.testing.assert_array_equal(g["perm"], o["perm"])
+    assert g["V"] == o["V"]
+    np.testing.assert_array_equal(g["map"], o["map"])
+    ok = ~o["bad"]
+    assert ok.mean() > 0.99
+    err = np.abs(g["image"] - o["image"])[:, ok].max()
+    assert err <= 1e-5, err
+    np.testing.assert_array_equal(g["last"][ok], o["last"][ok])
+    assert abs(g["loss"] - o["loss"]) <= 1e-6 * o["loss"] + 1e-7
+    rows = o["map"]
+    for name, sl in (("mean", slice(0, 3)), ("log_scale", slice(3, 6)), ("quat", slice(6, 10)),
+                     ("logit", slice(10, 11)), ("sh", slice(11, None))):
+        e = U.rel_l2(g["grads"][sl][:, rows], o["grads"][sl][:, rows])
+        assert e < 1e-3, (name, e)
+        e = U.rel_l2(g["m"][sl][:, rows], o["m"][sl][:, rows])
+        assert e < 1e-3, (name, "m", e)
+    assert U.rel_l2(g["metric"][rows], o["metric"][rows]) < 1e-3
+    # parameters: rows outside visible clusters are untouched; visible rows
+    # moved by -lr sign(g) where the gradient sign is unambiguous
+    og = o["grads"]
+    clear = np.abs(og) > 1e-3 * np.sqrt(np.mean(og[:, rows] ** 2, axis=1, keepdims=True))
+    clear[:, np.setdiff1d(np.arange(og.shape[1]), rows)] = False
+    np.testing.assert_allclose(g["params"][clear], o["params"][clear], rtol=1e-6, atol=1e-7)
+    hidden = np.setdiff1d(np.arange(og.shape[1]), rows)
+    np.testing.assert_array_equal(g["params"][:, hidden], o["planes0"][:, hidden].astype(np.float32))
+
+
+def test_fused_backward_adam_equals_separate(orc):
+    d = scenegen.uniform_box_scene(4096, 3, 2, 128, 128)
+    sc, cam, tgt = d["scene"], d["camera"], d["target"]
+    a = _run_gpu_step(sc, cam, tgt, fused=False)
+    b = _run_gpu_step(sc, cam, tgt, fused=True)
+    np.testing.assert_array_equal(a["perm"], b["perm"])
+    np.testing.assert_allclose(b["m"], a["m"], rtol=1e-4, atol=1e-12)
+    np.testing.assert_allclose(b["v"], a["v"], rtol=1e-4, atol=1e-20)
+    assert np.mean(np.abs(b["params"] - a["params"]) > 1e-6) < 1e-3
+
+
+def test_adam_kernel_matches_oracle(orc):
+    rng = np.random.default_rng(7)
+    nplanes, n = 14, 1000
+    stride = 1024
+    p = np.zeros((nplanes, stride), np.float32)
+    p[:, :n] = rng.standard_normal((nplanes, n))
+    gr = np.zeros_like(p)
+    gr[:, :n] = rng.standard_normal((nplanes, n)) * 1e-2
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    m[:, :n] = rng.standard_normal((nplanes, n)) * 1e-3
+    v[:, :n] = rng.uniform(0, 1e-4, (nplanes, n))
+    rows = np.concatenate([np.arange(0, 128), np.arange(384, 1000)]).astype(np.uint32)
+    lr = np.linspace(1e-4, 1e-2, nplanes).astype(np.float32)
+    tp, tg, tm, tv = U.t(p), U.t(gr), U.t(m), U.t(v)
+    trow = U.t(rows.view(np.int32))
+    dV = U.t(np.array([rows.size], np.int32))
+    B.lgs_adam_step(tp, tg, tm, tv, nplanes, lr, 0.9, 0.999, 1e-15, 5, trow, dV, n)
+    torch.cuda.synchronize()
+    P64c = np.ascontiguousarray(p[:, :n], np.float64)
+    M64c = np.ascontiguousarray(m[:, :n], np.float64)
+    V64c = np.ascontiguousarray(v[:, :n], np.float64)
+    # the kernel receives beta1, beta2 and eps as float32: use the same values
+    orc.adam(P64c, gr[:, :n].astype(np.float64), M64c, V64c, lr.astype(np.float64), 5, rows,
+             beta1=float(np.float32(0.9)), beta2=float(np.float32(0.999)),
+             eps=float(np.float32(1e-15)))
+    np.testing.assert_allclose(tp.cpu().numpy()[:, :n], P64c, rtol=1e-6, atol=1e-7)
+    # m and v are sums of two terms that can cancel; float32 rounds beta1,
+    # beta2 and the terms, so the error is relative to the terms
+    tm_scale = 0.9 * np.abs(m[:, :n]) + 0.1 * np.abs(gr[:, :n])
+    tv_scale = 0.999 * v[:, :n] + 0.001 * gr[:, :n] ** 2
+    assert (np.abs(tm.cpu().numpy()[:, :n] - M64c) <= 1e-6 * tm_scale + 1e-30).all()
+    assert (np.abs(tv.cpu().numpy()[:, :n] - V64c) <= 1e-6 * tv_scale + 1e-30).all()
+    hidden = np.arange(128, 384)
+    assert tp.cpu().numpy()[:, hidden].tobytes() == p[:, hidden].tobytes()
+    assert tm.cpu().numpy()[:, hidden].tobytes() == m[:, hidden].tobytes()
+    assert tv.cpu().numpy()[:, hidden].tobytes() == v[:, hidden].tobytes()
+
+
+def test_cull_does_not_change_the_image(orc):
+    # the same render with the compaction map and with every row visible
+    d = scenegen.uniform_box_scene(20000, 1, 8, 256, 192, focal=256.0)
+    d["scene"]["mean"][:8000, 0] += 4.0
+    tr = PL.Trainer(d["scene"], 256, 192)
+    tr.morton_reorder()
+    cs = B.camera_struct(d["camera"])
+    tr.render(None, cs)
+    torch.cuda.synchronize()
+    img_cull = tr.image.cpu().numpy().copy()
+    V = int(tr.d_V.item())
+    assert V < tr.n
+    # render every row (identity map, V = n)
+    g = tr.gaussians()
+    B.lgs_preprocess(g, None, None, cs, 16, 16, tr.splats)
+    B.lgs_bin_sort(tr.splats, None, tr.n, cs, 16, 16, tr.vals, tr.d_P, tr.ranges, tr.ws_bin)
+    B.lgs_raster_fwd(tr.splats, tr.vals, tr.ranges, cs, 16, 16, tr.image, tr.finalT, tr.last)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(tr.image.cpu().numpy(), img_cull)
