@@ -237,7 +237,8 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
  * grad_acc (device) [max_splats][16] floats, row j:
  *   0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 do (activated opacity), 6..8 dr dg db,
  *   9 S = sum of (dL/do per pixel)^2, 10 M = sum of dL/do per pixel,
- *   11 C = count of included fragments as uint32, 12..15 zero.
+ *   11 C = count of included fragments as uint32, 12..15 zero (scratch of
+ *   lgs_preprocess_bwd_adam).
  * accumulate = 0 zeroes rows j < max_splats first; 1 adds to them.
  * ---------------------------------------------------------------------- */
 lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
@@ -277,13 +278,15 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
                          int32_t step, const uint32_t *map, const int32_t *d_num_visible,
                          int64_t max_rows, lgs_stream stream);
 
-/* a9 + a10 in one pass: the gradient of each parameter is computed and
- * applied at once, without a gradient buffer. m and v are planes with the
- * stride of g; g->data is updated in place. Same results as lgs_preprocess_bwd
- * followed by lgs_adam_step up to rounding. */
+/* a9 + a10 without a gradient buffer: each parameter's gradient is applied
+ * by Adam as soon as it is computed. m and v are planes with the stride of g;
+ * g->data is updated in place. Same results as lgs_preprocess_bwd followed by
+ * lgs_adam_step up to rounding. Slots 12..15 of each grad_acc row are used as
+ * scratch (the centre's gradient and a culled flag pass between the two
+ * kernels of this call); slots 0..11 are not modified. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
-                                   const lgs_camera *cam, const float *grad_acc,
+                                   const lgs_camera *cam, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream);
 

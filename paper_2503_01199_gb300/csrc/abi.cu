@@ -25,7 +25,7 @@ lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t
 lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
                           const lgs_camera *cam, const float *gacc, float *gout, cudaStream_t s);
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
-                               const int32_t *d_V, const lgs_camera *cam, const float *gacc,
+                               const int32_t *d_V, const lgs_camera *cam, float *gacc,
                                const float *lr, float b1, float b2, float eps, int step,
                                cudaStream_t s);
 lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t stride, int np,
@@ -245,7 +245,7 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
 
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
-                                   const lgs_camera *cam, const float *grad_acc,
+                                   const lgs_camera *cam, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream) {
     if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||

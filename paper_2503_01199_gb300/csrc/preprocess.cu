@@ -119,8 +119,7 @@ struct Fwd {
     float u, v;
     int radius;
     float dir[3], dinv;      // view direction and 1/|p - centre|
-    float raw[3], rgb[3];
-    float o;
+    float logit;
 };
 
 struct Cam {
@@ -143,18 +142,22 @@ Cam make_cam(const lgs_camera *c, int tw, int th) {
     return k;
 }
 
-__device__ __forceinline__ void forward(const Cam &K, const float *__restrict__ P, int64_t stride,
-                                        int64_t row, int deg, Fwd &f, float *sh_out /* nullable */) {
+// Geometry of one Gaussian (planes 0..10): camera-space centre, 3D and 2D
+// covariance, conic, screen centre, radius and tile-rectangle cull, view
+// direction. Returns false when the Gaussian is culled.
+__device__ __forceinline__ bool geom_forward(const Cam &K, const float *__restrict__ P,
+                                             int64_t stride, int64_t row, Fwd &f) {
     const float mx = P[0 * stride + row], my = P[1 * stride + row], mz = P[2 * stride + row];
     f.px = K.R[0] * mx + K.R[1] * my + K.R[2] * mz + K.t[0];
     f.py = K.R[3] * mx + K.R[4] * my + K.R[5] * mz + K.t[1];
     f.pz = K.R[6] * mx + K.R[7] * my + K.R[8] * mz + K.t[2];
     f.culled = !(f.pz > K.znear);
-    if (f.culled) return;
+    if (f.culled) return false;
 #pragma unroll
     for (int k = 0; k < 3; ++k) f.s[k] = expf(P[(3 + k) * stride + row]);
     float q0 = P[6 * stride + row], q1 = P[7 * stride + row], q2 = P[8 * stride + row],
           q3 = P[9 * stride + row];
+    f.logit = P[10 * stride + row];
     const float qlen = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
     f.qinv = 1.0f / qlen;
     q0 *= f.qinv; q1 *= f.qinv; q2 *= f.qinv; q3 *= f.qinv;
@@ -198,7 +201,7 @@ __device__ __forceinline__ void forward(const Cam &K, const float *__restrict__ 
     f.b = f.Tm[3] * w0[0] + f.Tm[4] * w0[1] + f.Tm[5] * w0[2];
     f.c = f.Tm[3] * w1[0] + f.Tm[4] * w1[1] + f.Tm[5] * w1[2] + kLowPass;
     f.det = f.a * f.c - f.b * f.b;
-    if (!(f.det > 0.0f)) { f.culled = true; return; }
+    if (!(f.det > 0.0f)) { f.culled = true; return false; }
     const float idet = 1.0f / f.det;
     f.A = f.c * idet;
     f.B = -f.b * idet;
@@ -209,33 +212,29 @@ __device__ __forceinline__ void forward(const Cam &K, const float *__restrict__ 
     const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - f.det));
     f.radius = (int)ceilf(3.0f * sqrtf(lam));
     const int4 rc = tile_rect(f.u, f.v, (float)f.radius, K.tw, K.th, K.gx, K.gy);
-    if (rc.z <= rc.x || rc.w <= rc.y) { f.culled = true; return; }
-    // colour
+    if (rc.z <= rc.x || rc.w <= rc.y) { f.culled = true; return false; }
     const float dx = mx - K.cc[0], dy = my - K.cc[1], dz = mz - K.cc[2];
     const float dl = sqrtf(dx * dx + dy * dy + dz * dz);
     f.dinv = 1.0f / dl;
     f.dir[0] = dx * f.dinv; f.dir[1] = dy * f.dinv; f.dir[2] = dz * f.dinv;
-    float Y[16];
-    sh_basis(deg, f.dir[0], f.dir[1], f.dir[2], Y);
-    const int K2 = (deg + 1) * (deg + 1);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) f.raw[ch] = 0.5f;
-    for (int k = 0; k < K2; ++k) {
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            const float c = P[(11 + 3 * k + ch) * stride + row];
-            if (sh_out) sh_out[3 * k + ch] = c;
-            f.raw[ch] += c * Y[k];
-        }
-    }
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) f.rgb[ch] = fmaxf(f.raw[ch], 0.0f);
-    f.o = 1.0f / (1.0f + expf(-P[10 * stride + row]));
+    return true;
 }
 
+// raw colour (before the clamp at 0): 0.5 + sum_k c_k Y_k
+template <int DEG>
+__device__ __forceinline__ void color_forward(const float *__restrict__ P, int64_t stride,
+                                              int64_t row, const float *Y, float *raw) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
+    raw[0] = raw[1] = raw[2] = 0.5f;
+#pragma unroll
+    for (int k = 0; k < KK; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) raw[ch] += P[(11 + 3 * k + ch) * stride + row] * Y[k];
+}
+
+template <int DEG>
 __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict__ P, int64_t stride,
-                                                        int64_t n, int deg,
-                                                        const uint32_t *__restrict__ map,
+                                                        int64_t n, const uint32_t *__restrict__ map,
                                                         const int32_t *d_V, Cam K,
                                                         float *__restrict__ rec,
                                                         float *__restrict__ depth,
@@ -245,9 +244,8 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = map ? map[j] : j;
         Fwd f;
-        forward(K, P, stride, row, deg, f, nullptr);
         float4 *r4 = reinterpret_cast<float4 *>(rec + 12 * j);
-        if (f.culled) {
+        if (!geom_forward(K, P, stride, row, f)) {
             r4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             r4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -255,48 +253,42 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
             radius[j] = 0;
             continue;
         }
+        float Y[16], raw[3];
+        sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], Y);
+        color_forward<DEG>(P, stride, row, Y, raw);
+        const float o = 1.0f / (1.0f + expf(-f.logit));
         r4[0] = make_float4(f.u, f.v, f.A, f.B);
-        r4[1] = make_float4(f.C, f.o, f.rgb[0], f.rgb[1]);
-        r4[2] = make_float4(f.rgb[2], 0.f, 0.f, 0.f);
+        r4[1] = make_float4(f.C, o, fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f));
+        r4[2] = make_float4(fmaxf(raw[2], 0.f), 0.f, 0.f, 0.f);
         depth[j] = f.pz;
         radius[j] = f.radius;
     }
 }
 
 // ---------------------------------------------------------------------------
-// backward: gradient of every parameter plane for one Gaussian. `emit(k, g)`
-// receives plane k's gradient (planes in the order of lgs.h).
+// backward: the gradient of every parameter plane of one Gaussian, handed to
+// `sink(k, g)` as soon as it is known (planes in the order of lgs.h). The
+// colour part streams over the SH planes; nothing is kept in local arrays.
 // ---------------------------------------------------------------------------
-template <typename Emit>
-__device__ __forceinline__ void backward(const Cam &K, const float *__restrict__ P, int64_t stride,
-                                         int64_t row, int deg, const float *__restrict__ g16,
-                                         Emit emit) {
+template <int DEG, typename Sink>
+__device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__ P, int64_t stride,
+                                         int64_t row, const float *__restrict__ g16, Sink &sink) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
     Fwd f;
-    float sh[48];
-    forward(K, P, stride, row, deg, f, sh);
-    const int K2 = (deg + 1) * (deg + 1);
-    if (f.culled) {
-        for (int k = 0; k < 11 + 3 * K2; ++k) emit(k, 0.0f);
-        return;
+    if (!geom_forward(K, P, stride, row, f)) {
+#pragma unroll
+        for (int k = 0; k < 11 + 3 * KK; ++k) sink(k, 0.0f);
+        return false;
     }
     const float4 ga = reinterpret_cast<const float4 *>(g16)[0];
     const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
     const float4 gc = reinterpret_cast<const float4 *>(g16)[2];
     const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, go = gb.y;
-    const float grgb[3] = {f.raw[0] > 0.f ? gb.z : 0.f, f.raw[1] > 0.f ? gb.w : 0.f,
-                           f.raw[2] > 0.f ? gc.x : 0.f};
-    // ---- colour: SH coefficients and view direction
-    float Y[16];
-    sh_basis(deg, f.dir[0], f.dir[1], f.dir[2], Y);
-    float wk[16];
-    for (int k = 0; k < K2; ++k) {
-        wk[k] = grgb[0] * sh[3 * k] + grgb[1] * sh[3 * k + 1] + grgb[2] * sh[3 * k + 2];
+    // ---- opacity: o = sigmoid(logit)
+    {
+        const float o = 1.0f / (1.0f + expf(-f.logit));
+        sink(10, go * o * (1.f - o));
     }
-    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
-    sh_basis_grad(deg, f.dir[0], f.dir[1], f.dir[2], wk, gdx, gdy, gdz);
-    const float dd = gdx * f.dir[0] + gdy * f.dir[1] + gdz * f.dir[2];
-    float gm[3] = {(gdx - f.dir[0] * dd) * f.dinv, (gdy - f.dir[1] * dd) * f.dinv,
-                   (gdz - f.dir[2] * dd) * f.dinv};
     // ---- conic -> projected covariance: dS2 = -Q dQ Q, B used twice
     const float hB = 0.5f * gB;
     const float t00 = f.A * gA + f.B * hB, t01 = f.A * hB + f.B * gC;
@@ -306,9 +298,8 @@ __device__ __forceinline__ void backward(const Cam &K, const float *__restrict__
     const float s11 = -(t10 * f.B + t11 * f.C);
     // ---- S2 = Tm Sigma Tm^T:  dSigma = Tm^T dS2 Tm,  dTm = 2 dS2 Tm Sigma
     const float *T = f.Tm;
-    float gS[6];  // symmetric xx xy xz yy yz zz; off-diagonals hold d/dSigma_ij (one side)
+    float gS[6];  // symmetric: xx xy xz yy yz zz (full-matrix gradient entries)
     {
-        // M = dS2 Tm (2 x 3)
         float M0[3], M1[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -325,8 +316,7 @@ __device__ __forceinline__ void backward(const Cam &K, const float *__restrict__
     float gT[6];
     {
         const float *S = f.Sg;
-        // Tm Sigma (2 x 3)
-        float U0[3], U1[3];
+        float U0[3], U1[3];  // Tm Sigma
         U0[0] = T[0] * S[0] + T[1] * S[1] + T[2] * S[2];
         U0[1] = T[0] * S[1] + T[1] * S[3] + T[2] * S[4];
         U0[2] = T[0] * S[2] + T[1] * S[4] + T[2] * S[5];
@@ -355,64 +345,66 @@ __device__ __forceinline__ void backward(const Cam &K, const float *__restrict__
     gpx += gu * K.fx * iz;
     gpy += gv * K.fy * iz;
     gpz += -(gu * K.fx * f.px + gv * K.fy * f.py) * iz2;
-    // ---- camera transform
+    // ---- camera transform: the geometric part of the centre's gradient
+    float gm[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gm[k] += K.R[k] * gpx + K.R[3 + k] * gpy + K.R[6 + k] * gpz;
-    emit(0, gm[0]);
-    emit(1, gm[1]);
-    emit(2, gm[2]);
-    // ---- Sigma = sum_k s_k^2 r_k r_k^T: dr_k = 2 s_k^2 G r_k, ds_k = 2 s_k r_k^T G r_k
-    // with G the symmetric gradient [[gS0, gS1/2 ..]] -- off-diagonals of gS
-    // count both (i,j) and (j,i) so they are halved into G.
-    const float G00 = gS[0], G11 = gS[3], G22 = gS[5];
-    const float G01 = gS[1], G02 = gS[2], G12 = gS[4];
-    float gR[9];
+    for (int k = 0; k < 3; ++k) gm[k] = K.R[k] * gpx + K.R[3 + k] * gpy + K.R[6 + k] * gpz;
+    // ---- Sigma = sum_k s_k^2 r_k r_k^T with G the full symmetric gradient:
+    // d/dlog s_k = 2 s_k^2 r_k^T G r_k, d/dr_k = 2 s_k^2 G r_k
+    {
+        const float G00 = gS[0], G11 = gS[3], G22 = gS[5];
+        const float G01 = gS[1], G02 = gS[2], G12 = gS[4];
+        float gR[9];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float r0 = f.Rq[k], r1 = f.Rq[3 + k], r2 = f.Rq[6 + k];
-        const float Gr0 = G00 * r0 + G01 * r1 + G02 * r2;
-        const float Gr1 = G01 * r0 + G11 * r1 + G12 * r2;
-        const float Gr2 = G02 * r0 + G12 * r1 + G22 * r2;
-        const float s2 = f.s[k] * f.s[k];
-        // d/d(log s_k) = s_k d/ds_k = 2 s_k^2 r^T G r
-        emit(3 + k, 2.f * s2 * (r0 * Gr0 + r1 * Gr1 + r2 * Gr2));
-        gR[k] = 2.f * s2 * Gr0;
-        gR[3 + k] = 2.f * s2 * Gr1;
-        gR[6 + k] = 2.f * s2 * Gr2;
+        for (int k = 0; k < 3; ++k) {
+            const float r0 = f.Rq[k], r1 = f.Rq[3 + k], r2 = f.Rq[6 + k];
+            const float Gr0 = G00 * r0 + G01 * r1 + G02 * r2;
+            const float Gr1 = G01 * r0 + G11 * r1 + G12 * r2;
+            const float Gr2 = G02 * r0 + G12 * r1 + G22 * r2;
+            const float s2 = f.s[k] * f.s[k];
+            sink(3 + k, 2.f * s2 * (r0 * Gr0 + r1 * Gr1 + r2 * Gr2));
+            gR[k] = 2.f * s2 * Gr0;
+            gR[3 + k] = 2.f * s2 * Gr1;
+            gR[6 + k] = 2.f * s2 * Gr2;
+        }
+        // Rq(q): derivative of each entry w.r.t. (w, x, y, z) of the unit q
+        const float w = f.qn[0], x = f.qn[1], y = f.qn[2], zq = f.qn[3];
+        float gq[4];
+        gq[0] = 2.f * (-zq * gR[1] + y * gR[2] + zq * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+        gq[1] = 2.f * (y * gR[1] + zq * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] +
+                       zq * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+        gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + zq * gR[5] -
+                       w * gR[6] + zq * gR[7] - 2.f * y * gR[8]);
+        gq[3] = 2.f * (-2.f * zq * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * zq * gR[4] +
+                       y * gR[5] + x * gR[6] + y * gR[7]);
+        const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * zq;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sink(6 + k, (gq[k] - f.qn[k] * dq) * f.qinv);
     }
-    // ---- Rq(q): derivative of each entry w.r.t. (w, x, y, z) of the unit q
-    const float w = f.qn[0], x = f.qn[1], y = f.qn[2], zq = f.qn[3];
-    float gq[4];
-    gq[0] = 2.f * (-zq * gR[1] + y * gR[2] + zq * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-    gq[1] = 2.f * (y * gR[1] + zq * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + zq * gR[6] +
-                   w * gR[7] - 2.f * x * gR[8]);
-    gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + zq * gR[5] - w * gR[6] +
-                   zq * gR[7] - 2.f * y * gR[8]);
-    gq[3] = 2.f * (-2.f * zq * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * zq * gR[4] +
-                   y * gR[5] + x * gR[6] + y * gR[7]);
-    const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * zq;
+    // ---- colour: clamp test, SH coefficients (streamed) and view direction
+    float Y[16], raw[3];
+    sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], Y);
+    color_forward<DEG>(P, stride, row, Y, raw);
+    const float grgb[3] = {raw[0] > 0.f ? gb.z : 0.f, raw[1] > 0.f ? gb.w : 0.f,
+                           raw[2] > 0.f ? gc.x : 0.f};
+    float wk[16];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) emit(6 + k, (gq[k] - f.qn[k] * dq) * f.qinv);
-    emit(10, go * f.o * (1.f - f.o));
-    for (int k = 0; k < K2; ++k) {
+    for (int k = 0; k < KK; ++k) {
+        float w = 0.f;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) emit(11 + 3 * k + ch, grgb[ch] * Y[k]);
+        for (int ch = 0; ch < 3; ++ch) {
+            w += grgb[ch] * P[(11 + 3 * k + ch) * stride + row];
+            sink(11 + 3 * k + ch, grgb[ch] * Y[k]);
+        }
+        wk[k] = w;
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__restrict__ P,
-                                                            int64_t stride, int64_t n, int deg,
-                                                            const uint32_t *__restrict__ map,
-                                                            const int32_t *d_V, Cam K,
-                                                            const float *__restrict__ gacc,
-                                                            float *__restrict__ gout) {
-    const int64_t V = load_count(d_V, n);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = map ? map[j] : j;
-        backward(K, P, stride, row, deg, gacc + 16 * j,
-                 [&](int k, float g) { gout[k * stride + row] = g; });
-    }
+    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+    sh_basis_grad(DEG, f.dir[0], f.dir[1], f.dir[2], wk, gdx, gdy, gdz);
+    const float dd = gdx * f.dir[0] + gdy * f.dir[1] + gdz * f.dir[2];
+    sink(0, gm[0] + (gdx - f.dir[0] * dd) * f.dinv);
+    sink(1, gm[1] + (gdy - f.dir[1] * dd) * f.dinv);
+    sink(2, gm[2] + (gdz - f.dir[2] * dd) * f.dinv);
+    return true;
 }
 
 struct AdamArgs {
@@ -427,22 +419,115 @@ __device__ __forceinline__ void adam_update(float &p, float &m, float &v, float 
     p -= lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
 }
 
-__global__ void __launch_bounds__(kThreads) k_preprocess_bwd_adam(
-    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
-    int64_t n, int deg, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
-    const float *__restrict__ gacc, AdamArgs a) {
+struct GradSink {
+    float *__restrict__ out;
+    int64_t stride, row;
+    __device__ __forceinline__ void operator()(int k, float g) { out[k * stride + row] = g; }
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__restrict__ P,
+                                                            int64_t stride, int64_t n,
+                                                            const uint32_t *__restrict__ map,
+                                                            const int32_t *d_V, Cam K,
+                                                            const float *__restrict__ gacc,
+                                                            float *__restrict__ gout) {
     const int64_t V = load_count(d_V, n);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = map ? map[j] : j;
-        // gradients first (the forward reads the parameters), then the update
-        float g[59];
-        backward(K, P, stride, row, deg, gacc + 16 * j, [&](int k, float x) { g[k] = x; });
-        const int np = 11 + 3 * (deg + 1) * (deg + 1);
-        for (int k = 0; k < np; ++k) {
+        GradSink sink{gout, stride, row};
+        backward<DEG>(K, P, stride, row, gacc + 16 * j, sink);
+    }
+}
+
+// Fused backward + Adam in two passes over the visible Gaussians.
+// Part A: the gradients of every geometric plane; Adam on planes 3..10
+// (scales, rotation, opacity) at once. The centre's gradient (including its
+// colour part, through the view direction and the SH coefficients as they
+// were before this step) is parked in slots 12..14 of the Gaussian's
+// gradient row, slot 15 = 1 if the Gaussian is culled.
+struct GeomSink {
+    float *__restrict__ P;
+    float *__restrict__ M;
+    float *__restrict__ V;
+    float *__restrict__ slots;
+    int64_t stride, row;
+    const AdamArgs *a;
+    __device__ __forceinline__ void operator()(int k, float g) {
+        if (k < 3) {
+            slots[k] = g;
+        } else if (k < 11) {
+            const int64_t i = k * stride + row;
+            float p = P[i], m = M[i], v = V[i];
+            adam_update(p, m, v, g, a->lr[k], *a);
+            P[i] = p;
+            M[i] = m;
+            V[i] = v;
+        }
+    }
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
+    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
+    int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
+    float *__restrict__ gacc, AdamArgs a) {
+    const int64_t V = load_count(d_V, n);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = map ? map[j] : j;
+        float *slots = gacc + 16 * j + 12;
+        GeomSink sink{P, Mo, Vo, slots, stride, row, &a};
+        const bool live = backward<DEG>(K, P, stride, row, gacc + 16 * j, sink);
+        slots[3] = live ? 0.0f : 1.0f;
+    }
+}
+
+// Part B: Adam on the SH planes and the centre. The direction, the basis Y
+// and the colour clamp are recomputed from the centre and coefficients, which
+// part A left untouched; then the SH planes stream through Adam and the
+// centre takes the gradient part A parked.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
+                                                    float *__restrict__ Vo, int64_t stride,
+                                                    int64_t n, const uint32_t *__restrict__ map,
+                                                    const int32_t *d_V, Cam K,
+                                                    const float *__restrict__ gacc, AdamArgs a) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
+    const int64_t V = load_count(d_V, n);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = map ? map[j] : j;
+        const float4 gs = *reinterpret_cast<const float4 *>(gacc + 16 * j + 12);
+        const float *g8 = gacc + 16 * j;
+        const float dx = P[row] - K.cc[0], dy = P[stride + row] - K.cc[1],
+                    dz = P[2 * stride + row] - K.cc[2];
+        const float dinv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16], raw[3];
+        sh_basis(DEG, dx * dinv, dy * dinv, dz * dinv, Y);
+        color_forward<DEG>(P, stride, row, Y, raw);
+        const bool live = gs.w == 0.0f;
+        const float grgb[3] = {live && raw[0] > 0.f ? g8[6] : 0.f, live && raw[1] > 0.f ? g8[7] : 0.f,
+                               live && raw[2] > 0.f ? g8[8] : 0.f};
+#pragma unroll
+        for (int k = 0; k < KK; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const int pl = 11 + 3 * k + ch;
+                const int64_t i = pl * stride + row;
+                float p = P[i], m = Mo[i], v = Vo[i];
+                adam_update(p, m, v, grgb[ch] * Y[k], a.lr[pl], a);
+                P[i] = p;
+                Mo[i] = m;
+                Vo[i] = v;
+            }
+        const float gm[3] = {gs.x, gs.y, gs.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
             const int64_t i = k * stride + row;
             float p = P[i], m = Mo[i], v = Vo[i];
-            adam_update(p, m, v, g[k], a.lr[k], a);
+            adam_update(p, m, v, gm[k], a.lr[k], a);
             P[i] = p;
             Mo[i] = m;
             Vo[i] = v;
@@ -486,30 +571,54 @@ lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t
                       const lgs_camera *cam, int tw, int th, const lgs_splats *out,
                       cudaStream_t s) {
     const Cam K = make_cam(cam, tw, th);
-    count_launch();
-    k_preprocess<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(
-        g->data, g->stride, g->n, g->sh_degree, map, d_V, K, out->rec, out->depth, out->radius);
+    const unsigned grid = grid_for(g->n, kThreads, 16);
+    switch (g->sh_degree) {
+    case 0: count_launch(); k_preprocess<0><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
+    case 1: count_launch(); k_preprocess<1><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
+    case 2: count_launch(); k_preprocess<2><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
+    default: count_launch(); k_preprocess<3><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
+    }
     return check_launch();
 }
 
 lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
                           const lgs_camera *cam, const float *gacc, float *gout, cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
-    count_launch();
-    k_preprocess_bwd<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(
-        g->data, g->stride, g->n, g->sh_degree, map, d_V, K, gacc, gout);
+    const unsigned grid = grid_for(g->n, kThreads, 16);
+    switch (g->sh_degree) {
+    case 0: count_launch(); k_preprocess_bwd<0><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
+    case 1: count_launch(); k_preprocess_bwd<1><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
+    case 2: count_launch(); k_preprocess_bwd<2><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
+    default: count_launch(); k_preprocess_bwd<3><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
+    }
     return check_launch();
 }
 
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
-                               const int32_t *d_V, const lgs_camera *cam, const float *gacc,
+                               const int32_t *d_V, const lgs_camera *cam, float *gacc,
                                const float *lr, float b1, float b2, float eps, int step,
                                cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
-    count_launch();
-    k_preprocess_bwd_adam<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(
-        g->data, m, v, g->stride, g->n, g->sh_degree, map, d_V, K, gacc, a);
+    const unsigned ga = grid_for(g->n, kThreads, 16), gb = grid_for(g->n, 256, 8);
+    switch (g->sh_degree) {
+    case 0:
+        count_launch(); k_bwd_adam_geom<0><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<0><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        break;
+    case 1:
+        count_launch(); k_bwd_adam_geom<1><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<1><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        break;
+    case 2:
+        count_launch(); k_bwd_adam_geom<2><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<2><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        break;
+    default:
+        count_launch(); k_bwd_adam_geom<3><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<3><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        break;
+    }
     return check_launch();
 }
 

@@ -5,10 +5,13 @@
 // Radix sort, one 8-bit digit per pass, reduce-then-scan:
 //   upsweep   - a fixed grid of G CTAs, CTA b owns a contiguous run of
 //               4096-item tiles and counts its digits;
-//   scan      - one CTA turns the [256][G] counts (digit-major) into the
-//               global start of each (digit, CTA);
-//   downsweep - each CTA walks its tiles in order, ranks the items of a
-//               tile stably with a warp multisplit (match.any), stages them
+//   scan      - one block per digit scans that digit's row of the [256][G]
+//               counts (its start within the digit for each CTA) and
+//               records the digit's total;
+//   downsweep - each CTA scans the 256 digit totals into digit starts,
+//               walks its tiles in order, ranks the items of a
+//               tile stably with a warp multisplit (peer masks from
+//               per-bit ballots), stages them
 //               in shared memory in local digit order and writes them out
 //               at its running per-digit offsets.
 // A CTA handles its tiles in input order and ranks are stable inside a
@@ -39,6 +42,20 @@ __device__ __forceinline__ int64_t read_count(int64_t n_max, const int64_t *d_n6
     if (d_n64) n = *d_n64;
     else if (d_n32) n = *d_n32;
     return n < n_max ? n : n_max;
+}
+
+// Lanes of `act` whose 8-bit digit equals this lane's, from one ballot per
+// digit bit (every lane of `act` must call it). Cheaper than match.any, which
+// runs on the address-divergence pipe and saturates it here.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t act, int d) {
+    uint32_t peers = act;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1;
+        const uint32_t m = __ballot_sync(act, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
 }
 
 template <typename K>
@@ -99,7 +116,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const K *__restr
         const int d = ok ? digit_of(keys[i], shift) : -1;
         const uint32_t act = __ballot_sync(0xffffffffu, ok);
         if (ok) {
-            const uint32_t peers = __match_any_sync(act, d);
+            const uint32_t peers = digit_peers(act, d);
             if (lane == __ffs(peers) - 1) s_cnt[wid][d] += __popc(peers);
         }
         __syncwarp();
@@ -112,40 +129,31 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const K *__restr
     }
 }
 
-// In-place exclusive scan of counts[len] (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *counts, int len) {
+// Per digit d (one block each): exclusive scan of counts[d][0..G) in place,
+// and totals[d] = the row's sum. The digits' bases are scanned by each
+// downsweep CTA from the 256 totals.
+__global__ void __launch_bounds__(1024) k_scan_digit_rows(uint32_t *counts, int G,
+                                                         uint32_t *totals) {
     __shared__ uint64_t s_tmp[33];
-    __shared__ uint64_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    constexpr int kPer = 8;
-    for (int base = 0; base < len; base += 1024 * kPer) {
-        uint32_t v[kPer];
-        uint64_t sum = 0;
-        const int i0 = base + threadIdx.x * kPer;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            v[k] = (i0 + k < len) ? counts[i0 + k] : 0u;
-            sum += v[k];
-        }
+    uint32_t *row = counts + (int64_t)blockIdx.x * G;
+    uint64_t carry = 0;
+    for (int base = 0; base < G; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t x = i < G ? row[i] : 0u;
         uint64_t tot;
-        uint64_t pre = block_exclusive_scan(sum, s_tmp, &tot) + s_carry;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            if (i0 + k < len) counts[i0 + k] = (uint32_t)pre;
-            pre += v[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
+        const uint64_t ex = block_exclusive_scan(x, s_tmp, &tot);
+        if (i < G) row[i] = (uint32_t)(carry + ex);
+        carry += tot;
     }
+    if (threadIdx.x == 0) totals[blockIdx.x] = (uint32_t)carry;
 }
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
-    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ offsets, int64_t n_max,
-    const int64_t *d_n64, const int32_t *d_n32, int shift) {
+    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ offsets,
+    const uint32_t *__restrict__ totals, int64_t n_max, const int64_t *d_n64, const int32_t *d_n32,
+    int shift) {
     __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
     __shared__ uint32_t s_run[kRadix];
     __shared__ uint32_t s_start[kRadix];
@@ -162,7 +170,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     const int64_t n = read_count(n_max, d_n64, d_n32);
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int64_t t0 = tiles * b / G, t1 = tiles * (b + 1) / G;
-    if (threadIdx.x < kRadix) s_run[threadIdx.x] = offsets[(int64_t)threadIdx.x * G + b];
+    {
+        // global start of each digit, then of this CTA's share of it
+        const uint64_t tot = threadIdx.x < kRadix ? totals[threadIdx.x] : 0u;
+        const uint64_t base = block_exclusive_scan(tot, s_scan, nullptr);
+        if (threadIdx.x < kRadix)
+            s_run[threadIdx.x] = (uint32_t)base + offsets[(int64_t)threadIdx.x * G + b];
+    }
     const uint32_t lt = lanemask_lt();
 
     for (int64_t tile = t0; tile < t1; ++tile) {
@@ -185,7 +199,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
             const int d = dig[j];
             const uint32_t act = __ballot_sync(0xffffffffu, d >= 0);
             if (d >= 0) {
-                const uint32_t peers = __match_any_sync(act, d);
+                const uint32_t peers = digit_peers(act, d);
                 const uint32_t before = s_wcnt[wid][d];
                 rank[j] = before + __popc(peers & lt);
                 __syncwarp(peers);
@@ -247,6 +261,7 @@ lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const i
     if (n_max > 0xffffffffLL) return LGS_ERR_INVALID_ARG;
     const int G = sort_grid();
     uint32_t *counts = static_cast<uint32_t *>(scratch);
+    uint32_t *totals = counts + (size_t)kRadix * G;
     const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * kTile;
     static bool attr_set = false;
     if (!attr_set) {
@@ -261,11 +276,12 @@ lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const i
         count_launch();
         k_radix_upsweep<K><<<G, kSortThreads, 0, s>>>(keys[cur], n_max, d_n64, d_n32, shift, counts);
         count_launch();
-        k_scan_counts<<<1, 1024, 0, s>>>(counts, kRadix * G);
+        k_scan_digit_rows<<<kRadix, (G + 31) / 32 * 32 < 1024 ? (G + 31) / 32 * 32 : 1024, 0, s>>>(
+            counts, G, totals);
         count_launch();
         k_radix_downsweep<K><<<G, kSortThreads, dyn, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
-                                                       vals[cur ^ 1], counts, n_max, d_n64, d_n32,
-                                                       shift);
+                                                       vals[cur ^ 1], counts, totals, n_max, d_n64,
+                                                       d_n32, shift);
         cur ^= 1;
     }
     *out_buf = cur;
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *__r
 
 int radix_passes(int bits) { return bits <= 0 ? 1 : (bits + 7) / 8; }
 
-size_t radix_hist_bytes() { return (size_t)kRadix * sort_grid() * sizeof(uint32_t); }
+size_t radix_hist_bytes() { return (size_t)kRadix * (sort_grid() + 1) * sizeof(uint32_t); }
 
 size_t radix_sort_workspace(int64_t n, int key_bytes) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };

@@ -115,7 +115,9 @@ def test_full_step_config1(orc, deg):
     err = np.abs(g["image"] - o["image"])[:, ok].max()
     assert err <= 1e-5, err
     np.testing.assert_array_equal(g["last"][ok], o["last"][ok])
-    assert abs(g["loss"] - o["loss"]) <= 1e-6 * o["loss"] + 1e-7
+    # the loss also sums the flagged pixels, so it is checked on shared
+    # inputs in test_loss_l1_kernel_matches_oracle; here only loosely
+    assert abs(g["loss"] - o["loss"]) <= 1e-4 * o["loss"]
     rows = o["map"]
     for name, sl in (("mean", slice(0, 3)), ("log_scale", slice(3, 6)), ("quat", slice(6, 10)),
                      ("logit", slice(10, 11)), ("sh", slice(11, None))):
@@ -143,6 +145,20 @@ def test_fused_backward_adam_equals_separate(orc):
     np.testing.assert_allclose(b["m"], a["m"], rtol=1e-4, atol=1e-12)
     np.testing.assert_allclose(b["v"], a["v"], rtol=1e-4, atol=1e-20)
     assert np.mean(np.abs(b["params"] - a["params"]) > 1e-6) < 1e-3
+
+
+def test_loss_l1_kernel_matches_oracle(orc):
+    img = scenegen.random_image(41, 3, 333, 257) * 1.2 - 0.1
+    tgt = scenegen.random_image(42, 3, 333, 257)
+    tgt[0, :5, :7] = img[0, :5, :7]  # exact ties: sign(0) = 0
+    L, dL = orc.l1_loss(img, tgt)
+    ti, tt = U.t(img), U.t(tgt)
+    g = torch.empty_like(ti)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    B.lgs_loss_l1(ti, tt, g, loss)
+    torch.cuda.synchronize()
+    assert abs(float(loss.item()) - L) <= 1e-6 * L
+    np.testing.assert_array_equal(g.cpu().numpy(), dL.astype(np.float32))
 
 
 def test_adam_kernel_matches_oracle(orc):
