@@ -60,6 +60,7 @@ typedef int32_t lgs_status;
 #define LGS_ERR_CAPACITY 2
 #define LGS_ERR_CUDA 3
 #define LGS_ERR_TIMEOUT 4
+#define LGS_ERR_TOO_LARGE 5 /* size beyond a fixed maximum of this library */
 
 typedef void *lgs_stream; /* cudaStream_t */
 
@@ -148,6 +149,33 @@ lgs_status lgs_cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *ca
                                     uint32_t *cluster_visible_out, uint32_t *map_out,
                                     int32_t *d_num_visible, void *workspace,
                                     size_t workspace_bytes, lgs_stream stream);
+
+/* Allocation-free variant of lgs_cluster_cull_compact (the paper has no
+ * counterpart; it is an interface addition of this library).
+ * Some callers cannot call cudaMalloc or hand out a workspace: code that runs
+ * inside another framework's memory pool and must not allocate outside it,
+ * code that must not synchronise the device (cudaMalloc and cudaFree can),
+ * and plugin or render-loop hosts that forbid allocation at frame time. This
+ * entry point takes the same inputs and writes the same outputs as
+ * lgs_cluster_cull_compact, but its scratch lives in a fixed array of
+ * device memory inside the library (about 770 KB; every GPU that loads the
+ * library holds it until the process exits). It calls no cudaMalloc, no
+ * cudaFree and no allocating library routine.
+ *   - Limit: ceil(n / cluster_size) <= LGS_NOALLOC_MAX_CLUSTERS (8,388,608
+ *     Gaussians at 128 per cluster); larger inputs return LGS_ERR_TOO_LARGE
+ *     and enqueue nothing.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current). Make that first call before any
+ *     stream capture.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (nothing in it needs to start at zero). Calls that overlap on the GPU,
+ *     e.g. on two streams without ordering between them, race on it: order
+ *     them on one stream or with events. */
+#define LGS_NOALLOC_MAX_CLUSTERS 65536
+lgs_status lgs_cluster_cull_compact_noalloc(const lgs_gaussians *g, const lgs_camera *cam,
+                                            int32_t cluster_size, float *aabb_out,
+                                            uint32_t *cluster_visible_out, uint32_t *map_out,
+                                            int32_t *d_num_visible, lgs_stream stream);
 
 /* dst[k * dst_stride + j] = src[k * src_stride + map[j]] for j < V (device). */
 lgs_status lgs_compact_gather(const float *src, int64_t src_stride, float *dst,

@@ -15,14 +15,16 @@ import torch
 from . import build as _build
 
 LGS_OK, LGS_ERR_INVALID_ARG, LGS_ERR_CAPACITY, LGS_ERR_CUDA, LGS_ERR_TIMEOUT = 0, 1, 2, 3, 4
+LGS_ERR_TOO_LARGE = 5
+NOALLOC_MAX_CLUSTERS = 65536
 SPLAT_FLOATS = 12
 GRAD_FLOATS = 16
 MAX_PLANES = 59
 
 ENTRY_POINTS = (
     "lgs_version", "lgs_last_cuda_error", "lgs_kernel_launches", "lgs_morton_workspace_size", "lgs_morton_reorder",
-    "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_compact_gather",
-    "lgs_preprocess",
+    "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_cluster_cull_compact_noalloc",
+    "lgs_compact_gather", "lgs_preprocess",
     "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_raster_fwd",
     "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
     "lgs_adam_step", "lgs_preprocess_bwd_adam",
@@ -81,6 +83,7 @@ def load(build_if_missing: bool = True):
         "lgs_morton_reorder": (i32, [P, P, i64, i64, i32, P, P, P, sz, P]),
         "lgs_ccc_workspace_size": (sz, [i64, i32]),
         "lgs_cluster_cull_compact": (i32, [P, P, i32, P, P, P, P, P, sz, P]),
+        "lgs_cluster_cull_compact_noalloc": (i32, [P, P, i32, P, P, P, P, P]),
         "lgs_compact_gather": (i32, [P, i64, P, i64, i32, P, P, i64, P]),
         "lgs_preprocess": (i32, [P, P, P, P, i32, i32, P, P]),
         "lgs_bin_sort_workspace_size": (sz, [i64, i64, i32]),
@@ -105,7 +108,8 @@ def load(build_if_missing: bool = True):
 def _check(status: int, what: str):
     if status != LGS_OK:
         err = _lib.lgs_last_cuda_error() if _lib is not None else 0
-        names = {1: "LGS_ERR_INVALID_ARG", 2: "LGS_ERR_CAPACITY", 3: "LGS_ERR_CUDA", 4: "LGS_ERR_TIMEOUT"}
+        names = {1: "LGS_ERR_INVALID_ARG", 2: "LGS_ERR_CAPACITY", 3: "LGS_ERR_CUDA", 4: "LGS_ERR_TIMEOUT",
+                 5: "LGS_ERR_TOO_LARGE"}
         raise LgsError(f"{what} failed: {names.get(status, status)} (cuda error {err})")
 
 
@@ -194,6 +198,19 @@ def lgs_cluster_cull_compact(g: LgsGaussians, cam: LgsCamera, cluster_size, aabb
                                       _ptr(aabb_out), _ptr(cluster_visible_out), _ptr(map_out),
                                       _ptr(d_num_visible), _ptr(workspace), workspace.numel(),
                                       _stream(stream)), "lgs_cluster_cull_compact")
+
+
+def lgs_cluster_cull_compact_noalloc(g: LgsGaussians, cam: LgsCamera, cluster_size, aabb_out,
+                                     cluster_visible_out, map_out, d_num_visible, stream=None):
+    """Same as lgs_cluster_cull_compact, with no workspace: for callers that
+    cannot allocate device memory. Uses a fixed scratch array inside the
+    library (see include/lgs.h for its limit and sharing rules)."""
+    L = load()
+    _check(L.lgs_cluster_cull_compact_noalloc(ctypes.byref(g), ctypes.byref(cam), cluster_size,
+                                              _ptr(aabb_out), _ptr(cluster_visible_out),
+                                              _ptr(map_out), _ptr(d_num_visible),
+                                              _stream(stream)),
+           "lgs_cluster_cull_compact_noalloc")
 
 
 def lgs_compact_gather(src, dst, n_planes, map_, d_num_visible, max_rows, stream=None):

@@ -20,6 +20,9 @@ lgs_status cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *cam, i
 lgs_status compact_gather(const float *src, int64_t src_stride, float *dst, int64_t dst_stride,
                           int n_planes, const uint32_t *map, const int32_t *d_V, int64_t max_rows,
                           cudaStream_t s);
+lgs_status cluster_cull_compact_noalloc(const lgs_gaussians *g, const lgs_camera *cam, int cs,
+                                        float *aabb_out, uint32_t *vis_out, uint32_t *map,
+                                        int32_t *d_V, cudaStream_t s);
 lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
                       const lgs_camera *cam, int tw, int th, const lgs_splats *out, cudaStream_t s);
 lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
@@ -142,6 +145,17 @@ lgs_status lgs_cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *ca
         return LGS_ERR_INVALID_ARG;
     return cluster_cull_compact(g, cam, cluster_size, aabb_out, cluster_visible_out, map_out,
                                 d_num_visible, workspace, as_stream(stream));
+}
+
+lgs_status lgs_cluster_cull_compact_noalloc(const lgs_gaussians *g, const lgs_camera *cam,
+                                            int32_t cluster_size, float *aabb_out,
+                                            uint32_t *cluster_visible_out, uint32_t *map_out,
+                                            int32_t *d_num_visible, lgs_stream stream) {
+    if (bad_gaussians(g) || bad_camera(cam) || cluster_size <= 0 || !map_out || !d_num_visible ||
+        g->n == 0)
+        return LGS_ERR_INVALID_ARG;
+    return cluster_cull_compact_noalloc(g, cam, cluster_size, aabb_out, cluster_visible_out,
+                                        map_out, d_num_visible, as_stream(stream));
 }
 
 lgs_status lgs_compact_gather(const float *src, int64_t src_stride, float *dst,

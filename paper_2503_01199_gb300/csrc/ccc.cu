@@ -1,6 +1,8 @@
 // Morton re-sort (Sec. 3.2.1) and Cluster-Cull-Compact (Sec. 3.2.2).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "lgs_internal.cuh"
 
 namespace lgs {
@@ -260,6 +262,66 @@ lgs_status compact_gather(const float *src, int64_t src_stride, float *dst, int6
     k_gather_planes<<<grid_for(max_rows, kThreads), kThreads, 0, s>>>(
         src, src_stride, dst, dst_stride, n_planes, map, max_rows, d_V);
     return check_launch();
+}
+
+}  // namespace lgs
+
+namespace lgs {
+
+// ---------------------------------------------------------------------------
+// lgs_cluster_cull_compact_noalloc: the same cull and compaction, with its
+// scratch in a fixed device array instead of a caller workspace
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoallocMaxClusters = LGS_NOALLOC_MAX_CLUSTERS;
+// ccc_workspace_size() for the largest cluster count: flags, offsets, count, scan
+constexpr size_t kNoallocBytes = ((kNoallocMaxClusters * 4 + 255) / 256) * 256 +
+                                 ((kNoallocMaxClusters * 8 + 255) / 256) * 256 + 256 + 4096;
+
+// One copy per device that loads the library; kept until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device; in host code the symbol itself is not a device address).
+lgs_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return LGS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 64) return LGS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_cuda_error(e);
+            return LGS_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LGS_OK;
+}
+
+}  // namespace
+
+lgs_status cluster_cull_compact_noalloc(const lgs_gaussians *g, const lgs_camera *cam, int cs,
+                                        float *aabb_out, uint32_t *vis_out, uint32_t *map,
+                                        int32_t *d_V, cudaStream_t s) {
+    if (ceil_div(g->n, cs) > kNoallocMaxClusters) return LGS_ERR_TOO_LARGE;
+    if (ccc_workspace_size(g->n, cs) > kNoallocBytes) return LGS_ERR_TOO_LARGE;
+    void *ws = nullptr;
+    lgs_status st = noalloc_scratch(&ws);
+    if (st != LGS_OK) return st;
+    // every byte of the scratch that this call reads is written earlier in
+    // the same call (flags, scan partials, offsets, count): nothing to clear
+    return cluster_cull_compact(g, cam, cs, aabb_out, vis_out, map, d_V, ws, s);
 }
 
 }  // namespace lgs
