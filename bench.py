@@ -160,7 +160,7 @@ def run_gpu(args) -> dict | None:
     B.load()
     d = make_workload(rank, args.n_gaussians)
     sc, cam, tgt_np = d["scene"], d["camera"], d["target"]
-    tr = PL.Trainer(sc, W_IMG, H_IMG, PL.StepConfig(tile=TILE, pair_capacity=192_000_000),
+    tr = PL.Trainer(sc, W_IMG, H_IMG, PL.StepConfig(tile=TILE, pair_capacity=128_000_000),
                     device=str(dev))
     del sc
     cs = B.camera_struct(cam)

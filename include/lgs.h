@@ -35,11 +35,14 @@
  *
  * Projected splat record (Sec. 3: {x, y, Sigma^screen, c, o}), 12 floats per
  * visible Gaussian j, 48-byte aligned rows of `rec`:
- *   rec[12 j + 0..8] = u, v, A, B, C, o, r, g, b
+ *   rec[12 j + 0..9] = u, v, A, B, C, o, r, g, b, tau
  * where (u, v) is the screen centre in pixels, (A, B, C) the inverse 2D
- * covariance [[A, B], [B, C]] used in the exponent of Eq. 2, o the opacity
- * and (r, g, b) the colour. Slots 9..11 are reserved. depth[j] is the
- * camera-space z, radius[j] the integer screen radius (0 = culled).
+ * covariance [[A, B], [B, C]] used in the exponent of Eq. 2, o the opacity,
+ * (r, g, b) the colour and tau the largest value of the exponent's quadratic
+ * form d^T [[A, B], [B, C]] d at which alpha = o exp(-q/2) can reach 1/255:
+ * tau = 2 ln(255 o) widened by 1e-3 (1 + |tau|). Slots 10..11 are reserved.
+ * depth[j] is the camera-space z, radius[j] the integer screen radius
+ * (0 = culled).
  *
  * Pixel (x, y) is sampled at its centre (x + 0.5, y + 0.5). Images are
  * planar float32 [3][height][width].
@@ -209,20 +212,30 @@ lgs_status lgs_preprocess(const lgs_gaussians *g, const uint32_t *map,
  * whose pixel square meets [u - r, u + r] x [v - r, v + r]:
  *   x0 = floor((u - r) / tile_w), x1 = floor((u + r) / tile_w) + 1 (same in
  *   y), clamped to the tile grid, computed in single precision.
+ * With tile_cull = 1 (the tile-level culling of App. A.1) a tile of that
+ * rectangle is listed only if the minimum of d^T [[A, B], [B, C]] d over the
+ * box of its pixel centres (d = splat centre - pixel centre) is <= tau: the
+ * other tiles cannot receive a contribution (alpha < 1/255 at every pixel),
+ * so images, transmittances and gradients are the same as with
+ * tile_cull = 0; only list positions change. Both tests are single
+ * precision with explicit rounding.
  * Each tile's list is in increasing depth; equal depths keep increasing
  * compacted index (a stable sort of the key (tile << 32 | depth bits)).
  * Outputs (device): vals[P] = compacted splat index of each pair, grouped by
- * tile; tile_ranges[2 t], [2 t + 1] = begin, end of tile t (row-major tile
- * id t = ty * grid_w + tx); *d_num_pairs = P.
+ * tile (the tiles' groups are laid out in an order of the library's
+ * choosing); tile_ranges[2 t], [2 t + 1] = begin, end of tile t's list in
+ * vals (row-major tile id t = ty * grid_w + tx); *d_num_pairs = P.
  * If P > pair_capacity only the first pair_capacity pairs are written, the
  * device overflow flag is raised and lgs_get_overflow() reports the size
  * needed; the image is then incomplete.
  * ---------------------------------------------------------------------- */
+/* n_tiles: the tile count of the largest image the workspace will serve. */
 size_t lgs_bin_sort_workspace_size(int64_t max_splats, int64_t pair_capacity, int32_t n_tiles);
 lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int64_t max_splats,
-                        const lgs_camera *cam, int32_t tile_w, int32_t tile_h, uint32_t *vals,
-                        int64_t pair_capacity, int64_t *d_num_pairs, uint32_t *tile_ranges,
-                        void *workspace, size_t workspace_bytes, lgs_stream stream);
+                        const lgs_camera *cam, int32_t tile_w, int32_t tile_h, int32_t tile_cull,
+                        uint32_t *vals, int64_t pair_capacity, int64_t *d_num_pairs,
+                        uint32_t *tile_ranges, void *workspace, size_t workspace_bytes,
+                        lgs_stream stream);
 
 /* Synchronises the device, returns LGS_ERR_CAPACITY and the largest pair
  * count seen if some lgs_bin_sort overflowed since the last query (and
@@ -265,8 +278,8 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
  * grad_acc (device) [max_splats][16] floats, row j:
  *   0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 do (activated opacity), 6..8 dr dg db,
  *   9 S = sum of (dL/do per pixel)^2, 10 M = sum of dL/do per pixel,
- *   11 C = count of included fragments as uint32, 12..15 zero (scratch of
- *   lgs_preprocess_bwd_adam).
+ *   11 C = count of included fragments as uint32, 12..15 zero (slots 6..8
+ *   and 12..14 are rewritten by lgs_preprocess_bwd_adam).
  * accumulate = 0 zeroes rows j < max_splats first; 1 adds to them.
  * ---------------------------------------------------------------------- */
 lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
@@ -309,9 +322,10 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
 /* a9 + a10 without a gradient buffer: each parameter's gradient is applied
  * by Adam as soon as it is computed. m and v are planes with the stride of g;
  * g->data is updated in place. Same results as lgs_preprocess_bwd followed by
- * lgs_adam_step up to rounding. Slots 12..15 of each grad_acc row are used as
- * scratch (the centre's gradient and a culled flag pass between the two
- * kernels of this call); slots 0..11 are not modified. */
+ * lgs_adam_step up to rounding. grad_acc rows are used as scratch between
+ * the two kernels of this call: slots 6..8 receive the colour gradient with
+ * clamped channels zeroed (0 for culled Gaussians) and slots 12..14 the
+ * view direction; the other slots are not modified. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
                                    const lgs_camera *cam, float *grad_acc,

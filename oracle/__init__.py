@@ -91,12 +91,12 @@ def lib():
             "or_set_margins": (None, [f64] * 5),
             "or_sh_basis_spherical": (None, [i32, P, P]),
             "or_sh_basis_cartesian": (None, [i32, P, P, P]),
-            "or_preprocess": (None, [i64, i32, P, P, P, P, P, P, i32, i32, P, P, P, P, P, P, P, P]),
+            "or_preprocess": (None, [i64, i32, P, P, P, P, P, P, i32, i32, P, P, P, P, P, P, P, P, P]),
             "or_morton_interleave": (ctypes.c_uint64, [ctypes.c_uint32] * 3),
             "or_morton_codes": (None, [i64, P, P]),
             "or_sort_u64_stable": (None, [i64, P, P]),
             "or_cluster_cull": (i64, [i64, i32, P, P, P, P, P, P, P]),
-            "or_bin": (i64, [i64, P, P, P, P, i32, i32, i32, i32, i64, P, P]),
+            "or_bin": (i64, [i64, P, P, P, P, P, P, i32, i32, i32, i32, i32, i64, P, P]),
             "or_render_fwd": (ctypes.c_uint64, [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
             "or_render_bwd": (None, [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, i64, P, P, P, P, P]),
             "or_l1_loss": (f64, [i64, P, P, P]),
@@ -194,12 +194,13 @@ def preprocess(scene: dict, cam: dict, tile=(16, 16)) -> dict:
     n = mean.shape[0]
     out = {"uv": np.zeros((n, 2)), "conic": np.zeros((n, 3)), "depth": np.zeros(n),
            "opacity": np.zeros(n), "rgb": np.zeros((n, 3)), "radius": np.zeros(n, np.int32),
-           "rect": np.zeros((n, 4), np.int32), "flags": np.zeros(n, np.uint8)}
+           "rect": np.zeros((n, 4), np.int32), "flags": np.zeros(n, np.uint8),
+           "tau": np.zeros(n)}
     camv = camera_array(cam)
     lib().or_preprocess(n, int(scene["sh_degree"]), _p(mean), _p(ls), _p(q), _p(logit), _p(sh),
                         _p(camv), tile[0], tile[1], _p(out["uv"]), _p(out["conic"]),
                         _p(out["depth"]), _p(out["opacity"]), _p(out["rgb"]), _p(out["radius"]),
-                        _p(out["rect"]), _p(out["flags"]))
+                        _p(out["rect"]), _p(out["flags"]), _p(out["tau"]))
     return out
 
 
@@ -242,19 +243,28 @@ def cluster_cull(scene: dict, cam: dict, cluster: int = 128) -> dict:
     return {"aabb": aabb, "visible": vis, "flags": flags, "map": rowmap[:V], "V": int(V)}
 
 
-def bin_splats(u, v, radius, depth, width: int, height: int, tile=(16, 16)):
-    """Per-tile depth-ordered lists: (vals, ranges[ntiles, 2], P)."""
+def bin_splats(u, v, radius, depth, width: int, height: int, tile=(16, 16), conic=None,
+               tau=None, cull=None):
+    """Per-tile depth-ordered lists: (vals, ranges[ntiles, 2], P). With conic
+    and tau given (float32 [n,3], [n]) the tile-level culling test applies
+    (cull defaults to whether they are given)."""
     u, v = _c(u, np.float32), _c(v, np.float32)
     radius, depth = _c(radius, np.int32), _c(depth, np.float32)
     n = u.shape[0]
+    if cull is None:
+        cull = conic is not None and tau is not None
+    if cull:
+        conic, tau = _c(conic, np.float32), _c(tau, np.float32)
     gx, gy = (width + tile[0] - 1) // tile[0], (height + tile[1] - 1) // tile[1]
     ranges = np.zeros((gx * gy, 2), np.uint32)
+    cp = _p(conic) if cull else None
+    tp = _p(tau) if cull else None
     # count first, then fill
-    P = lib().or_bin(n, _p(u), _p(v), _p(radius), _p(depth), width, height, tile[0], tile[1], 0,
-                     None, _p(ranges))
+    P = lib().or_bin(n, _p(u), _p(v), _p(radius), _p(depth), cp, tp, int(bool(cull)), width,
+                     height, tile[0], tile[1], 0, None, _p(ranges))
     vals = np.zeros(max(P, 1), np.uint32)
-    P2 = lib().or_bin(n, _p(u), _p(v), _p(radius), _p(depth), width, height, tile[0], tile[1], P,
-                      _p(vals), _p(ranges))
+    P2 = lib().or_bin(n, _p(u), _p(v), _p(radius), _p(depth), cp, tp, int(bool(cull)), width,
+                      height, tile[0], tile[1], P, _p(vals), _p(ranges))
     assert P2 == P
     return vals[:P], ranges, int(P)
 
@@ -370,11 +380,13 @@ def grad_planes(g: dict) -> np.ndarray:
 # --------------------------------------------------------------------------
 # composites
 # --------------------------------------------------------------------------
-def render_scene(scene: dict, cam: dict, tile=(16, 16)) -> dict:
-    """preprocess -> bin -> forward; returns everything (double precision)."""
+def render_scene(scene: dict, cam: dict, tile=(16, 16), cull: bool = True) -> dict:
+    """preprocess -> bin (with tile-level culling unless cull=False) ->
+    forward; returns everything (double precision)."""
     sp = preprocess(scene, cam, tile)
     vals, ranges, P = bin_splats(sp["uv"][:, 0], sp["uv"][:, 1], sp["radius"], sp["depth"],
-                                 cam["width"], cam["height"], tile)
+                                 cam["width"], cam["height"], tile, conic=sp["conic"],
+                                 tau=sp["tau"], cull=cull)
     fw = render_fwd(sp, vals, ranges, cam, tile)
     return {"splats": sp, "vals": vals, "ranges": ranges, "P": P, **fw}
 

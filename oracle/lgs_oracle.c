@@ -341,6 +341,40 @@ static void tile_rect_f32(float u, float v, float r, int tw, int th, int gx, int
     rect[0] = (int)x0; rect[1] = (int)y0; rect[2] = (int)x1; rect[3] = (int)y1;
 }
 
+/* Tile-level culling (App. A.1: tiles where a splat has decayed to nothing
+ * are not listed). Tile (tx, ty) can receive a contribution when the minimum
+ * of q(d) = A dx^2 + 2 B dx dy + C dy^2 over the box of its pixel centres
+ * (d = splat centre - pixel centre) is <= tau. The minimum is 0 when the box
+ * holds the centre, else it lies on an edge at the clamped 1D minimiser.
+ * Single precision, in the kernel's operation order: the decision selects
+ * list entries, which must match bit for bit. */
+static float quad_form_f32(float A, float B, float C, float dx, float dy) {
+    float t1 = (A * dx) * dx;
+    float t2 = ((B * dx) * dy) * 2.0f;
+    float t3 = (C * dy) * dy;
+    return (t1 + t2) + t3;
+}
+
+static int tile_reachable_f32(float u, float v, float A, float B, float C, float tau, int tx,
+                              int ty, int tw, int th) {
+    float xl = (float)(tx * tw) + 0.5f, xh = (float)(tx * tw + tw) + -0.5f;
+    float yl = (float)(ty * th) + 0.5f, yh = (float)(ty * th + th) + -0.5f;
+    float ax = u - xh, bx = u - xl, ay = v - yh, by = v - yl;
+    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return 1;
+    /* edge minimiser -B dx / C as (B dx) * (1/C), reciprocals rounded once */
+    float rA = 1.0f / A, rC = 1.0f / C;
+    float d, q;
+    d = fminf(fmaxf(-((B * ax) * rC), ay), by);
+    q = quad_form_f32(A, B, C, ax, d);
+    d = fminf(fmaxf(-((B * bx) * rC), ay), by);
+    q = fminf(q, quad_form_f32(A, B, C, bx, d));
+    d = fminf(fmaxf(-((B * ay) * rA), ax), bx);
+    q = fminf(q, quad_form_f32(A, B, C, d, ay));
+    d = fminf(fmaxf(-((B * by) * rA), ax), bx);
+    q = fminf(q, quad_form_f32(A, B, C, d, by));
+    return q <= tau;
+}
+
 static int frac_near_int(double x, double margin) {
     double f = x - floor(x);
     return f < margin || f > 1.0 - margin;
@@ -349,10 +383,18 @@ static int frac_near_int(double x, double margin) {
 /* flags bit0: 3 sqrt(lambda_max) within rounding of an integer (radius);
  *       bit1: near-plane test within rounding of its threshold;
  *       bit2: u -+ r or v -+ r within rounding of a tile boundary. */
+/* tau: the largest d^T conic d at which alpha = o exp(-q/2) reaches 1/255,
+ * 2 ln(255 o), widened by 1e-3 (1 + |tau|) [reading: App. A.1's tile-level
+ * culling with a margin far above single-precision rounding]. */
+static double contrib_tau(double o) {
+    double t = 2.0 * log(255.0 * o);
+    return t > -1e30 ? t + 1e-3 * (1.0 + fabs(t)) : -INFINITY;
+}
+
 void or_preprocess(int64_t n, int deg, const double *mean, const double *log_scale,
                    const double *quat, const double *logit, const double *sh, const double *camv,
                    int tw, int th, double *uv, double *conic, double *depth, double *opacity,
-                   double *rgb, int32_t *radius, int32_t *rect, uint8_t *flags) {
+                   double *rgb, int32_t *radius, int32_t *rect, uint8_t *flags, double *tau) {
     ocam C = cam_unpack(camv);
     int K = (deg + 1) * (deg + 1);
     int gx = (C.W + tw - 1) / tw, gy = (C.H + th - 1) / th;
@@ -382,8 +424,10 @@ void or_preprocess(int64_t n, int deg, const double *mean, const double *log_sca
             rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = 0.0;
             radius[i] = 0;
             for (int k = 0; k < 4; ++k) rect[4 * i + k] = 0;
+            tau[i] = -INFINITY;
             continue;
         }
+        tau[i] = contrib_tau(g.o);
         uv[2 * i] = g.u; uv[2 * i + 1] = g.v;
         for (int k = 0; k < 3; ++k) conic[3 * i + k] = g.conic[k];
         depth[i] = g.pc[2];
@@ -520,16 +564,26 @@ int64_t or_cluster_cull(int64_t n, int cluster, const double *mean, const double
 /* the float bits order like the values. Returns the number of pairs P;    */
 /* writes at most cap pairs.                                                */
 /* ------------------------------------------------------------------------ */
+/* cull = 1 adds the tile-level culling test above (conic [n][3] and tau [n]
+ * are then read; they may be NULL when cull = 0). */
+static int listed(const float *u, const float *v, const float *conic, const float *tau, int cull,
+                  int64_t i, int x, int y, int tw, int th) {
+    if (!cull) return 1;
+    return tile_reachable_f32(u[i], v[i], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], tau[i],
+                              x, y, tw, th);
+}
+
 int64_t or_bin(int64_t n, const float *u, const float *v, const int32_t *radius,
-               const float *depth, int W, int H, int tw, int th, int64_t cap, uint32_t *vals,
-               uint32_t *ranges) {
+               const float *depth, const float *conic, const float *tau, int cull, int W, int H,
+               int tw, int th, int64_t cap, uint32_t *vals, uint32_t *ranges) {
     int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
     int64_t P = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (radius[i] <= 0) continue;
         int rc[4];
         tile_rect_f32(u[i], v[i], (float)radius[i], tw, th, gx, gy, rc);
-        if (rc[2] > rc[0] && rc[3] > rc[1]) P += (int64_t)(rc[2] - rc[0]) * (rc[3] - rc[1]);
+        for (int y = rc[1]; y < rc[3]; ++y)
+            for (int x = rc[0]; x < rc[2]; ++x) P += listed(u, v, conic, tau, cull, i, x, y, tw, th);
     }
     uint64_t *key = (uint64_t *)malloc((size_t)(P > 0 ? P : 1) * sizeof(uint64_t));
     uint32_t *val = (uint32_t *)malloc((size_t)(P > 0 ? P : 1) * sizeof(uint32_t));
@@ -543,6 +597,7 @@ int64_t or_bin(int64_t n, const float *u, const float *v, const int32_t *radius,
         memcpy(&db, depth + i, 4);
         for (int y = rc[1]; y < rc[3]; ++y)
             for (int x = rc[0]; x < rc[2]; ++x) {
+                if (!listed(u, v, conic, tau, cull, i, x, y, tw, th)) continue;
                 key[k] = ((uint64_t)(y * gx + x) << 32) | db;
                 val[k] = (uint32_t)i;
                 ++k;

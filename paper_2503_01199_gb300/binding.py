@@ -87,7 +87,7 @@ def load(build_if_missing: bool = True):
         "lgs_compact_gather": (i32, [P, i64, P, i64, i32, P, P, i64, P]),
         "lgs_preprocess": (i32, [P, P, P, P, i32, i32, P, P]),
         "lgs_bin_sort_workspace_size": (sz, [i64, i64, i32]),
-        "lgs_bin_sort": (i32, [P, P, i64, P, i32, i32, P, i64, P, P, P, sz, P]),
+        "lgs_bin_sort": (i32, [P, P, i64, P, i32, i32, i32, P, i64, P, P, P, sz, P]),
         "lgs_get_overflow": (i32, [P]),
         "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, P, P, P, P]),
         "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
@@ -232,10 +232,10 @@ def lgs_bin_sort_workspace_size(max_splats: int, pair_capacity: int, n_tiles: in
 
 
 def lgs_bin_sort(sp: LgsSplats, d_num_visible, max_splats, cam: LgsCamera, tile_w, tile_h, vals,
-                 d_num_pairs, tile_ranges, workspace, stream=None):
+                 d_num_pairs, tile_ranges, workspace, stream=None, tile_cull=1):
     L = load()
     _check(L.lgs_bin_sort(ctypes.byref(sp), _ptr(d_num_visible), max_splats, ctypes.byref(cam),
-                          tile_w, tile_h, _ptr(vals), vals.numel(), _ptr(d_num_pairs),
+                          tile_w, tile_h, int(tile_cull), _ptr(vals), vals.numel(), _ptr(d_num_pairs),
                           _ptr(tile_ranges), _ptr(workspace), workspace.numel(), _stream(stream)),
            "lgs_bin_sort")
 

@@ -36,8 +36,8 @@ lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t st
                      const int32_t *d_V, int64_t max_rows, cudaStream_t s);
 size_t bin_sort_workspace_size(int64_t maxV, int64_t cap, int ntiles);
 lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, const lgs_camera *cam,
-                    int tw, int th, uint32_t *vals, int64_t cap, int64_t *d_P, uint32_t *ranges,
-                    void *ws, cudaStream_t s);
+                    int tw, int th, int cull, uint32_t *vals, int64_t cap, int64_t *d_P,
+                    uint32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t s);
 lgs_status get_overflow(int64_t *needed);
 lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
                       const lgs_camera *cam, int tw, int th, float *image, float *finalT,
@@ -185,16 +185,21 @@ size_t lgs_bin_sort_workspace_size(int64_t max_splats, int64_t pair_capacity, in
 }
 
 lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int64_t max_splats,
-                        const lgs_camera *cam, int32_t tile_w, int32_t tile_h, uint32_t *vals,
-                        int64_t pair_capacity, int64_t *d_num_pairs, uint32_t *tile_ranges,
-                        void *workspace, size_t workspace_bytes, lgs_stream stream) {
+                        const lgs_camera *cam, int32_t tile_w, int32_t tile_h, int32_t tile_cull,
+                        uint32_t *vals, int64_t pair_capacity, int64_t *d_num_pairs,
+                        uint32_t *tile_ranges, void *workspace, size_t workspace_bytes,
+                        lgs_stream stream) {
     if (bad_camera(cam) || bad_splats(sp, max_splats) || bad_tiles(cam, tile_w, tile_h) ||
+        (tile_cull != 0 && tile_cull != 1) ||
         !vals || !d_num_pairs || !tile_ranges || max_splats <= 0 || max_splats > 0x7fffffffLL ||
-        pair_capacity <= 0 || pair_capacity > 0xffffffffLL || !workspace ||
-        workspace_bytes < bin_sort_workspace_size(max_splats, pair_capacity, 0))
+        pair_capacity <= 0 || pair_capacity > 0xffffffffLL || !workspace)
         return LGS_ERR_INVALID_ARG;
-    return bin_sort(sp, d_num_visible, max_splats, cam, tile_w, tile_h, vals, pair_capacity,
-                    d_num_pairs, tile_ranges, workspace, as_stream(stream));
+    const int ntiles = (int)(ceil_div(cam->width, tile_w) * ceil_div(cam->height, tile_h));
+    if (workspace_bytes < bin_sort_workspace_size(max_splats, pair_capacity, ntiles))
+        return LGS_ERR_INVALID_ARG;
+    return bin_sort(sp, d_num_visible, max_splats, cam, tile_w, tile_h, tile_cull, vals,
+                    pair_capacity, d_num_pairs, tile_ranges, workspace, workspace_bytes,
+                    as_stream(stream));
 }
 
 lgs_status lgs_get_overflow(int64_t *needed) { return get_overflow(needed); }

@@ -68,6 +68,50 @@ __device__ __forceinline__ int4 tile_rect(float u, float v, float r, int tw, int
     return make_int4((int)x0, (int)y0, (int)x1, (int)y1);
 }
 
+// A*dx^2 + 2*B*dx*dy + C*dy^2 with a fixed rounding order.
+__device__ __forceinline__ float quad_form(float A, float B, float C, float dx, float dy) {
+    const float t1 = __fmul_rn(__fmul_rn(A, dx), dx);
+    const float t2 = __fmul_rn(__fmul_rn(__fmul_rn(B, dx), dy), 2.0f);
+    const float t3 = __fmul_rn(__fmul_rn(C, dy), dy);
+    return __fadd_rn(__fadd_rn(t1, t2), t3);
+}
+
+// Whether a box of pixel centres [xl, xh] x [yl, yh] can receive a
+// contribution from a splat: the minimum of the conic's quadratic form
+// q(d) = d^T [[A, B], [B, C]] d over the box (d = splat centre - pixel
+// centre) is at most tau, where tau bounds q at alpha = 1/255
+// (alpha = o exp(-q / 2)). The minimum is 0 if the box holds the centre,
+// else it lies on an edge at the clamped one-dimensional minimiser
+// (-B dx / C on an edge of constant dx; rA = 1/A and rC = 1/C, correctly
+// rounded). Single precision, explicit rounding.
+__device__ __forceinline__ bool box_reachable(float u, float v, float A, float B, float C,
+                                              float rA, float rC, float tau, float xl, float xh,
+                                              float yl, float yh) {
+    const float ax = __fsub_rn(u, xh), bx = __fsub_rn(u, xl);
+    const float ay = __fsub_rn(v, yh), by = __fsub_rn(v, yl);
+    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return true;
+    float d, q;
+    d = fminf(fmaxf(-__fmul_rn(__fmul_rn(B, ax), rC), ay), by);
+    q = quad_form(A, B, C, ax, d);
+    d = fminf(fmaxf(-__fmul_rn(__fmul_rn(B, bx), rC), ay), by);
+    q = fminf(q, quad_form(A, B, C, bx, d));
+    d = fminf(fmaxf(-__fmul_rn(__fmul_rn(B, ay), rA), ax), bx);
+    q = fminf(q, quad_form(A, B, C, d, ay));
+    d = fminf(fmaxf(-__fmul_rn(__fmul_rn(B, by), rA), ax), bx);
+    q = fminf(q, quad_form(A, B, C, d, by));
+    return q <= tau;
+}
+
+// The same test for tile (tx, ty): its pixel centres span
+// [tx tw + 0.5, tx tw + tw - 0.5] x [ty th + 0.5, ty th + th - 0.5].
+__device__ __forceinline__ bool tile_reachable(float u, float v, float A, float B, float C,
+                                               float rA, float rC, float tau, int tx, int ty,
+                                               int tw, int th) {
+    const float xl = __fadd_rn((float)(tx * tw), 0.5f), xh = __fadd_rn((float)(tx * tw + tw), -0.5f);
+    const float yl = __fadd_rn((float)(ty * th), 0.5f), yh = __fadd_rn((float)(ty * th + th), -0.5f);
+    return box_reachable(u, v, A, B, C, rA, rC, tau, xl, xh, yl, yh);
+}
+
 // ---------------------------------------------------------------------------
 // host-side building blocks implemented in sort.cu
 // ---------------------------------------------------------------------------

@@ -257,9 +257,14 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
         sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], Y);
         color_forward<DEG>(P, stride, row, Y, raw);
         const float o = 1.0f / (1.0f + expf(-f.logit));
+        // tau: the largest q = d^T conic d at which alpha = o exp(-q/2) can
+        // still reach 1/255, widened by 1e-3 (1 + |tau|), far above the
+        // rounding of the kernels' alpha and of the tile test
+        const float t = 2.0f * logf(255.0f * o);
+        const float tau = t > -1e30f ? t + 1e-3f * (1.0f + fabsf(t)) : -INFINITY;
         r4[0] = make_float4(f.u, f.v, f.A, f.B);
         r4[1] = make_float4(f.C, o, fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f));
-        r4[2] = make_float4(fmaxf(raw[2], 0.f), 0.f, 0.f, 0.f);
+        r4[2] = make_float4(fmaxf(raw[2], 0.f), tau, 0.f, 0.f);
         depth[j] = f.pz;
         radius[j] = f.radius;
     }
@@ -272,12 +277,15 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
 // ---------------------------------------------------------------------------
 template <int DEG, typename Sink>
 __device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__ P, int64_t stride,
-                                         int64_t row, const float *__restrict__ g16, Sink &sink) {
+                                         int64_t row, const float *__restrict__ g16, Sink &sink,
+                                         float *dir_out = nullptr, float *grgb_out = nullptr) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
     Fwd f;
     if (!geom_forward(K, P, stride, row, f)) {
 #pragma unroll
         for (int k = 0; k < 11 + 3 * KK; ++k) sink(k, 0.0f);
+        if (grgb_out) grgb_out[0] = grgb_out[1] = grgb_out[2] = 0.0f;
+        if (dir_out) dir_out[0] = dir_out[1] = dir_out[2] = 0.0f;
         return false;
     }
     const float4 ga = reinterpret_cast<const float4 *>(g16)[0];
@@ -387,6 +395,16 @@ __device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__
     color_forward<DEG>(P, stride, row, Y, raw);
     const float grgb[3] = {raw[0] > 0.f ? gb.z : 0.f, raw[1] > 0.f ? gb.w : 0.f,
                            raw[2] > 0.f ? gc.x : 0.f};
+    if (grgb_out) {
+        grgb_out[0] = grgb[0];
+        grgb_out[1] = grgb[1];
+        grgb_out[2] = grgb[2];
+    }
+    if (dir_out) {
+        dir_out[0] = f.dir[0];
+        dir_out[1] = f.dir[1];
+        dir_out[2] = f.dir[2];
+    }
     float wk[16];
 #pragma unroll
     for (int k = 0; k < KK; ++k) {
@@ -442,22 +460,20 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__rest
 }
 
 // Fused backward + Adam in two passes over the visible Gaussians.
-// Part A: the gradients of every geometric plane; Adam on planes 3..10
-// (scales, rotation, opacity) at once. The centre's gradient (including its
-// colour part, through the view direction and the SH coefficients as they
-// were before this step) is parked in slots 12..14 of the Gaussian's
-// gradient row, slot 15 = 1 if the Gaussian is culled.
+// Part A (one thread per Gaussian): the gradients of the geometric planes
+// 0..10 (centre, scales, rotation, opacity) applied by Adam at once. The SH
+// planes' gradients are (colour gradient masked by the clamp) x Y_k(view
+// direction); part A leaves the masked colour gradient in slots 6..8 and the
+// view direction in slots 12..14 of the Gaussian's gradient row (zeros if
+// the Gaussian is culled).
 struct GeomSink {
     float *__restrict__ P;
     float *__restrict__ M;
     float *__restrict__ V;
-    float *__restrict__ slots;
     int64_t stride, row;
     const AdamArgs *a;
     __device__ __forceinline__ void operator()(int k, float g) {
-        if (k < 3) {
-            slots[k] = g;
-        } else if (k < 11) {
+        if (k < 11) {
             const int64_t i = k * stride + row;
             float p = P[i], m = M[i], v = V[i];
             adam_update(p, m, v, g, a->lr[k], *a);
@@ -477,60 +493,61 @@ __global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = map ? map[j] : j;
-        float *slots = gacc + 16 * j + 12;
-        GeomSink sink{P, Mo, Vo, slots, stride, row, &a};
-        const bool live = backward<DEG>(K, P, stride, row, gacc + 16 * j, sink);
-        slots[3] = live ? 0.0f : 1.0f;
+        float *g16 = gacc + 16 * j;
+        GeomSink sink{P, Mo, Vo, stride, row, &a};
+        float dir[3], grgb[3];
+        backward<DEG>(K, P, stride, row, g16, sink, dir, grgb);
+        g16[6] = grgb[0];
+        g16[7] = grgb[1];
+        g16[8] = grgb[2];
+        g16[12] = dir[0];
+        g16[13] = dir[1];
+        g16[14] = dir[2];
     }
 }
 
-// Part B: Adam on the SH planes and the centre. The direction, the basis Y
-// and the colour clamp are recomputed from the centre and coefficients, which
-// part A left untouched; then the SH planes stream through Adam and the
-// centre takes the gradient part A parked.
+// Part B: Adam on the SH planes, one thread per (Gaussian, group of up to 4
+// coefficients), groups outermost so that a warp streams consecutive rows
+// of the same planes.
 template <int DEG>
 __global__ void __launch_bounds__(256) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
                                                     float *__restrict__ Vo, int64_t stride,
                                                     int64_t n, const uint32_t *__restrict__ map,
-                                                    const int32_t *d_V, Cam K,
+                                                    const int32_t *d_V,
                                                     const float *__restrict__ gacc, AdamArgs a) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
+    constexpr int NG = (KK + 3) / 4;
     const int64_t V = load_count(d_V, n);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
-         j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t total = V * NG;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int grp = (int)(t / V);
+        const int64_t j = t - (int64_t)grp * V;
         const int64_t row = map ? map[j] : j;
-        const float4 gs = *reinterpret_cast<const float4 *>(gacc + 16 * j + 12);
-        const float *g8 = gacc + 16 * j;
-        const float dx = P[row] - K.cc[0], dy = P[stride + row] - K.cc[1],
-                    dz = P[2 * stride + row] - K.cc[2];
-        const float dinv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-        float Y[16], raw[3];
-        sh_basis(DEG, dx * dinv, dy * dinv, dz * dinv, Y);
-        color_forward<DEG>(P, stride, row, Y, raw);
-        const bool live = gs.w == 0.0f;
-        const float grgb[3] = {live && raw[0] > 0.f ? g8[6] : 0.f, live && raw[1] > 0.f ? g8[7] : 0.f,
-                               live && raw[2] > 0.f ? g8[8] : 0.f};
+        const float *g16 = gacc + 16 * j;
+        const float4 d4 = *reinterpret_cast<const float4 *>(g16 + 12);
+        const float gr[3] = {g16[6], g16[7], g16[8]};
+        float Y[16];
+        sh_basis(DEG, d4.x, d4.y, d4.z, Y);
 #pragma unroll
-        for (int k = 0; k < KK; ++k)
+        for (int q = 0; q < 4; ++q) {
+            const int k = 4 * grp + q;
+            if (k < KK) {
+                float yk = Y[0];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const int pl = 11 + 3 * k + ch;
-                const int64_t i = pl * stride + row;
-                float p = P[i], m = Mo[i], v = Vo[i];
-                adam_update(p, m, v, grgb[ch] * Y[k], a.lr[pl], a);
-                P[i] = p;
-                Mo[i] = m;
-                Vo[i] = v;
+                for (int c = 1; c < KK; ++c)
+                    if (c == k) yk = Y[c];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const int pl = 11 + 3 * k + ch;
+                    const int64_t i = pl * stride + row;
+                    float p = P[i], m = Mo[i], v = Vo[i];
+                    adam_update(p, m, v, gr[ch] * yk, a.lr[pl], a);
+                    P[i] = p;
+                    Mo[i] = m;
+                    Vo[i] = v;
+                }
             }
-        const float gm[3] = {gs.x, gs.y, gs.z};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int64_t i = k * stride + row;
-            float p = P[i], m = Mo[i], v = Vo[i];
-            adam_update(p, m, v, gm[k], a.lr[k], a);
-            P[i] = p;
-            Mo[i] = m;
-            Vo[i] = v;
         }
     }
 }
@@ -600,23 +617,24 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
                                cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
-    const unsigned ga = grid_for(g->n, kThreads, 16), gb = grid_for(g->n, 256, 8);
+    const int ng = ((g->sh_degree + 1) * (g->sh_degree + 1) + 3) / 4;
+    const unsigned ga = grid_for(g->n, kThreads, 16), gb = grid_for(g->n * ng, 256, 16);
     switch (g->sh_degree) {
     case 0:
         count_launch(); k_bwd_adam_geom<0><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<0><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<0><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     case 1:
         count_launch(); k_bwd_adam_geom<1><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<1><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<1><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     case 2:
         count_launch(); k_bwd_adam_geom<2><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<2><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<2><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     default:
         count_launch(); k_bwd_adam_geom<3><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<3><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<3><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     }
     return check_launch();

@@ -154,17 +154,20 @@ def test_cluster_cull_compact_matches_oracle(orc, gen):
 # ---------------------------------------------------------------------------
 # a4 bin sort
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("cull", [0, 1])
 @pytest.mark.parametrize("n,W,H,tile", [(4096, 128, 128, (16, 16)), (50000, 1297, 840, (16, 16)),
                                         (3000, 200, 77, (16, 16)), (1, 64, 64, (16, 16)),
                                         (20000, 1600, 1063, (16, 16))])
-def test_bin_sort_bit_exact(orc, n, W, H, tile):
+def test_bin_sort_bit_exact(orc, n, W, H, tile, cull):
     s = U.random_splat_dict(n, 10 + n, W, H, max_radius=40)
     s["radius"][::13] = 0
-    vals, ranges, P = U.gpu_bin(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H, tile)
-    rv, rr, rP = orc.bin_splats(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H, tile)
+    s["tau"][::17] = -np.inf                        # splats that reach no pixel
+    vals, ranges, P = U.gpu_bin(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H, tile,
+                                conic=s["conic"], tau=s["tau"], cull=cull)
+    rv, rr, rP = orc.bin_splats(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H, tile,
+                                conic=s["conic"], tau=s["tau"], cull=bool(cull))
     assert P == rP
-    np.testing.assert_array_equal(ranges, rr)
-    np.testing.assert_array_equal(vals, rv)
+    U.assert_same_tile_lists(vals, ranges, rv, rr)
 
 
 def test_bin_sort_empty_and_device_count(orc):
@@ -177,8 +180,7 @@ def test_bin_sort_empty_and_device_count(orc):
     vals, ranges, P = U.gpu_bin(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], 300, 200, V=V)
     rv, rr, rP = orc.bin_splats(s["uv"][:V, 0], s["uv"][:V, 1], s["radius"][:V], s["depth"][:V], 300, 200)
     assert P == rP
-    np.testing.assert_array_equal(vals, rv)
-    np.testing.assert_array_equal(ranges, rr)
+    U.assert_same_tile_lists(vals, ranges, rv, rr)
 
 
 def test_bin_sort_overflow_is_reported(orc):
@@ -208,9 +210,10 @@ def _raster_case(orc, sp, cam, tile=(16, 16), seed=0, min_ok=0.995):
     W, H = cam["width"], cam["height"]
     w = np.random.default_rng(seed).standard_normal((3, H, W)).astype(np.float32) * 1e-3
     g = U.gpu_raster(sp, cam, tile, dLdI=w)
-    vals, ranges, P = orc.bin_splats(sp["uv"][:, 0], sp["uv"][:, 1], sp["radius"], sp["depth"], W, H, tile)
+    vals, ranges, P = orc.bin_splats(sp["uv"][:, 0], sp["uv"][:, 1], sp["radius"], sp["depth"], W, H,
+                                     tile, conic=sp["conic"], tau=sp["tau"])
     assert g["P"] == P
-    np.testing.assert_array_equal(g["vals"], vals)
+    U.assert_same_tile_lists(g["vals"], g["ranges"], vals, ranges)
     o = orc.render_fwd(sp, vals, ranges, cam, tile)
     ok = o["pixflags"] == 0
     assert ok.mean() > min_ok, ok.mean()
@@ -229,6 +232,33 @@ def _raster_case(orc, sp, cam, tile=(16, 16), seed=0, min_ok=0.995):
     np.testing.assert_array_equal(g["C"][sok], ob["C"][sok])
     assert (g["pad"] == 0).all()
     return g, o, ob
+
+
+def test_tile_culling_keeps_the_image_bit_identical(orc):
+    cam = scenegen.pinhole_camera(320, 240, 320.0, bg=(0.2, 0.3, 0.1))
+    sp = U.random_splat_dict(20000, 25, 320, 240, max_radius=40)
+    w = np.random.default_rng(26).standard_normal((3, 240, 320)).astype(np.float32) * 1e-3
+    a = U.gpu_raster(sp, cam, dLdI=w, cull=0)
+    b = U.gpu_raster(sp, cam, dLdI=w, cull=1)
+    assert b["P"] < 0.8 * a["P"]
+    np.testing.assert_array_equal(a["image"], b["image"])
+    np.testing.assert_array_equal(a["T"], b["T"])
+    # the last contributor is the same splat (list positions differ)
+    def last_id(g):
+        out = np.full(g["last"].shape, -1, np.int64)
+        gx = -(-320 // 16)
+        for t in range(g["ranges"].shape[0]):
+            ty, tx = divmod(t, gx)
+            blk = g["last"][ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
+            m = blk > 0
+            ids = np.full(blk.shape, -1, np.int64)
+            ids[m] = g["vals"][g["ranges"][t, 0] + blk[m] - 1]
+            out[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = ids
+        return out
+    np.testing.assert_array_equal(last_id(a), last_id(b))
+    for q in range(9):
+        assert U.rel_l2(b["grad9"][:, q], a["grad9"][:, q]) < 1e-5
+    np.testing.assert_array_equal(a["C"], b["C"])
 
 
 def test_raster_random_splats(orc, shared_margins):

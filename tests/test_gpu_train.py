@@ -80,7 +80,24 @@ def oracle_step(orc, scene, cam, target, tile=(16, 16), step=1, lr=None):
     bad |= r["pixflags"] != 0
     return {"perm": perm, "map": rows, "V": cc["V"], "image": r["image"], "loss": L, "grads": grads,
             "params": newp, "m": m, "v": v, "metric": metric, "bad": bad, "planes0": planes,
-            "sflags": bw["sflags"], "last": r["last"]}
+            "sflags": bw["sflags"], "last": last_rows(r["last"], r["vals"], r["ranges"], rows, tile)}
+
+
+def last_rows(last, vals, ranges, rowmap, tile=(16, 16)):
+    """Gaussian row of each pixel's last composited splat (-1: none); list
+    positions depend on the tile culling, the splat does not."""
+    H, W = last.shape
+    tw, th = tile
+    gx = -(-W // tw)
+    out = np.full((H, W), -1, np.int64)
+    for t in range(ranges.shape[0]):
+        ty, tx = divmod(t, gx)
+        blk = last[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw]
+        m = blk > 0
+        ids = np.full(blk.shape, -1, np.int64)
+        ids[m] = np.asarray(rowmap)[vals[ranges[t, 0] + blk[m] - 1]]
+        out[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw] = ids
+    return out
 
 
 def _run_gpu_step(scene, cam, target, fused, tile=(16, 16)):
@@ -94,7 +111,9 @@ def _run_gpu_step(scene, cam, target, fused, tile=(16, 16)):
            "image": tr.image.cpu().numpy(), "loss": float(tr.loss.item()),
            "params": tr.params.cpu().numpy()[:, :n].astype(np.float64),
            "m": tr.m.cpu().numpy()[:, :n], "v": tr.v.cpu().numpy()[:, :n],
-           "metric": tr.metric.cpu().numpy(), "last": tr.last.cpu().numpy(), "lr": tr.lr}
+           "metric": tr.metric.cpu().numpy(), "lr": tr.lr}
+    out["last"] = last_rows(tr.last.cpu().numpy(), tr.vals.cpu().numpy().view(np.uint32),
+                            tr.ranges.cpu().numpy().view(np.uint32), out["map"], tile)
     if not fused:
         out["grads"] = tr.grad_planes.cpu().numpy()[:, :n]
     return out

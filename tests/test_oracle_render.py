@@ -190,3 +190,44 @@ def test_binning_matches_brute_force(orc, tile):
         assert list(vals[a:b]) == members
         total += len(members)
     assert total == P
+
+
+def _tau(opacity):
+    t = 2.0 * np.log(255.0 * np.asarray(opacity, np.float64))
+    return np.where(t > -1e30, t + 1e-3 * (1.0 + np.abs(t)), -np.inf).astype(np.float32)
+
+
+def test_tile_culling_keeps_every_contributing_pair(orc):
+    # App. A.1 tile-level culling: a tile is dropped only if no pixel centre
+    # in it can reach alpha >= 1/255. Brute force over every pixel centre of
+    # every tile of every rectangle, in double precision.
+    W, H, tw = 96, 80, 16
+    s = scenegen.random_splats(300, 9, W, H, max_radius=30)
+    tau = _tau(s["opacity"])
+    full = orc.bin_splats(s["u"], s["v"], s["radius"], s["depth"], W, H)
+    cull = orc.bin_splats(s["u"], s["v"], s["radius"], s["depth"], W, H, conic=s["conic"], tau=tau)
+    gx, gy = W // tw, H // tw
+    listed = set()
+    for t in range(gx * gy):
+        for j in cull[0][cull[1][t, 0]:cull[1][t, 1]]:
+            listed.add((int(j), t))
+    pairs_full = {(int(j), t) for t in range(gx * gy) for j in full[0][full[1][t, 0]:full[1][t, 1]]}
+    assert listed <= pairs_full
+    A, B, C = (s["conic"][:, k].astype(np.float64) for k in range(3))
+    for (j, t) in pairs_full:
+        tx, ty = t % gx, t // gx
+        px, py = np.meshgrid(tx * tw + np.arange(tw) + 0.5, ty * tw + np.arange(tw) + 0.5)
+        dx, dy = float(s["u"][j]) - px, float(s["v"][j]) - py
+        a = float(s["opacity"][j]) * np.exp(-0.5 * (A[j] * dx * dx + C[j] * dy * dy) - B[j] * dx * dy)
+        if (a >= 1.0 / 255.0).any():
+            assert (j, t) in listed, (j, t)
+    assert len(listed) < 0.9 * len(pairs_full)   # the rectangles over-cover
+
+
+def test_tile_culling_leaves_the_image_unchanged(orc):
+    d = scenegen.uniform_box_scene(3000, 1, 13, 96, 96, focal=96.0)
+    a = orc.render_scene(d["scene"], d["camera"], cull=False)
+    b = orc.render_scene(d["scene"], d["camera"], cull=True)
+    np.testing.assert_array_equal(a["image"], b["image"])
+    np.testing.assert_array_equal(a["T"], b["T"])
+    assert b["P"] < a["P"]
