@@ -242,6 +242,18 @@ lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int6
  * clears the flag), else LGS_OK with *needed = 0. */
 lgs_status lgs_get_overflow(int64_t *needed);
 
+/* Arithmetic of the per-pixel blend in lgs_raster_fwd / lgs_raster_bwd.
+ * LGS_FP32: everything in FP32. LGS_MIXED_FP16 / LGS_MIXED_BF16 (the
+ * mixed-precision raster of Sec. 3.1, with BF16 as a second 16-bit type):
+ * the Gaussian value G = exp(power), o G and alpha are computed in 16 bits
+ * for pairs of pixels; the exponent's quadratic form (from the FP32 inverse
+ * covariance), transmittance, colour accumulation and every gradient sum stay
+ * FP32. A backward must use the precision of the forward whose final_T and
+ * last_contrib it reads. */
+#define LGS_FP32 0
+#define LGS_MIXED_FP16 1
+#define LGS_MIXED_BF16 2
+
 /* ------------------------------------------------------------------------
  * a5. Forward rasterisation (Eq. 1-2, Alg. 1). Per pixel, front to back
  * over its tile's list: alpha = min(0.99, o exp(-0.5 (A dx^2 + C dy^2) -
@@ -250,12 +262,13 @@ lgs_status lgs_get_overflow(int64_t *needed);
  * colour += c alpha T and T *= 1 - alpha. image = colour + T bg.
  * Outputs (device): image [3][H][W]; final_T [H][W]; last_contrib [H][W] =
  * 1 + position within the tile list of the last composited splat (0: none).
- * tile_w x tile_h must be 16 x 16.
+ * tile_w x tile_h must be 16 x 16. precision: LGS_FP32, LGS_MIXED_FP16 or
+ * LGS_MIXED_BF16.
  * ---------------------------------------------------------------------- */
 lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
                           const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
-                          int32_t tile_h, float *image, float *final_T, int32_t *last_contrib,
-                          lgs_stream stream);
+                          int32_t tile_h, int32_t precision, float *image, float *final_T,
+                          int32_t *last_contrib, lgs_stream stream);
 
 /* ------------------------------------------------------------------------
  * a6. L1 photometric loss (the paper does not state its loss; this is the
@@ -281,12 +294,13 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
  *   11 C = count of included fragments as uint32, 12..15 zero (slots 6..8
  *   and 12..14 are rewritten by lgs_preprocess_bwd_adam).
  * accumulate = 0 zeroes rows j < max_splats first; 1 adds to them.
+ * precision must be the one the forward used.
  * ---------------------------------------------------------------------- */
 lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
                           const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
-                          int32_t tile_h, const float *final_T, const int32_t *last_contrib,
-                          const float *dL_dimage, float *grad_acc, int64_t max_splats,
-                          int32_t accumulate, lgs_stream stream);
+                          int32_t tile_h, int32_t precision, const float *final_T,
+                          const int32_t *last_contrib, const float *dL_dimage, float *grad_acc,
+                          int64_t max_splats, int32_t accumulate, lgs_stream stream);
 
 /* ------------------------------------------------------------------------
  * a8. Densification metric (Sec. 3.3): C Var = S - M^2 / C (0 if C = 0) for

@@ -16,6 +16,7 @@ from . import build as _build
 
 LGS_OK, LGS_ERR_INVALID_ARG, LGS_ERR_CAPACITY, LGS_ERR_CUDA, LGS_ERR_TIMEOUT = 0, 1, 2, 3, 4
 LGS_ERR_TOO_LARGE = 5
+LGS_FP32, LGS_MIXED_FP16, LGS_MIXED_BF16 = 0, 1, 2
 NOALLOC_MAX_CLUSTERS = 65536
 SPLAT_FLOATS = 12
 GRAD_FLOATS = 16
@@ -89,9 +90,9 @@ def load(build_if_missing: bool = True):
         "lgs_bin_sort_workspace_size": (sz, [i64, i64, i32]),
         "lgs_bin_sort": (i32, [P, P, i64, P, i32, i32, i32, P, i64, P, P, P, sz, P]),
         "lgs_get_overflow": (i32, [P]),
-        "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, P, P, P, P]),
+        "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P]),
         "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
-        "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, P, P, P, P, i64, i32, P]),
+        "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P, i64, i32, P]),
         "lgs_opacity_variance": (i32, [P, P, P, i64, P, P]),
         "lgs_preprocess_bwd": (i32, [P, P, P, P, P, P, P]),
         "lgs_adam_step": (i32, [P, P, P, P, i64, i32, P, f32, f32, f32, i32, P, P, i64, P]),
@@ -251,11 +252,11 @@ def lgs_get_overflow() -> int:
 
 
 def lgs_raster_fwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h, image,
-                   final_T, last_contrib, stream=None):
+                   final_T, last_contrib, stream=None, precision=LGS_FP32):
     L = load()
     _check(L.lgs_raster_fwd(ctypes.byref(sp), _ptr(vals), _ptr(tile_ranges), ctypes.byref(cam),
-                            tile_w, tile_h, _ptr(image), _ptr(final_T), _ptr(last_contrib),
-                            _stream(stream)), "lgs_raster_fwd")
+                            tile_w, tile_h, int(precision), _ptr(image), _ptr(final_T),
+                            _ptr(last_contrib), _stream(stream)), "lgs_raster_fwd")
 
 
 def lgs_loss_l1(image, target, dL_dimage, d_loss, stream=None):
@@ -265,12 +266,13 @@ def lgs_loss_l1(image, target, dL_dimage, d_loss, stream=None):
 
 
 def lgs_raster_bwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h, final_T,
-                   last_contrib, dL_dimage, grad_acc, accumulate=False, stream=None):
+                   last_contrib, dL_dimage, grad_acc, accumulate=False, stream=None,
+                   precision=LGS_FP32):
     L = load()
     _check(L.lgs_raster_bwd(ctypes.byref(sp), _ptr(vals), _ptr(tile_ranges), ctypes.byref(cam),
-                            tile_w, tile_h, _ptr(final_T), _ptr(last_contrib), _ptr(dL_dimage),
-                            _ptr(grad_acc), grad_acc.shape[0], int(bool(accumulate)),
-                            _stream(stream)), "lgs_raster_bwd")
+                            tile_w, tile_h, int(precision), _ptr(final_T), _ptr(last_contrib),
+                            _ptr(dL_dimage), _ptr(grad_acc), grad_acc.shape[0],
+                            int(bool(accumulate)), _stream(stream)), "lgs_raster_bwd")
 
 
 def lgs_opacity_variance(grad_acc, map_, d_num_visible, max_rows, metric, stream=None):

@@ -40,10 +40,10 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
                     uint32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t s);
 lgs_status get_overflow(int64_t *needed);
 lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
-                      const lgs_camera *cam, int tw, int th, float *image, float *finalT,
-                      int32_t *last, cudaStream_t s);
+                      const lgs_camera *cam, int tw, int th, int precision, float *image,
+                      float *finalT, int32_t *last, cudaStream_t s);
 lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
-                      const lgs_camera *cam, int tw, int th, const float *finalT,
+                      const lgs_camera *cam, int tw, int th, int precision, const float *finalT,
                       const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
                       int accumulate, cudaStream_t s);
 lgs_status loss_l1(const float *img, const float *tgt, int64_t n, float *g, float *loss,
@@ -206,13 +206,14 @@ lgs_status lgs_get_overflow(int64_t *needed) { return get_overflow(needed); }
 
 lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
                           const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
-                          int32_t tile_h, float *image, float *final_T, int32_t *last_contrib,
-                          lgs_stream stream) {
+                          int32_t tile_h, int32_t precision, float *image, float *final_T,
+                          int32_t *last_contrib, lgs_stream stream) {
     if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !image || !final_T ||
-        !last_contrib || bad_tiles(cam, tile_w, tile_h))
+        !last_contrib || bad_tiles(cam, tile_w, tile_h) || precision < LGS_FP32 ||
+        precision > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
-    return raster_fwd(sp, vals, tile_ranges, cam, tile_w, tile_h, image, final_T, last_contrib,
-                      as_stream(stream));
+    return raster_fwd(sp, vals, tile_ranges, cam, tile_w, tile_h, precision, image, final_T,
+                      last_contrib, as_stream(stream));
 }
 
 lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float *dL_dimage,
@@ -223,15 +224,16 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
 
 lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
                           const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
-                          int32_t tile_h, const float *final_T, const int32_t *last_contrib,
-                          const float *dL_dimage, float *grad_acc, int64_t max_splats,
-                          int32_t accumulate, lgs_stream stream) {
+                          int32_t tile_h, int32_t precision, const float *final_T,
+                          const int32_t *last_contrib, const float *dL_dimage, float *grad_acc,
+                          int64_t max_splats, int32_t accumulate, lgs_stream stream) {
     if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !final_T ||
         !last_contrib || !dL_dimage || !grad_acc || !aligned16(grad_acc) || max_splats < 0 ||
-        bad_tiles(cam, tile_w, tile_h))
+        bad_tiles(cam, tile_w, tile_h) || precision < LGS_FP32 || precision > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
-    return raster_bwd(sp, vals, tile_ranges, cam, tile_w, tile_h, final_T, last_contrib, dL_dimage,
-                      grad_acc, max_splats, accumulate, as_stream(stream));
+    return raster_bwd(sp, vals, tile_ranges, cam, tile_w, tile_h, precision, final_T,
+                      last_contrib, dL_dimage, grad_acc, max_splats, accumulate,
+                      as_stream(stream));
 }
 
 lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,

@@ -1,12 +1,27 @@
 // Tile rasteriser, forward (Eq. 1-2, Alg. 1) and backward (Eq. 3, App. A.1
 // Eq. 4-6) with the opacity-gradient moments of Sec. 3.3.
 //
-// One CTA per 16 x 16 tile, one pixel per thread. The tile's sorted splats
-// are staged through shared memory in batches of 256 (one per thread). In
-// the backward each warp reduces the per-pixel terms of a splat across its
-// 32 pixels with a reduce-scatter butterfly (16 shuffles for 11 values,
-// ending with value i on lanes 2i, 2i+1), and lanes 0, 2, .., 20 issue one
-// atomic each: 11 adjacent floats of the splat's 64-byte gradient row.
+// One CTA of 4 warps per 16 x 16 tile; warp w owns the 8 x 8 quadrant w of
+// the tile and every thread a horizontal pair of pixels. The tile's sorted
+// splats are staged through shared memory 128 at a time (one per thread).
+// While staging, each thread tests its splat against the four quadrants
+// with the same conservative test the binning uses per tile (the minimum of
+// the exponent's quadratic form over the quadrant's pixel centres against
+// tau), so each warp walks only the splats that can reach its quadrant.
+// In the backward each thread first sums a splat's per-pixel terms over its
+// two pixels, the warp reduces the 12 sums with a reduce-scatter butterfly
+// (16 shuffles; value i ends on lanes 2i, 2i + 1) and lanes 0, 2, .., 22
+// issue one atomic each (App. A.1 Eq. 5-6: one atomic per value per warp).
+//
+// The exponent is power = dx (a dx + b dy) + c dy^2 with a = -A/2, b = -B,
+// c = -C/2, evaluated with explicitly rounded FP32 operations in one helper
+// shared by both passes, so the backward re-derives exactly the alphas the
+// forward composited. In the mixed-precision variants the Gaussian value G,
+// o G and alpha are computed for the pixel pair as one FP16x2 or BF16x2
+// value; the exponent (conic), transmittance, colour accumulators and
+// gradient sums stay FP32.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lgs_internal.cuh"
@@ -15,77 +30,183 @@ namespace lgs {
 
 namespace {
 
-constexpr int kTileW = 16, kTileH = 16;
-constexpr int kBlock = kTileW * kTileH;
+constexpr int kTile = 16;
+constexpr int kBatch = 128;  // threads per CTA = splats staged per round
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
 struct SplatS {
-    float u, v, A, B, C, o, r, g, b;
+    float u, v, a, b, c, o, r, g, bl;
+    uint32_t oh;  // o as a 16-bit pair (mixed precision only)
 };
 
 struct RCam {
-    int W, H, gx;
+    int W, H, gx, ntiles;
     float bg[3];
 };
 
-__device__ __forceinline__ void load_splat(const float *__restrict__ rec, uint32_t j, SplatS &s) {
-    const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)j);
-    const float4 a = p[0], b = p[1];
-    const float c = rec[12 * (int64_t)j + 8];
-    s.u = a.x; s.v = a.y; s.A = a.z; s.B = a.w;
-    s.C = b.x; s.o = b.y; s.r = b.z; s.g = b.w; s.b = c;
+template <int PREC>
+__device__ __forceinline__ uint32_t pack_pair(float x) {
+    if constexpr (PREC == LGS_MIXED_FP16) {
+        const __half2 h = __float2half2_rn(x);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    } else if constexpr (PREC == LGS_MIXED_BF16) {
+        const __nv_bfloat162 h = __float2bfloat162_rn(x);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    } else {
+        return 0u;
+    }
 }
 
-__global__ void __launch_bounds__(kBlock) k_raster_fwd(const float *__restrict__ rec,
-                                                      const uint32_t *__restrict__ vals,
-                                                      const uint32_t *__restrict__ ranges, RCam K,
-                                                      float *__restrict__ image,
-                                                      float *__restrict__ finalT,
-                                                      int32_t *__restrict__ last) {
-    __shared__ SplatS s_sp[kBlock];
-    const int tile = blockIdx.x;
-    const int tx = tile % K.gx, ty = tile / K.gx;
-    const int px = tx * kTileW + (threadIdx.x % kTileW), py = ty * kTileH + (threadIdx.x / kTileW);
-    const bool inside = px < K.W && py < K.H;
-    const float pxc = px + 0.5f, pyc = py + 0.5f;
-    const uint32_t r0 = ranges[2 * tile], r1 = ranges[2 * tile + 1];
-    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
-    int32_t lst = 0;
-    bool done = !inside;
-    for (uint32_t b0 = r0; b0 < r1; b0 += kBlock) {
-        if (__syncthreads_count(done) == kBlock) break;
-        const uint32_t idx = b0 + threadIdx.x;
-        if (idx < r1) load_splat(rec, vals[idx], s_sp[threadIdx.x]);
-        __syncthreads();
-        const int cnt = min((uint32_t)kBlock, r1 - b0);
-        for (int k = 0; k < cnt && !done; ++k) {
-            const SplatS &s = s_sp[k];
-            const float dx = s.u - pxc, dy = s.v - pyc;
-            const float power = -0.5f * (s.A * dx * dx + s.C * dy * dy) - s.B * dx * dy;
-            const float alpha = fminf(kAlphaMax, s.o * __expf(power));
-            if (alpha < kAlphaMin) continue;
-            const float Tn = T * (1.0f - alpha);
-            if (Tn < kTMin) {
-                done = true;
-                break;
-            }
-            const float w = alpha * T;
-            cr += s.r * w;
-            cg += s.g * w;
-            cb += s.b * w;
-            T = Tn;
-            lst = (int32_t)(b0 - r0) + k + 1;
-        }
+// Loads splat j into s and returns the 4-bit mask of the tile quadrants
+// (bit w: quadrant x0 + 8 (w & 1), y0 + 8 (w >> 1)) it may reach.
+template <int PREC>
+__device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_t j, float x0,
+                                          float y0, SplatS &s) {
+    const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)j);
+    const float4 x = __ldg(p), y = __ldg(p + 1);
+    const float2 z = __ldg(reinterpret_cast<const float2 *>(rec + 12 * (int64_t)j + 8));
+    s.u = x.x;
+    s.v = x.y;
+    s.a = -0.5f * x.z;
+    s.b = -x.w;
+    s.c = -0.5f * y.x;
+    s.o = y.y;
+    s.r = y.z;
+    s.g = y.w;
+    s.bl = z.x;
+    s.oh = pack_pair<PREC>(y.y);
+    const float rA = __frcp_rn(x.z), rC = __frcp_rn(y.x);
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const float xl = x0 + 8.0f * (w & 1), yl = y0 + 8.0f * (w >> 1);
+        if (box_reachable(x.x, x.y, x.z, x.w, y.x, rA, rC, z.y, xl, xl + 7.0f, yl, yl + 7.0f))
+            m |= 1u << w;
     }
-    if (inside) {
-        const int64_t p = (int64_t)py * K.W + px, hw = (int64_t)K.W * K.H;
-        image[p] = cr + T * K.bg[0];
-        image[hw + p] = cg + T * K.bg[1];
-        image[2 * hw + p] = cb + T * K.bg[2];
-        finalT[p] = T;
-        last[p] = lst;
+    return m;
+}
+
+// Exponent at two horizontally adjacent pixels of one row.
+__device__ __forceinline__ void power2(const SplatS &s, float fx, float fy, float &p0,
+                                       float &p1) {
+    const float dx0 = __fsub_rn(s.u, fx), dx1 = __fsub_rn(s.u, __fadd_rn(fx, 1.0f));
+    const float dy = __fsub_rn(s.v, fy);
+    const float bdy = __fmul_rn(s.b, dy), cdy2 = __fmul_rn(__fmul_rn(s.c, dy), dy);
+    p0 = __fmaf_rn(dx0, __fmaf_rn(s.a, dx0, bdy), cdy2);
+    p1 = __fmaf_rn(dx1, __fmaf_rn(s.a, dx1, bdy), cdy2);
+}
+
+// G = exp(power), alpha = min(0.99, o G) and whether the clamp is active,
+// for a pixel pair.
+template <int PREC>
+__device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, float &G0, float &G1,
+                                       float &a0, float &a1, bool &cl0, bool &cl1) {
+    if constexpr (PREC == LGS_FP32) {
+        G0 = __expf(p0);
+        G1 = __expf(p1);
+        const float q0 = s.o * G0, q1 = s.o * G1;
+        a0 = fminf(kAlphaMax, q0);
+        a1 = fminf(kAlphaMax, q1);
+        cl0 = q0 >= kAlphaMax;
+        cl1 = q1 >= kAlphaMax;
+    } else if constexpr (PREC == LGS_MIXED_FP16) {
+        const __half2 G = h2exp(__floats2half2_rn(p0, p1));
+        const __half2 q = __hmul2(*reinterpret_cast<const __half2 *>(&s.oh), G);
+        const __half2 cap = __float2half2_rn(kAlphaMax);
+        const float2 Gf = __half22float2(G), af = __half22float2(__hmin2(q, cap));
+        const __half2 ge = __hge2(q, cap);
+        G0 = Gf.x;
+        G1 = Gf.y;
+        a0 = af.x;
+        a1 = af.y;
+        cl0 = __low2float(ge) != 0.0f;
+        cl1 = __high2float(ge) != 0.0f;
+    } else {
+        const __nv_bfloat162 G = h2exp(__floats2bfloat162_rn(p0, p1));
+        const __nv_bfloat162 q = __hmul2(*reinterpret_cast<const __nv_bfloat162 *>(&s.oh), G);
+        const __nv_bfloat162 cap = __float2bfloat162_rn(kAlphaMax);
+        const float2 Gf = __bfloat1622float2(G), af = __bfloat1622float2(__hmin2(q, cap));
+        const __nv_bfloat162 ge = __hge2(q, cap);
+        G0 = Gf.x;
+        G1 = Gf.y;
+        a0 = af.x;
+        a1 = af.y;
+        cl0 = __low2float(ge) != 0.0f;
+        cl1 = __high2float(ge) != 0.0f;
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kBatch) k_raster_fwd(const float *__restrict__ rec,
+                                                     const uint32_t *__restrict__ vals,
+                                                     const uint32_t *__restrict__ ranges, RCam K,
+                                                     float *__restrict__ image,
+                                                     float *__restrict__ finalT,
+                                                     int32_t *__restrict__ last) {
+    __shared__ SplatS s_sp[kBatch];
+    __shared__ uint8_t s_fl[kBatch];
+    const int tile = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = tile % K.gx, ty = tile / K.gx;
+    const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
+    const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+    const float tx0 = (float)(tx * kTile) + 0.5f, ty0 = (float)(ty * kTile) + 0.5f;
+    const uint32_t r0 = ranges[2 * tile], r1 = ranges[2 * tile + 1];
+    float T[2] = {1.0f, 1.0f}, cr[2] = {0.f, 0.f}, cg[2] = {0.f, 0.f}, cb[2] = {0.f, 0.f};
+    int32_t lst[2] = {0, 0};
+    uint32_t live = (x < K.W && y < K.H ? 1u : 0u) | (x + 1 < K.W && y < K.H ? 2u : 0u);
+    for (uint32_t b0 = r0; b0 < r1; b0 += kBatch) {
+        if (__syncthreads_count(live != 0) == 0) break;
+        const uint32_t idx = b0 + threadIdx.x;
+        if (idx < r1) s_fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, vals[idx], tx0, ty0, s_sp[threadIdx.x]);
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)kBatch, r1 - b0);
+#pragma unroll 1
+        for (int q = 0; q < kBatch / 32; ++q) {
+            const int t = 32 * q + lane;
+            uint32_t m = __ballot_sync(0xffffffffu, t < cnt && ((s_fl[t] >> w) & 1u));
+            while (m && live) {
+                const int k = 32 * q + __ffs(m) - 1;
+                m &= m - 1;
+                const SplatS s = s_sp[k];
+                float p0, p1, G0, G1, a0, a1;
+                bool c0, c1;
+                power2(s, fx, fy, p0, p1);
+                blend2<PREC>(s, p0, p1, G0, G1, a0, a1, c0, c1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float a = h ? a1 : a0;
+                    if (((live >> h) & 1u) && a >= kAlphaMin) {
+                        const float Tn = T[h] * (1.0f - a);
+                        if (Tn < kTMin) {
+                            live &= ~(1u << h);
+                        } else {
+                            const float wgt = a * T[h];
+                            cr[h] = fmaf(s.r, wgt, cr[h]);
+                            cg[h] = fmaf(s.g, wgt, cg[h]);
+                            cb[h] = fmaf(s.bl, wgt, cb[h]);
+                            T[h] = Tn;
+                            lst[h] = (int32_t)(b0 - r0) + k + 1;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t hw = (int64_t)K.W * K.H;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (x + h < K.W && y < K.H) {
+            const int64_t p = (int64_t)y * K.W + x + h;
+            image[p] = cr[h] + T[h] * K.bg[0];
+            image[hw + p] = cg[h] + T[h] * K.bg[1];
+            image[2 * hw + p] = cb[h] + T[h] * K.bg[2];
+            finalT[p] = T[h];
+            last[p] = lst[h];
+        }
     }
 }
 
@@ -122,100 +243,136 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-__global__ void __launch_bounds__(kBlock) k_raster_bwd(
+template <int PREC>
+__global__ void __launch_bounds__(kBatch) k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ ranges, RCam K, const float *__restrict__ finalT,
     const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc) {
-    __shared__ SplatS s_sp[kBlock];
-    __shared__ uint32_t s_id[kBlock];
+    __shared__ SplatS s_sp[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ uint8_t s_fl[kBatch];
     __shared__ int s_maxlast;
     const int tile = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
-    const int lane = threadIdx.x & 31;
-    const int px = tx * kTileW + (threadIdx.x % kTileW), py = ty * kTileH + (threadIdx.x / kTileW);
-    const bool inside = px < K.W && py < K.H;
-    const float pxc = px + 0.5f, pyc = py + 0.5f;
+    const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
+    const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+    const float tx0 = (float)(tx * kTile) + 0.5f, ty0 = (float)(ty * kTile) + 0.5f;
     const uint32_t r0 = ranges[2 * tile];
-    const int64_t p = (int64_t)py * K.W + px, hw = (int64_t)K.W * K.H;
-    float T = 1.0f, gI[3] = {0.f, 0.f, 0.f};
-    int lst = 0;
-    if (inside) {
-        T = finalT[p];
-        lst = last[p];
-        gI[0] = dLdI[p];
-        gI[1] = dLdI[hw + p];
-        gI[2] = dLdI[2 * hw + p];
+    const int64_t hw = (int64_t)K.W * K.H;
+    // per pixel: transmittance (recovered back to front), dL/dI, T_final bg.dL/dI,
+    // and acc.dL/dI with acc the colour composited behind the current splat
+    float T[2], g0[2], g1[2], g2[2], bgT[2], accg[2];
+    int32_t lst[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        T[h] = 1.0f;
+        g0[h] = g1[h] = g2[h] = 0.0f;
+        lst[h] = 0;
+        if (x + h < K.W && y < K.H) {
+            const int64_t p = (int64_t)y * K.W + x + h;
+            T[h] = finalT[p];
+            lst[h] = last[p];
+            g0[h] = dLdI[p];
+            g1[h] = dLdI[hw + p];
+            g2[h] = dLdI[2 * hw + p];
+        }
+        bgT[h] = T[h] * (K.bg[0] * g0[h] + K.bg[1] * g1[h] + K.bg[2] * g2[h]);
+        accg[h] = 0.0f;
     }
-    const float Tf = T;
-    const float bgdot = K.bg[0] * gI[0] + K.bg[1] * gI[1] + K.bg[2] * gI[2];
+    const int32_t wmax = __reduce_max_sync(0xffffffffu, max(lst[0], lst[1]));
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
-    atomicMax(&s_maxlast, lst);
+    if (lane == 0) atomicMax(&s_maxlast, wmax);
     __syncthreads();
     const int maxlast = s_maxlast;
-    float acc[3] = {0.f, 0.f, 0.f}, pa = 0.f, prgb[3] = {0.f, 0.f, 0.f};
-    // positions maxlast-1 .. 0 of the tile list, in batches from the back
-    for (int end = maxlast; end > 0; end -= kBlock) {
-        const int cnt = min(kBlock, end);
+    // positions maxlast-1 .. 0 of the tile list, 128 at a time from the back
+    for (int end = maxlast; end > 0; end -= kBatch) {
+        const int cnt = min(kBatch, end);
         __syncthreads();
-        if (threadIdx.x < cnt) {
+        if ((int)threadIdx.x < cnt) {
             const uint32_t j = vals[r0 + end - 1 - threadIdx.x];
             s_id[threadIdx.x] = j;
-            load_splat(rec, j, s_sp[threadIdx.x]);
+            s_fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, j, tx0, ty0, s_sp[threadIdx.x]);
         }
         __syncthreads();
-        for (int k = 0; k < cnt; ++k) {
-            const int pos = end - 1 - k;
-            const SplatS &s = s_sp[k];
-            float v[16];
+#pragma unroll 1
+        for (int q = 0; q < kBatch / 32; ++q) {
+            const int t = 32 * q + lane;
+            uint32_t m = __ballot_sync(0xffffffffu, t < cnt && end - 1 - t < wmax &&
+                                                        ((s_fl[t] >> w) & 1u));
+            while (m) {
+                const int k = 32 * q + __ffs(m) - 1;
+                m &= m - 1;
+                const int pos = end - 1 - k;
+                const SplatS s = s_sp[k];
+                float v[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.f;
-            uint32_t contrib = 0;
-            if (pos < lst) {
-                const float dx = s.u - pxc, dy = s.v - pyc;
-                const float power = -0.5f * (s.A * dx * dx + s.C * dy * dy) - s.B * dx * dy;
-                const float G = __expf(power);
-                const float oG = s.o * G;
-                const float alpha = fminf(kAlphaMax, oG);
-                if (alpha >= kAlphaMin) {
-                    contrib = 1;
-                    const float om = 1.0f - alpha;
-                    const float Tk = T / om;
-                    // colour behind this splat, normalised by the transmittance after it
-                    acc[0] = pa * prgb[0] + (1.f - pa) * acc[0];
-                    acc[1] = pa * prgb[1] + (1.f - pa) * acc[1];
-                    acc[2] = pa * prgb[2] + (1.f - pa) * acc[2];
-                    const float dLda = Tk * ((s.r - acc[0]) * gI[0] + (s.g - acc[1]) * gI[1] +
-                                             (s.b - acc[2]) * gI[2]) -
-                                       Tf * bgdot / om;
-                    const float wT = alpha * Tk;
-                    v[6] = wT * gI[0];
-                    v[7] = wT * gI[1];
-                    v[8] = wT * gI[2];
-                    if (oG < kAlphaMax) {
-                        const float dLdo = G * dLda;
-                        const float dLdp = alpha * dLda;
-                        v[0] = -(s.A * dx + s.B * dy) * dLdp;
-                        v[1] = -(s.B * dx + s.C * dy) * dLdp;
-                        v[2] = -0.5f * dx * dx * dLdp;
-                        v[3] = -dx * dy * dLdp;
-                        v[4] = -0.5f * dy * dy * dLdp;
-                        v[5] = dLdo;
-                        v[9] = dLdo * dLdo;
-                        v[10] = dLdo;
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                float p0, p1, G0, G1, a0, a1;
+                bool c0, c1;
+                power2(s, fx, fy, p0, p1);
+                blend2<PREC>(s, p0, p1, G0, G1, a0, a1, c0, c1);
+                float gr = 0.f, gg = 0.f, gb = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f,
+                      syy = 0.f, dO = 0.f, S = 0.f, n = 0.f;
+                const float dy = __fsub_rn(s.v, fy);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float a = h ? a1 : a0;
+                    if (pos < lst[h] && a >= kAlphaMin) {
+                        const float G = h ? G1 : G0;
+                        const bool clamped = h ? c1 : c0;
+                        const float rom = __fdividef(1.0f, 1.0f - a);
+                        const float Tk = T[h] * rom;
+                        const float dd = s.r * g0[h] + s.g * g1[h] + s.bl * g2[h] - accg[h];
+                        const float dLda = Tk * dd - bgT[h] * rom;
+                        const float wT = a * Tk;
+                        gr = fmaf(wT, g0[h], gr);
+                        gg = fmaf(wT, g1[h], gg);
+                        gb = fmaf(wT, g2[h], gb);
+                        if (!clamped) {
+                            const float dx = __fsub_rn(s.u, __fadd_rn(fx, (float)h));
+                            const float dLdo = G * dLda, qq = a * dLda;
+                            dO += dLdo;
+                            S = fmaf(dLdo, dLdo, S);
+                            const float qx = dx * qq, qy = dy * qq;
+                            sx += qx;
+                            sy += qy;
+                            sxx = fmaf(dx, qx, sxx);
+                            sxy = fmaf(dy, qx, sxy);
+                            syy = fmaf(dy, qy, syy);
+                        }
+                        n += 1.0f;
+                        accg[h] = fmaf(a, dd, accg[h]);
+                        T[h] = Tk;
                     }
-                    T = Tk;
-                    pa = alpha;
-                    prgb[0] = s.r; prgb[1] = s.g; prgb[2] = s.b;
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float red = warp_reduce_scatter16(v, lane);
-                const uint32_t c = __reduce_add_sync(0xffffffffu, contrib);
-                float *row = gacc + 16 * (int64_t)s_id[k];
-                const int vi = lane >> 1;
-                if ((lane & 1) == 0 && vi < 11) atomicAdd(row + vi, red);
-                if (lane == 1) atomicAdd(reinterpret_cast<unsigned int *>(row + 11), c);
+                if (__any_sync(0xffffffffu, n != 0.0f)) {
+                    // -(A sx + B sy), -(B sx + C sy), -sxx/2, -sxy, -syy/2 with
+                    // A = -2a, B = -b, C = -2c
+                    v[0] = 2.0f * s.a * sx + s.b * sy;
+                    v[1] = s.b * sx + 2.0f * s.c * sy;
+                    v[2] = -0.5f * sxx;
+                    v[3] = -sxy;
+                    v[4] = -0.5f * syy;
+                    v[5] = dO;
+                    v[6] = gr;
+                    v[7] = gg;
+                    v[8] = gb;
+                    v[9] = S;
+                    v[10] = dO;
+                    v[11] = n;
+                    const float red = warp_reduce_scatter16(v, lane);
+                    float *row = gacc + 16 * (int64_t)s_id[k];
+                    const int vi = lane >> 1;
+                    if ((lane & 1) == 0) {
+                        if (vi < 11)
+                            atomicAdd(row + vi, red);
+                        else if (vi == 11)
+                            atomicAdd(reinterpret_cast<unsigned int *>(row + 11),
+                                      (unsigned int)(red + 0.5f));
+                    }
+                }
             }
         }
     }
@@ -232,8 +389,16 @@ __global__ void __launch_bounds__(256) k_loss_l1(const float *__restrict__ img,
         s += fabsf(d);
         g[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
     }
+    // block sum, then one atomic per block
+    __shared__ float s_part[8];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < 8 ? s_part[threadIdx.x] : 0.f;
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(loss, s * inv);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_variance(const float *__restrict__ gacc,
@@ -249,11 +414,12 @@ __global__ void __launch_bounds__(256) k_variance(const float *__restrict__ gacc
     }
 }
 
-RCam make_rcam(const lgs_camera *c, int tw) {
+RCam make_rcam(const lgs_camera *c, int tw, int th) {
     RCam k;
     k.W = c->width;
     k.H = c->height;
     k.gx = (int)ceil_div(c->width, tw);
+    k.ntiles = k.gx * (int)ceil_div(c->height, th);
     k.bg[0] = c->bg[0]; k.bg[1] = c->bg[1]; k.bg[2] = c->bg[2];
     return k;
 }
@@ -261,26 +427,49 @@ RCam make_rcam(const lgs_camera *c, int tw) {
 }  // namespace
 
 lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
-                      const lgs_camera *cam, int tw, int th, float *image, float *finalT,
-                      int32_t *last, cudaStream_t s) {
-    if (tw != kTileW || th != kTileH) return LGS_ERR_INVALID_ARG;
-    const RCam K = make_rcam(cam, tw);
-    const int ntiles = K.gx * (int)ceil_div(cam->height, th);
+                      const lgs_camera *cam, int tw, int th, int precision, float *image,
+                      float *finalT, int32_t *last, cudaStream_t s) {
+    if (tw != kTile || th != kTile) return LGS_ERR_INVALID_ARG;
+    const RCam K = make_rcam(cam, tw, th);
+    const unsigned grid = (unsigned)K.ntiles;
     count_launch();
-    k_raster_fwd<<<ntiles, kBlock, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+    switch (precision) {
+        case LGS_FP32:
+            k_raster_fwd<LGS_FP32><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+            break;
+        case LGS_MIXED_FP16:
+            k_raster_fwd<LGS_MIXED_FP16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+            break;
+        case LGS_MIXED_BF16:
+            k_raster_fwd<LGS_MIXED_BF16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+            break;
+        default:
+            return LGS_ERR_INVALID_ARG;
+    }
     return check_launch();
 }
 
 lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
-                      const lgs_camera *cam, int tw, int th, const float *finalT,
+                      const lgs_camera *cam, int tw, int th, int precision, const float *finalT,
                       const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
                       int accumulate, cudaStream_t s) {
-    if (tw != kTileW || th != kTileH) return LGS_ERR_INVALID_ARG;
+    if (tw != kTile || th != kTile) return LGS_ERR_INVALID_ARG;
+    if (precision < LGS_FP32 || precision > LGS_MIXED_BF16) return LGS_ERR_INVALID_ARG;
     if (!accumulate) cudaMemsetAsync(gacc, 0, (size_t)max_splats * 16 * sizeof(float), s);
-    const RCam K = make_rcam(cam, tw);
-    const int ntiles = K.gx * (int)ceil_div(cam->height, th);
+    const RCam K = make_rcam(cam, tw, th);
+    const unsigned grid = (unsigned)K.ntiles;
     count_launch();
-    k_raster_bwd<<<ntiles, kBlock, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
+    switch (precision) {
+        case LGS_FP32:
+            k_raster_bwd<LGS_FP32><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
+            break;
+        case LGS_MIXED_FP16:
+            k_raster_bwd<LGS_MIXED_FP16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
+            break;
+        default:
+            k_raster_bwd<LGS_MIXED_BF16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
+            break;
+    }
     return check_launch();
 }
 

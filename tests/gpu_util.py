@@ -103,7 +103,7 @@ def gpu_bin(u, v, radius, depth, W, H, tile=(16, 16), cap=None, V=None, conic=No
             P)
 
 
-def gpu_raster(sp: dict, cam: dict, tile=(16, 16), dLdI=None, cull=1):
+def gpu_raster(sp: dict, cam: dict, tile=(16, 16), dLdI=None, cull=1, precision=B.LGS_FP32):
     """Bin + forward (+ backward if dLdI is given) of float32 splats.
     sp: uv, conic, opacity, rgb, depth, radius, tau (float32 / int32)."""
     n = sp["uv"].shape[0]
@@ -123,12 +123,12 @@ def gpu_raster(sp: dict, cam: dict, tile=(16, 16), dLdI=None, cull=1):
     image = torch.zeros((3, H, W), dtype=torch.float32, device=DEV)
     T = torch.zeros((H, W), dtype=torch.float32, device=DEV)
     last = torch.zeros((H, W), dtype=torch.int32, device=DEV)
-    B.lgs_raster_fwd(spl, vals, ranges, cs, tile[0], tile[1], image, T, last)
+    B.lgs_raster_fwd(spl, vals, ranges, cs, tile[0], tile[1], image, T, last, precision=precision)
     out = {}
     if dLdI is not None:
         gacc = torch.zeros((max(n, 1), 16), dtype=torch.float32, device=DEV)
         B.lgs_raster_bwd(spl, vals, ranges, cs, tile[0], tile[1], T, last,
-                         t(np.asarray(dLdI, np.float32)), gacc)
+                         t(np.asarray(dLdI, np.float32)), gacc, precision=precision)
         torch.cuda.synchronize()
         ga = gacc.cpu().numpy()[:n]
         out.update(grad9=ga[:, :9], S=ga[:, 9], M=ga[:, 10], C=ga[:, 11].view(np.uint32),

@@ -290,6 +290,7 @@ def test_raster_dense_opaque_stack(orc, shared_margins):
     cam = scenegen.pinhole_camera(96, 96, 96.0)
     sp = U.random_splat_dict(4000, 23, 96, 96, max_radius=24)
     sp["opacity"] = np.random.default_rng(24).uniform(0.9, 1.0, 4000).astype(np.float32)
+    sp["tau"] = U.tau_of(sp["opacity"])   # the record's tau follows its opacity
     # two clamped splats leave T = (1 - 0.99)^2, exactly the 1e-4 stop
     # threshold, which rounding decides: those pixels are flagged
     _raster_case(orc, sp, cam, min_ok=0.9)

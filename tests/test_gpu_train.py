@@ -176,7 +176,10 @@ def test_loss_l1_kernel_matches_oracle(orc):
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     B.lgs_loss_l1(ti, tt, g, loss)
     torch.cuda.synchronize()
-    assert abs(float(loss.item()) - L) <= 1e-6 * L
+    # FP32 sums: per thread, per block, then one atomic per block in an
+    # unordered sequence (hundreds of blocks); each rounding is <= 2^-24 of
+    # the running total, so allow 1e-5 relative (the image tolerance)
+    assert abs(float(loss.item()) - L) <= 1e-5 * L
     np.testing.assert_array_equal(g.cpu().numpy(), dL.astype(np.float32))
 
 
