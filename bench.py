@@ -167,7 +167,7 @@ def run_gpu(args) -> dict | None:
     target = torch.from_numpy(tgt_np).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(events=None):
+    def step(events=None, precision=B.LGS_FP32):
         def mark(i):
             if events is not None:
                 events[i].record(stream)
@@ -184,12 +184,12 @@ def run_gpu(args) -> dict | None:
                        tr.ws_bin)
         mark(4)
         B.lgs_raster_fwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.image,
-                         tr.finalT, tr.last)
+                         tr.finalT, tr.last, precision=precision)
         mark(5)
         B.lgs_loss_l1(tr.image, target, tr.dLdI, tr.loss)
         mark(6)
         B.lgs_raster_bwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.finalT, tr.last,
-                         tr.dLdI, tr.gacc)
+                         tr.dLdI, tr.gacc, precision=precision)
         mark(7)
         B.lgs_opacity_variance(tr.gacc, tr.rowmap, tr.d_V, tr.n, tr.metric)
         mark(8)
@@ -247,6 +247,28 @@ def run_gpu(args) -> dict | None:
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+    # ---- the same step with the mixed-precision raster (FP16 / BF16 blend)
+    mixed = {}
+    for name, prec in (("fp16", B.LGS_MIXED_FP16), ("bf16", B.LGS_MIXED_BF16)):
+        for _ in range(2):
+            step(precision=prec)
+        mev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        for k in range(args.steps):
+            step(mev[k], precision=prec)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        mixed[name] = {
+            "value": round(world * args.steps / (mms / 1e3), 2), "unit": UNIT,
+            "ms_per_step": round(mms / args.steps, 4),
+            "a5_raster_fwd_ms": round(float(np.mean([mev[k][4].elapsed_time(mev[k][5])
+                                                     for k in range(args.steps)])), 4),
+            "a7_raster_bwd_ms": round(float(np.mean([mev[k][6].elapsed_time(mev[k][7])
+                                                     for k in range(args.steps)])), 4)}
     clk = clocks.stop()
     loss_val = float(loss_host.item())
     if world > 1:
@@ -259,27 +281,30 @@ def run_gpu(args) -> dict | None:
     ms_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     e2e_value = world * args.steps / (e2e_ms / 1e3)
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant HBM-bound call: the fused preprocess
+    # backward + Adam (k_bwd_adam_geom + k_bwd_adam_sh), 1468 B per visible
+    # Gaussian at SH3: params, m, v read and written (6 x 59 x 4 B), the
+    # 9 gradients + S, M, C of its grad row (48 B) and its map entry (4 B)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
     npl = B.num_planes(SH_DEG)
-    kernel_bytes = {
-        "a9a10_bwd_adam": V * (6 * npl * 4 + 48 + 4),   # p, m, v read + write; grad row; map
-        "a3_preprocess": V * (npl * 4 + 4 + 48 + 4 + 4),  # params + map in; record, depth, radius out
-    }
-    single = {s: stage_ms[s] for s in ("a3_preprocess", "a5_raster_fwd", "a7_raster_bwd",
-                                        "a9a10_bwd_adam")}
-    dom = max(kernel_bytes, key=lambda s: stage_ms[s])
-    achieved = kernel_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    per_unit = {"a9a10_bwd_adam": 6 * npl * 4 + 48 + 4,
+                "a3_preprocess": npl * 4 + 4 + 48 + 4 + 4}  # params + map in; record, depth, radius out
+    dom = "a9a10_bwd_adam"
+    achieved = V * per_unit[dom] / (stage_ms[dom] * 1e-3) / 1e9
     tr_rec = traffic_record().get(dom, {})
-    traffic = tr_rec.get("bytes_per_launch") if tr_rec.get("source") == source_digest() else None
-    roofline = {"kernel": {"a9a10_bwd_adam": "k_preprocess_bwd_adam",
-                           "a3_preprocess": "k_preprocess"}[dom],
-                "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+    traffic = (round(tr_rec["bytes_per_unit"] * V) if tr_rec.get("source") == source_digest()
+               and "bytes_per_unit" in tr_rec else None)
+    roofline = {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_geom<3> + k_bwd_adam_sh<3>)",
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "peak_source": "measured" if hbm else "fallback",
-                "frac": round(achieved / (hbm if hbm else 6800.0), 4),
-                "traffic": traffic, "algorithmic_bytes": int(kernel_bytes[dom])}
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes": int(V * per_unit[dom]),
+                "bytes_per_visible_gaussian": per_unit[dom]}
+    pre_gbs = V * per_unit["a3_preprocess"] / (stage_ms["a3_preprocess"] * 1e-3) / 1e9
+    other = {"a3_preprocess": {"bound": "hbm", "achieved": round(pre_gbs, 1),
+                               "frac": round(pre_gbs / peak, 4)}}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -290,6 +315,8 @@ def run_gpu(args) -> dict | None:
                    "parallelism": f"replicas x{world}", "visible_gaussians": V, "pairs": P,
                    "l2": "inputs larger than L2 (2.1 GB resident state), no flush"},
         "roofline": roofline,
+        "roofline_other": other,
+        "mixed": mixed,
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(tgt_np.nbytes), "d2h_bytes_per_step": 4},

@@ -142,6 +142,21 @@ Cam make_cam(const lgs_camera *c, int tw, int th) {
     return k;
 }
 
+// View direction from the camera centre to the Gaussian centre and the
+// inverse distance, with explicitly rounded operations so that every kernel
+// that needs it derives the same bits (the SH pass re-derives the colour
+// clamp of the forward from it). A centre at the camera centre gets dir 0.
+__device__ __forceinline__ void view_dir(const Cam &K, float mx, float my, float mz, float *dir,
+                                         float &dinv) {
+    const float dx = __fsub_rn(mx, K.cc[0]), dy = __fsub_rn(my, K.cc[1]),
+                dz = __fsub_rn(mz, K.cc[2]);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    dinv = d2 > 0.0f ? __frcp_rn(__fsqrt_rn(d2)) : 0.0f;
+    dir[0] = __fmul_rn(dx, dinv);
+    dir[1] = __fmul_rn(dy, dinv);
+    dir[2] = __fmul_rn(dz, dinv);
+}
+
 // Geometry of one Gaussian (planes 0..10): camera-space centre, 3D and 2D
 // covariance, conic, screen centre, radius and tile-rectangle cull, view
 // direction. Returns false when the Gaussian is culled.
@@ -213,10 +228,7 @@ __device__ __forceinline__ bool geom_forward(const Cam &K, const float *__restri
     f.radius = (int)ceilf(3.0f * sqrtf(lam));
     const int4 rc = tile_rect(f.u, f.v, (float)f.radius, K.tw, K.th, K.gx, K.gy);
     if (rc.z <= rc.x || rc.w <= rc.y) { f.culled = true; return false; }
-    const float dx = mx - K.cc[0], dy = my - K.cc[1], dz = mz - K.cc[2];
-    const float dl = sqrtf(dx * dx + dy * dy + dz * dz);
-    f.dinv = 1.0f / dl;
-    f.dir[0] = dx * f.dinv; f.dir[1] = dy * f.dinv; f.dir[2] = dz * f.dinv;
+    view_dir(K, mx, my, mz, f.dir, f.dinv);
     return true;
 }
 
@@ -229,7 +241,8 @@ __device__ __forceinline__ void color_forward(const float *__restrict__ P, int64
 #pragma unroll
     for (int k = 0; k < KK; ++k)
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) raw[ch] += P[(11 + 3 * k + ch) * stride + row] * Y[k];
+        for (int ch = 0; ch < 3; ++ch)
+            raw[ch] = __fmaf_rn(P[(11 + 3 * k + ch) * stride + row], Y[k], raw[ch]);
 }
 
 template <int DEG>
@@ -275,23 +288,17 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
 // `sink(k, g)` as soon as it is known (planes in the order of lgs.h). The
 // colour part streams over the SH planes; nothing is kept in local arrays.
 // ---------------------------------------------------------------------------
-template <int DEG, typename Sink>
-__device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__ P, int64_t stride,
-                                         int64_t row, const float *__restrict__ g16, Sink &sink,
-                                         float *dir_out = nullptr, float *grgb_out = nullptr) {
-    constexpr int KK = (DEG + 1) * (DEG + 1);
-    Fwd f;
-    if (!geom_forward(K, P, stride, row, f)) {
-#pragma unroll
-        for (int k = 0; k < 11 + 3 * KK; ++k) sink(k, 0.0f);
-        if (grgb_out) grgb_out[0] = grgb_out[1] = grgb_out[2] = 0.0f;
-        if (dir_out) dir_out[0] = dir_out[1] = dir_out[2] = 0.0f;
-        return false;
-    }
+// Geometric part of the backward: gradients of planes 3..10 to sink(k, g)
+// and the geometric part of the centre's gradient (through u, v and the
+// projection) to gm; the colour's dependence on the centre through the view
+// direction is added by the caller.
+template <typename Sink>
+__device__ __forceinline__ void geom_backward(const Cam &K, const Fwd &f,
+                                              const float *__restrict__ g16, Sink &sink,
+                                              float *gm) {
     const float4 ga = reinterpret_cast<const float4 *>(g16)[0];
-    const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
-    const float4 gc = reinterpret_cast<const float4 *>(g16)[2];
-    const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, go = gb.y;
+    const float2 gb2 = reinterpret_cast<const float2 *>(g16)[2];
+    const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb2.x, go = gb2.y;
     // ---- opacity: o = sigmoid(logit)
     {
         const float o = 1.0f / (1.0f + expf(-f.logit));
@@ -354,7 +361,6 @@ __device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__
     gpy += gv * K.fy * iz;
     gpz += -(gu * K.fx * f.px + gv * K.fy * f.py) * iz2;
     // ---- camera transform: the geometric part of the centre's gradient
-    float gm[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) gm[k] = K.R[k] * gpx + K.R[3 + k] * gpy + K.R[6 + k] * gpz;
     // ---- Sigma = sum_k s_k^2 r_k r_k^T with G the full symmetric gradient:
@@ -389,22 +395,28 @@ __device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__
 #pragma unroll
         for (int k = 0; k < 4; ++k) sink(6 + k, (gq[k] - f.qn[k] * dq) * f.qinv);
     }
+}
+
+template <int DEG, typename Sink>
+__device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__ P, int64_t stride,
+                                         int64_t row, const float *__restrict__ g16, Sink &sink) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
+    Fwd f;
+    if (!geom_forward(K, P, stride, row, f)) {
+#pragma unroll
+        for (int k = 0; k < 11 + 3 * KK; ++k) sink(k, 0.0f);
+        return false;
+    }
+    float gm[3];
+    geom_backward(K, f, g16, sink, gm);
     // ---- colour: clamp test, SH coefficients (streamed) and view direction
+    const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
+    const float gcb = g16[8];
     float Y[16], raw[3];
     sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], Y);
     color_forward<DEG>(P, stride, row, Y, raw);
     const float grgb[3] = {raw[0] > 0.f ? gb.z : 0.f, raw[1] > 0.f ? gb.w : 0.f,
-                           raw[2] > 0.f ? gc.x : 0.f};
-    if (grgb_out) {
-        grgb_out[0] = grgb[0];
-        grgb_out[1] = grgb[1];
-        grgb_out[2] = grgb[2];
-    }
-    if (dir_out) {
-        dir_out[0] = f.dir[0];
-        dir_out[1] = f.dir[1];
-        dir_out[2] = f.dir[2];
-    }
+                           raw[2] > 0.f ? gcb : 0.f};
     float wk[16];
 #pragma unroll
     for (int k = 0; k < KK; ++k) {
@@ -460,12 +472,15 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__rest
 }
 
 // Fused backward + Adam in two passes over the visible Gaussians.
-// Part A (one thread per Gaussian): the gradients of the geometric planes
-// 0..10 (centre, scales, rotation, opacity) applied by Adam at once. The SH
-// planes' gradients are (colour gradient masked by the clamp) x Y_k(view
-// direction); part A leaves the masked colour gradient in slots 6..8 and the
-// view direction in slots 12..14 of the Gaussian's gradient row (zeros if
-// the Gaussian is culled).
+// Part A (one thread per Gaussian): the geometric backward; Adam on the
+// scale, rotation and opacity planes 3..10 at once; the geometric part of
+// the centre's gradient is parked in slots 12..14 of the Gaussian's gradient
+// row (zeros if the Gaussian is culled).
+// Part B (a CTA per 32 Gaussians, warp w for SH coefficients 4w..4w+3): the
+// colour clamp re-derived from the view direction and all coefficients, the
+// SH planes' gradients (masked colour gradient) x Y_k and their Adam
+// updates, the view direction's share of the centre's gradient summed over
+// the warps in shared memory, then Adam on the centre planes 0..2.
 struct GeomSink {
     float *__restrict__ P;
     float *__restrict__ M;
@@ -473,7 +488,7 @@ struct GeomSink {
     int64_t stride, row;
     const AdamArgs *a;
     __device__ __forceinline__ void operator()(int k, float g) {
-        if (k < 11) {
+        if (k >= 3 && k < 11) {
             const int64_t i = k * stride + row;
             float p = P[i], m = M[i], v = V[i];
             adam_update(p, m, v, g, a->lr[k], *a);
@@ -484,7 +499,6 @@ struct GeomSink {
     }
 };
 
-template <int DEG>
 __global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
     int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
@@ -495,58 +509,116 @@ __global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
         const int64_t row = map ? map[j] : j;
         float *g16 = gacc + 16 * j;
         GeomSink sink{P, Mo, Vo, stride, row, &a};
-        float dir[3], grgb[3];
-        backward<DEG>(K, P, stride, row, g16, sink, dir, grgb);
-        g16[6] = grgb[0];
-        g16[7] = grgb[1];
-        g16[8] = grgb[2];
-        g16[12] = dir[0];
-        g16[13] = dir[1];
-        g16[14] = dir[2];
+        float gm[3] = {0.f, 0.f, 0.f};
+        Fwd f;
+        if (geom_forward(K, P, stride, row, f)) {
+            geom_backward(K, f, g16, sink, gm);
+        } else {
+#pragma unroll
+            for (int k = 3; k < 11; ++k) sink(k, 0.0f);
+        }
+        g16[12] = gm[0];
+        g16[13] = gm[1];
+        g16[14] = gm[2];
     }
 }
 
-// Part B: Adam on the SH planes, one thread per (Gaussian, group of up to 4
-// coefficients), groups outermost so that a warp streams consecutive rows
-// of the same planes.
+template <int DEG, int G>
+__device__ __forceinline__ void sh_group_adam(float *__restrict__ P, float *__restrict__ Mo,
+                                              float *__restrict__ Vo, int64_t stride,
+                                              int64_t row, const float *Y, const float *grgb,
+                                              const AdamArgs &a, float *wk) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * G + q;
+        if (k < KK) {
+            float w = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const int pl = 11 + 3 * k + ch;
+                const int64_t i = pl * stride + row;
+                float p = P[i], m = Mo[i], v = Vo[i];
+                w = fmaf(grgb[ch], p, w);
+                adam_update(p, m, v, grgb[ch] * Y[k], a.lr[pl], a);
+                P[i] = p;
+                Mo[i] = m;
+                Vo[i] = v;
+            }
+            wk[k] = w;
+        }
+    }
+}
+
 template <int DEG>
-__global__ void __launch_bounds__(256) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
-                                                    float *__restrict__ Vo, int64_t stride,
-                                                    int64_t n, const uint32_t *__restrict__ map,
-                                                    const int32_t *d_V,
-                                                    const float *__restrict__ gacc, AdamArgs a) {
+__global__ void __launch_bounds__(32 * (((DEG + 1) * (DEG + 1) + 3) / 4)) k_bwd_adam_sh(
+    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
+    int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
+    const float *__restrict__ gacc, AdamArgs a) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
     constexpr int NG = (KK + 3) / 4;
+    __shared__ float s_gd[NG][3][32];
+    const int grp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t V = load_count(d_V, n);
-    const int64_t total = V * NG;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int grp = (int)(t / V);
-        const int64_t j = t - (int64_t)grp * V;
-        const int64_t row = map ? map[j] : j;
-        const float *g16 = gacc + 16 * j;
-        const float4 d4 = *reinterpret_cast<const float4 *>(g16 + 12);
-        const float gr[3] = {g16[6], g16[7], g16[8]};
-        float Y[16];
-        sh_basis(DEG, d4.x, d4.y, d4.z, Y);
+    for (int64_t jb = (int64_t)blockIdx.x * 32; jb < V; jb += (int64_t)gridDim.x * 32) {
+        const int64_t j = jb + lane;
+        const bool act = j < V;
+        float gd[3] = {0.f, 0.f, 0.f};
+        float dir[3] = {0.f, 0.f, 0.f}, dinv = 0.f, grgb[3] = {0.f, 0.f, 0.f};
+        int64_t row = 0;
+        // colour clamp from the coefficients before any warp of the CTA updates them
+        if (act) {
+            row = map ? map[j] : j;
+            const float *g16 = gacc + 16 * j;
+            view_dir(K, P[row], P[stride + row], P[2 * stride + row], dir, dinv);
+            float Y[16], raw[3];
+            sh_basis(DEG, dir[0], dir[1], dir[2], Y);
+            color_forward<DEG>(P, stride, row, Y, raw);
+            grgb[0] = raw[0] > 0.f ? g16[6] : 0.f;
+            grgb[1] = raw[1] > 0.f ? g16[7] : 0.f;
+            grgb[2] = raw[2] > 0.f ? g16[8] : 0.f;
+        }
+        if (NG > 1) __syncthreads();
+        if (act) {
+            float Y[16], wk[16];
+            sh_basis(DEG, dir[0], dir[1], dir[2], Y);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = 4 * grp + q;
-            if (k < KK) {
-                float yk = Y[0];
+            for (int k = 0; k < 16; ++k) wk[k] = 0.f;
+            switch (grp) {  // warp-uniform
+                case 0: sh_group_adam<DEG, 0>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
+                case 1: sh_group_adam<DEG, 1>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
+                case 2: sh_group_adam<DEG, 2>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
+                default: sh_group_adam<DEG, 3>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
+            }
+            sh_basis_grad(DEG, dir[0], dir[1], dir[2], wk, gd[0], gd[1], gd[2]);
+        }
+        if (NG > 1) {
+            s_gd[grp][0][lane] = gd[0];
+            s_gd[grp][1][lane] = gd[1];
+            s_gd[grp][2][lane] = gd[2];
+            __syncthreads();
+            if (grp == 0) {
 #pragma unroll
-                for (int c = 1; c < KK; ++c)
-                    if (c == k) yk = Y[c];
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const int pl = 11 + 3 * k + ch;
-                    const int64_t i = pl * stride + row;
-                    float p = P[i], m = Mo[i], v = Vo[i];
-                    adam_update(p, m, v, gr[ch] * yk, a.lr[pl], a);
-                    P[i] = p;
-                    Mo[i] = m;
-                    Vo[i] = v;
+                for (int w = 1; w < NG; ++w) {
+                    gd[0] += s_gd[w][0][lane];
+                    gd[1] += s_gd[w][1][lane];
+                    gd[2] += s_gd[w][2][lane];
                 }
+            }
+            __syncthreads();
+        }
+        if (grp == 0 && act) {
+            const float *g16 = gacc + 16 * j;
+            const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float g = g16[12 + c] + (gd[c] - dir[c] * dd) * dinv;
+                const int64_t i = c * stride + row;
+                float p = P[i], m = Mo[i], v = Vo[i];
+                adam_update(p, m, v, g, a.lr[c], a);
+                P[i] = p;
+                Mo[i] = m;
+                Vo[i] = v;
             }
         }
     }
@@ -618,23 +690,23 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
     const int ng = ((g->sh_degree + 1) * (g->sh_degree + 1) + 3) / 4;
-    const unsigned ga = grid_for(g->n, kThreads, 16), gb = grid_for(g->n * ng, 256, 16);
+    const unsigned ga = grid_for(g->n, kThreads, 16);
+    const unsigned gb = grid_for(ceil_div(g->n, 32), 1, 64 / ng);
+    count_launch();
+    k_bwd_adam_geom<<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+    count_launch();
     switch (g->sh_degree) {
     case 0:
-        count_launch(); k_bwd_adam_geom<0><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<0><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
+        k_bwd_adam_sh<0><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
         break;
     case 1:
-        count_launch(); k_bwd_adam_geom<1><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<1><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
+        k_bwd_adam_sh<1><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
         break;
     case 2:
-        count_launch(); k_bwd_adam_geom<2><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<2><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
+        k_bwd_adam_sh<2><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
         break;
     default:
-        count_launch(); k_bwd_adam_geom<3><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<3><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
+        k_bwd_adam_sh<3><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
         break;
     }
     return check_launch();
