@@ -26,7 +26,8 @@ ENTRY_POINTS = (
     "lgs_version", "lgs_last_cuda_error", "lgs_kernel_launches", "lgs_morton_workspace_size", "lgs_morton_reorder",
     "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_cluster_cull_compact_noalloc",
     "lgs_compact_gather", "lgs_preprocess",
-    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_raster_fwd",
+    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow",
+    "lgs_raster_fwd",
     "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
     "lgs_adam_step", "lgs_preprocess_bwd_adam",
 )

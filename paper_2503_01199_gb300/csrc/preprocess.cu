@@ -143,9 +143,9 @@ Cam make_cam(const lgs_camera *c, int tw, int th) {
 }
 
 // View direction from the camera centre to the Gaussian centre and the
-// inverse distance, with explicitly rounded operations so that every kernel
-// that needs it derives the same bits (the SH pass re-derives the colour
-// clamp of the forward from it). A centre at the camera centre gets dir 0.
+// inverse distance, with explicitly rounded operations so that the forward
+// and the backward derive the same bits (the colour clamp depends on it). A
+// centre at the camera centre gets dir 0.
 __device__ __forceinline__ void view_dir(const Cam &K, float mx, float my, float mz, float *dir,
                                          float &dinv) {
     const float dx = __fsub_rn(mx, K.cc[0]), dy = __fsub_rn(my, K.cc[1]),
@@ -399,12 +399,15 @@ __device__ __forceinline__ void geom_backward(const Cam &K, const Fwd &f,
 
 template <int DEG, typename Sink>
 __device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__ P, int64_t stride,
-                                         int64_t row, const float *__restrict__ g16, Sink &sink) {
+                                         int64_t row, const float *__restrict__ g16, Sink &sink,
+                                         float *dir_out = nullptr, float *grgb_out = nullptr) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
     Fwd f;
     if (!geom_forward(K, P, stride, row, f)) {
 #pragma unroll
         for (int k = 0; k < 11 + 3 * KK; ++k) sink(k, 0.0f);
+        if (dir_out) dir_out[0] = dir_out[1] = dir_out[2] = 0.0f;
+        if (grgb_out) grgb_out[0] = grgb_out[1] = grgb_out[2] = 0.0f;
         return false;
     }
     float gm[3];
@@ -417,6 +420,16 @@ __device__ __forceinline__ bool backward(const Cam &K, const float *__restrict__
     color_forward<DEG>(P, stride, row, Y, raw);
     const float grgb[3] = {raw[0] > 0.f ? gb.z : 0.f, raw[1] > 0.f ? gb.w : 0.f,
                            raw[2] > 0.f ? gcb : 0.f};
+    if (dir_out) {
+        dir_out[0] = f.dir[0];
+        dir_out[1] = f.dir[1];
+        dir_out[2] = f.dir[2];
+    }
+    if (grgb_out) {
+        grgb_out[0] = grgb[0];
+        grgb_out[1] = grgb[1];
+        grgb_out[2] = grgb[2];
+    }
     float wk[16];
 #pragma unroll
     for (int k = 0; k < KK; ++k) {
@@ -442,11 +455,13 @@ struct AdamArgs {
     float b1, b2, eps, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
 };
 
+// One Adam step; the quotient uses the fast reciprocal (2 ulp), far inside
+// the FP32 tolerance of the update.
 __device__ __forceinline__ void adam_update(float &p, float &m, float &v, float g, float lr,
                                             const AdamArgs &a) {
     m = a.b1 * m + (1.f - a.b1) * g;
     v = a.b2 * v + (1.f - a.b2) * g * g;
-    p -= lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+    p -= lr * __fdividef(m * a.c1, sqrtf(v * a.c2) + a.eps);
 }
 
 struct GradSink {
@@ -472,15 +487,16 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__rest
 }
 
 // Fused backward + Adam in two passes over the visible Gaussians.
-// Part A (one thread per Gaussian): the geometric backward; Adam on the
-// scale, rotation and opacity planes 3..10 at once; the geometric part of
-// the centre's gradient is parked in slots 12..14 of the Gaussian's gradient
-// row (zeros if the Gaussian is culled).
-// Part B (a CTA per 32 Gaussians, warp w for SH coefficients 4w..4w+3): the
-// colour clamp re-derived from the view direction and all coefficients, the
-// SH planes' gradients (masked colour gradient) x Y_k and their Adam
-// updates, the view direction's share of the centre's gradient summed over
-// the warps in shared memory, then Adam on the centre planes 0..2.
+// Part A (one thread per Gaussian): the whole backward; Adam on the planes
+// 0..10 (centre, scales, rotation, opacity) as their gradients are known.
+// The SH planes' gradients are (colour gradient masked by the clamp) x
+// Y_k(view direction): part A leaves the masked colour gradient in slots
+// 10..12 and the view direction in slots 13..15 of the gradient row (one
+// 32-byte sector; zeros if the Gaussian is culled).
+// Part B (one thread per SH coefficient k and Gaussian): Adam on the three
+// planes of coefficient k. Threads run coefficient-major within chunks of
+// 2048 Gaussians, so a warp streams 32 consecutive rows of the same planes
+// and a chunk's gradient-row sectors stay in L2 across its coefficients.
 struct GeomSink {
     float *__restrict__ P;
     float *__restrict__ M;
@@ -488,7 +504,7 @@ struct GeomSink {
     int64_t stride, row;
     const AdamArgs *a;
     __device__ __forceinline__ void operator()(int k, float g) {
-        if (k >= 3 && k < 11) {
+        if (k < 11) {
             const int64_t i = k * stride + row;
             float p = P[i], m = M[i], v = V[i];
             adam_update(p, m, v, g, a->lr[k], *a);
@@ -499,6 +515,7 @@ struct GeomSink {
     }
 };
 
+template <int DEG>
 __global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
     int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
@@ -509,117 +526,82 @@ __global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
         const int64_t row = map ? map[j] : j;
         float *g16 = gacc + 16 * j;
         GeomSink sink{P, Mo, Vo, stride, row, &a};
-        float gm[3] = {0.f, 0.f, 0.f};
-        Fwd f;
-        if (geom_forward(K, P, stride, row, f)) {
-            geom_backward(K, f, g16, sink, gm);
-        } else {
-#pragma unroll
-            for (int k = 3; k < 11; ++k) sink(k, 0.0f);
-        }
-        g16[12] = gm[0];
-        g16[13] = gm[1];
-        g16[14] = gm[2];
+        float dir[3], grgb[3];
+        backward<DEG>(K, P, stride, row, g16, sink, dir, grgb);
+        reinterpret_cast<float2 *>(g16)[5] = make_float2(grgb[0], grgb[1]);
+        reinterpret_cast<float4 *>(g16)[3] = make_float4(grgb[2], dir[0], dir[1], dir[2]);
     }
 }
 
-template <int DEG, int G>
-__device__ __forceinline__ void sh_group_adam(float *__restrict__ P, float *__restrict__ Mo,
-                                              float *__restrict__ Vo, int64_t stride,
-                                              int64_t row, const float *Y, const float *grgb,
-                                              const AdamArgs &a, float *wk) {
-    constexpr int KK = (DEG + 1) * (DEG + 1);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = 4 * G + q;
-        if (k < KK) {
-            float w = 0.f;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const int pl = 11 + 3 * k + ch;
-                const int64_t i = pl * stride + row;
-                float p = P[i], m = Mo[i], v = Vo[i];
-                w = fmaf(grgb[ch], p, w);
-                adam_update(p, m, v, grgb[ch] * Y[k], a.lr[pl], a);
-                P[i] = p;
-                Mo[i] = m;
-                Vo[i] = v;
-            }
-            wk[k] = w;
-        }
+// Y_k alone (k warp-uniform in part B), same expressions as sh_basis.
+__device__ __forceinline__ float sh_single(int k, float x, float y, float z) {
+    switch (k) {
+        case 0: return Y0;
+        case 1: return -Y1 * y;
+        case 2: return Y1 * z;
+        case 3: return -Y1 * x;
+        case 4: return Y22 * 2.0f * (x * y);
+        case 5: return Y21 * z * y;
+        case 6: return Y20 * 0.5f * (3.0f * (z * z) - 1.0f);
+        case 7: return Y21 * z * x;
+        case 8: return Y22 * ((x * x) - (y * y));
+        case 9: return Y33 * (3.0f * (x * x) * y - (y * y) * y);
+        case 10: return Y32 * z * 2.0f * (x * y);
+        case 11: return Y31 * (15.0f * (z * z) - 3.0f) * y;
+        case 12: return Y30 * 0.5f * (5.0f * (z * z) * z - 3.0f * z);
+        case 13: return Y31 * (15.0f * (z * z) - 3.0f) * x;
+        case 14: return Y32 * z * ((x * x) - (y * y));
+        default: return Y33 * ((x * x) * x - 3.0f * x * (y * y));
     }
 }
+
+constexpr int kChunk = 2048;
 
 template <int DEG>
-__global__ void __launch_bounds__(32 * (((DEG + 1) * (DEG + 1) + 3) / 4)) k_bwd_adam_sh(
-    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
-    int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
-    const float *__restrict__ gacc, AdamArgs a) {
+__global__ void __launch_bounds__(256) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
+                                                    float *__restrict__ Vo, int64_t stride,
+                                                    int64_t n, const uint32_t *__restrict__ map,
+                                                    const int32_t *d_V,
+                                                    const float *__restrict__ gacc, AdamArgs a) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
-    constexpr int NG = (KK + 3) / 4;
-    __shared__ float s_gd[NG][3][32];
-    const int grp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t V = load_count(d_V, n);
-    for (int64_t jb = (int64_t)blockIdx.x * 32; jb < V; jb += (int64_t)gridDim.x * 32) {
-        const int64_t j = jb + lane;
-        const bool act = j < V;
-        float gd[3] = {0.f, 0.f, 0.f};
-        float dir[3] = {0.f, 0.f, 0.f}, dinv = 0.f, grgb[3] = {0.f, 0.f, 0.f};
-        int64_t row = 0;
-        // colour clamp from the coefficients before any warp of the CTA updates them
-        if (act) {
-            row = map ? map[j] : j;
-            const float *g16 = gacc + 16 * j;
-            view_dir(K, P[row], P[stride + row], P[2 * stride + row], dir, dinv);
-            float Y[16], raw[3];
-            sh_basis(DEG, dir[0], dir[1], dir[2], Y);
-            color_forward<DEG>(P, stride, row, Y, raw);
-            grgb[0] = raw[0] > 0.f ? g16[6] : 0.f;
-            grgb[1] = raw[1] > 0.f ? g16[7] : 0.f;
-            grgb[2] = raw[2] > 0.f ? g16[8] : 0.f;
+    const int64_t total = V * KK;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t / (KK * kChunk);
+        const int64_t base = c * kChunk;
+        const int64_t r = t - c * (KK * kChunk);
+        int k;
+        int64_t j;
+        if (V - base >= kChunk) {
+            k = (int)(r / kChunk);
+            j = base + (r - (int64_t)k * kChunk);
+        } else {  // the last, partial chunk
+            const int64_t len = V - base;
+            k = (int)(r / len);
+            j = base + (r - (int64_t)k * len);
         }
-        if (NG > 1) __syncthreads();
-        if (act) {
-            float Y[16], wk[16];
-            sh_basis(DEG, dir[0], dir[1], dir[2], Y);
+        const int64_t row = map ? map[j] : j;
+        const float2 s0 = reinterpret_cast<const float2 *>(gacc + 16 * j)[5];
+        const float4 s1 = reinterpret_cast<const float4 *>(gacc + 16 * j)[3];
+        const float grgb[3] = {s0.x, s0.y, s1.x};
+        const float yk = sh_single(k, s1.y, s1.z, s1.w);
+        float p[3], m[3], v[3];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) wk[k] = 0.f;
-            switch (grp) {  // warp-uniform
-                case 0: sh_group_adam<DEG, 0>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
-                case 1: sh_group_adam<DEG, 1>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
-                case 2: sh_group_adam<DEG, 2>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
-                default: sh_group_adam<DEG, 3>(P, Mo, Vo, stride, row, Y, grgb, a, wk); break;
-            }
-            sh_basis_grad(DEG, dir[0], dir[1], dir[2], wk, gd[0], gd[1], gd[2]);
+        for (int ch = 0; ch < 3; ++ch) {
+            const int64_t i = (11 + 3 * k + ch) * stride + row;
+            p[ch] = P[i];
+            m[ch] = Mo[i];
+            v[ch] = Vo[i];
         }
-        if (NG > 1) {
-            s_gd[grp][0][lane] = gd[0];
-            s_gd[grp][1][lane] = gd[1];
-            s_gd[grp][2][lane] = gd[2];
-            __syncthreads();
-            if (grp == 0) {
 #pragma unroll
-                for (int w = 1; w < NG; ++w) {
-                    gd[0] += s_gd[w][0][lane];
-                    gd[1] += s_gd[w][1][lane];
-                    gd[2] += s_gd[w][2][lane];
-                }
-            }
-            __syncthreads();
-        }
-        if (grp == 0 && act) {
-            const float *g16 = gacc + 16 * j;
-            const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float g = g16[12 + c] + (gd[c] - dir[c] * dd) * dinv;
-                const int64_t i = c * stride + row;
-                float p = P[i], m = Mo[i], v = Vo[i];
-                adam_update(p, m, v, g, a.lr[c], a);
-                P[i] = p;
-                Mo[i] = m;
-                Vo[i] = v;
-            }
+        for (int ch = 0; ch < 3; ++ch) {
+            const int pl = 11 + 3 * k + ch;
+            adam_update(p[ch], m[ch], v[ch], grgb[ch] * yk, a.lr[pl], a);
+            const int64_t i = pl * stride + row;
+            P[i] = p[ch];
+            Mo[i] = m[ch];
+            Vo[i] = v[ch];
         }
     }
 }
@@ -689,24 +671,25 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
                                cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
-    const int ng = ((g->sh_degree + 1) * (g->sh_degree + 1) + 3) / 4;
     const unsigned ga = grid_for(g->n, kThreads, 16);
-    const unsigned gb = grid_for(ceil_div(g->n, 32), 1, 64 / ng);
-    count_launch();
-    k_bwd_adam_geom<<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-    count_launch();
+    const int kk = (g->sh_degree + 1) * (g->sh_degree + 1);
+    const unsigned gb = grid_for(g->n * kk, 256, 16);
     switch (g->sh_degree) {
     case 0:
-        k_bwd_adam_sh<0><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_geom<0><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<0><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     case 1:
-        k_bwd_adam_sh<1><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_geom<1><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<1><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     case 2:
-        k_bwd_adam_sh<2><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_geom<2><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<2><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     default:
-        k_bwd_adam_sh<3><<<gb, 32 * ng, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_geom<3><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
+        count_launch(); k_bwd_adam_sh<3><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
         break;
     }
     return check_launch();

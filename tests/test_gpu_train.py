@@ -166,6 +166,56 @@ def test_fused_backward_adam_equals_separate(orc):
     assert np.mean(np.abs(b["params"] - a["params"]) > 1e-6) < 1e-3
 
 
+@pytest.mark.parametrize("layout", ["clusters", "scattered", "unaligned_run"])
+def test_fused_backward_adam_map_layouts(layout):
+    """The fused call reaches rows through the map in both of its passes:
+    consecutive, scattered and unaligned runs of visible rows must all give
+    the separate path's result, and rows outside the map must stay
+    byte-identical."""
+    d = scenegen.uniform_box_scene(1000, 3, 9, 96, 96, focal=96.0)
+    sc, cam = d["scene"], d["camera"]
+    rng = np.random.default_rng(10)
+    if layout == "clusters":          # consecutive from row 0: all units bulk-copied
+        rows = np.arange(0, 1000)
+    elif layout == "scattered":       # not consecutive, V % 4 != 0
+        rows = np.sort(rng.choice(1000, 397, replace=False))
+    else:                             # consecutive but starting at row 2
+        rows = np.arange(2, 902)
+    V = rows.size
+    grads = np.zeros((1000, 16), np.float32)
+    grads[:V, :9] = rng.standard_normal((V, 9)).astype(np.float32) * 1e-2
+    lr = PL.lr_per_plane(3)
+    m0 = rng.standard_normal((59, 1000)).astype(np.float32) * 1e-3
+    v0 = rng.uniform(0, 1e-4, (59, 1000)).astype(np.float32)
+    out = []
+    for fused in (False, True):
+        planes, n = U.planes_tensor(sc)
+        m = torch.zeros_like(planes)
+        v = torch.zeros_like(planes)
+        m[:, :n] = U.t(m0)
+        v[:, :n] = U.t(v0)
+        g = B.gaussians_struct(planes, n, 3)
+        cs = B.camera_struct(cam)
+        mp = U.t(rows.astype(np.uint32).view(np.int32))
+        dV = U.t(np.array([V], np.int32))
+        gacc = U.t(grads)
+        if fused:
+            B.lgs_preprocess_bwd_adam(g, m, v, mp, dV, cs, gacc, lr, 0.9, 0.999, 1e-15, 3)
+        else:
+            gp = torch.zeros_like(planes)
+            B.lgs_preprocess_bwd(g, mp, dV, cs, gacc, gp)
+            B.lgs_adam_step(planes, gp, m, v, planes.shape[0], lr, 0.9, 0.999, 1e-15, 3, mp, dV, n)
+        torch.cuda.synchronize()
+        out.append((planes.cpu().numpy()[:, :n], m.cpu().numpy()[:, :n], v.cpu().numpy()[:, :n]))
+    (pa, ma, va), (pb, mb, vb) = out
+    hidden = np.setdiff1d(np.arange(1000), rows)
+    np.testing.assert_array_equal(pb[:, hidden], pa[:, hidden])
+    np.testing.assert_array_equal(mb[:, hidden], ma[:, hidden])
+    np.testing.assert_allclose(mb[:, rows], ma[:, rows], rtol=1e-4, atol=1e-9)
+    np.testing.assert_allclose(vb[:, rows], va[:, rows], rtol=1e-4, atol=1e-14)
+    np.testing.assert_allclose(pb[:, rows], pa[:, rows], rtol=1e-5, atol=1e-6)
+
+
 def test_loss_l1_kernel_matches_oracle(orc):
     img = scenegen.random_image(41, 3, 333, 257) * 1.2 - 0.1
     tgt = scenegen.random_image(42, 3, 333, 257)
