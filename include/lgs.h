@@ -82,6 +82,12 @@ typedef struct lgs_camera {
     int32_t width, height;
     float znear; /* Gaussians with camera z <= znear are culled */
     float bg[3]; /* background colour composited behind the last splat */
+    /* Optional device pointer to 12 floats (R row-major, then t). When not
+     * NULL, lgs_cluster_cull_compact and lgs_preprocess read the pose from
+     * it when their kernels run instead of R and t above, so a captured CUDA
+     * graph can be replayed for new poses (resolution and intrinsics stay
+     * those of the capture). The backward calls reject it. */
+    const float *d_pose;
 } lgs_camera;
 
 /* Gaussian parameter planes (see above). Device memory. */
@@ -90,8 +96,18 @@ typedef struct lgs_gaussians {
     int64_t n;      /* number of Gaussians */
     int64_t stride; /* plane stride in floats, >= n, multiple of 4 */
     int32_t sh_degree; /* 0..3 */
-    int32_t reserved;
+    /* Storage of the colour coefficients: LGS_SH_F32 (planes 11.. of data)
+     * or LGS_SH_BF16 / LGS_SH_F16: 16-bit planes at sh16 + k * stride,
+     * k = 3 coefficient + channel (planes 0..10 stay float32 in data).
+     * 16-bit storage is for rendering: only lgs_cluster_cull_compact and
+     * lgs_preprocess accept it; the backward and optimizer calls reject it. */
+    int32_t sh_dtype;
+    const void *sh16;
 } lgs_gaussians;
+
+#define LGS_SH_F32 0
+#define LGS_SH_BF16 1
+#define LGS_SH_F16 2
 
 /* Projected splats, indexed by compacted index j < V. Device memory. */
 typedef struct lgs_splats {

@@ -17,6 +17,7 @@ from . import build as _build
 LGS_OK, LGS_ERR_INVALID_ARG, LGS_ERR_CAPACITY, LGS_ERR_CUDA, LGS_ERR_TIMEOUT = 0, 1, 2, 3, 4
 LGS_ERR_TOO_LARGE = 5
 LGS_FP32, LGS_MIXED_FP16, LGS_MIXED_BF16 = 0, 1, 2
+LGS_SH_F32, LGS_SH_BF16, LGS_SH_F16 = 0, 1, 2
 NOALLOC_MAX_CLUSTERS = 65536
 SPLAT_FLOATS = 12
 GRAD_FLOATS = 16
@@ -41,12 +42,13 @@ class LgsCamera(ctypes.Structure):
     _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("znear", ctypes.c_float),
-                ("bg", ctypes.c_float * 3)]
+                ("bg", ctypes.c_float * 3), ("d_pose", ctypes.c_void_p)]
 
 
 class LgsGaussians(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int64),
-                ("sh_degree", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sh_degree", ctypes.c_int32), ("sh_dtype", ctypes.c_int32),
+                ("sh16", ctypes.c_void_p)]
 
 
 class LgsSplats(ctypes.Structure):
@@ -136,7 +138,10 @@ def _stream(stream=None) -> int:
 # --------------------------------------------------------------------------
 # descriptors
 # --------------------------------------------------------------------------
-def camera_struct(cam: dict) -> LgsCamera:
+def camera_struct(cam: dict, d_pose=None) -> LgsCamera:
+    """Host camera descriptor; d_pose (optional float32 CUDA tensor of 12:
+    R row-major, t) makes the cull and preprocess read the pose from device
+    memory when they run."""
     c = LgsCamera()
     R = [float(x) for x in np.asarray(cam["R"]).reshape(9)]
     t = [float(x) for x in np.asarray(cam["t"]).reshape(3)]
@@ -147,16 +152,26 @@ def camera_struct(cam: dict) -> LgsCamera:
     c.width, c.height = int(cam["width"]), int(cam["height"])
     c.znear = float(cam["znear"])
     c.bg[:] = bg
+    c.d_pose = _ptr(d_pose)
     return c
 
 
-def gaussians_struct(planes: torch.Tensor, n: int, sh_degree: int) -> LgsGaussians:
-    """planes: float32 CUDA tensor [>= num_planes, stride]."""
+def gaussians_struct(planes: torch.Tensor, n: int, sh_degree: int,
+                     sh16: torch.Tensor | None = None) -> LgsGaussians:
+    """planes: float32 CUDA tensor [>= num_planes, stride] (or [>= 11, stride]
+    with sh16 given); sh16: optional bfloat16 / float16 CUDA tensor
+    [3 (deg+1)^2, stride] holding the colour coefficients instead."""
     g = LgsGaussians()
     g.data = _ptr(planes)
     g.n = int(n)
     g.stride = int(planes.shape[-1])
     g.sh_degree = int(sh_degree)
+    g.sh_dtype = LGS_SH_F32
+    if sh16 is not None:
+        if sh16.shape[-1] != planes.shape[-1]:
+            raise LgsError("sh16 must have the planes' stride")
+        g.sh_dtype = {torch.bfloat16: LGS_SH_BF16, torch.float16: LGS_SH_F16}[sh16.dtype]
+        g.sh16 = _ptr(sh16)
     return g
 
 

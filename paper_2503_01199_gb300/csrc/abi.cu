@@ -95,7 +95,15 @@ bool bad_camera(const lgs_camera *c) {
 
 bool bad_gaussians(const lgs_gaussians *g) {
     return !g || !g->data || g->n < 0 || g->n > 0x7fffffffLL || g->stride < g->n ||
-           (g->stride & 3) || g->sh_degree < 0 || g->sh_degree > 3 || !aligned16(g->data);
+           (g->stride & 3) || g->sh_degree < 0 || g->sh_degree > 3 || !aligned16(g->data) ||
+           g->sh_dtype < LGS_SH_F32 || g->sh_dtype > LGS_SH_F16 ||
+           (g->sh_dtype != LGS_SH_F32 && (!g->sh16 || !aligned16(g->sh16)));
+}
+
+// calls that update or differentiate the parameters need FP32 colour planes
+// and the pose given on the host
+bool training_only(const lgs_gaussians *g, const lgs_camera *c) {
+    return g->sh_dtype != LGS_SH_F32 || c->d_pose != nullptr;
 }
 
 bool bad_splats(const lgs_splats *s, int64_t rows) {
@@ -246,7 +254,8 @@ lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,
 lgs_status lgs_preprocess_bwd(const lgs_gaussians *g, const uint32_t *map,
                               const int32_t *d_num_visible, const lgs_camera *cam,
                               const float *grad_acc, float *grad_planes, lgs_stream stream) {
-    if (bad_gaussians(g) || bad_camera(cam) || !grad_acc || !grad_planes || !aligned16(grad_acc))
+    if (bad_gaussians(g) || bad_camera(cam) || !grad_acc || !grad_planes || !aligned16(grad_acc) ||
+        training_only(g, cam))
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
     return preprocess_bwd(g, map, d_num_visible, cam, grad_acc, grad_planes, as_stream(stream));
@@ -270,7 +279,7 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream) {
     if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||
-        !aligned16(grad_acc) || !aligned16(m) || !aligned16(v))
+        !aligned16(grad_acc) || !aligned16(m) || !aligned16(v) || training_only(g, cam))
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
     return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, grad_acc, lr, beta1, beta2, eps,

@@ -98,10 +98,36 @@ struct Planes {
     float d[5];
 };
 
+// World-space frustum planes from camera-space ones: n_world = R^T n_cam,
+// d_world = n_cam . t + d_cam.
+__host__ __device__ inline Planes world_planes(const float cn[5][3], const float cd[5],
+                                               const float *R, const float *t) {
+    Planes pl;
+    for (int q = 0; q < 5; ++q) {
+        for (int j = 0; j < 3; ++j)
+            pl.n[q][j] = R[j] * cn[q][0] + R[3 + j] * cn[q][1] + R[6 + j] * cn[q][2];
+        pl.d[q] = cn[q][0] * t[0] + cn[q][1] * t[1] + cn[q][2] * t[2] + cd[q];
+    }
+    return pl;
+}
+
+struct CamPlanes {
+    float cn[5][3];
+    float cd[5];
+};
+
 __global__ void __launch_bounds__(kThreads) k_cluster_cull(const float *__restrict__ p,
                                                           int64_t n, int64_t stride, int cs,
-                                                          Planes pl, float *aabb_out,
+                                                          Planes pl, CamPlanes cp,
+                                                          const float *__restrict__ pose,
+                                                          float *aabb_out,
                                                           uint32_t *__restrict__ vis) {
+    if (pose) {  // pose read at run time (graph replay with new cameras)
+        float R[9], t[3];
+        for (int i = 0; i < 9; ++i) R[i] = __ldg(pose + i);
+        for (int i = 0; i < 3; ++i) t[i] = __ldg(pose + 9 + i);
+        pl = world_planes(cp.cn, cp.cd, R, t);
+    }
     const int64_t ncl = (n + cs - 1) / cs;
     const int lane = threadIdx.x & 31;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncl;
@@ -232,17 +258,13 @@ lgs_status cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *cam, i
     // frustum planes n . x + d >= 0 (inside), camera space -> world space
     const float limx = 1.3f * cam->width / (2.0f * cam->fx);
     const float limy = 1.3f * cam->height / (2.0f * cam->fy);
-    const float cn[5][3] = {{0, 0, 1}, {-1, 0, limx}, {1, 0, limx}, {0, -1, limy}, {0, 1, limy}};
-    const float cd[5] = {-cam->znear, 0, 0, 0, 0};
-    Planes pl;
-    for (int q = 0; q < 5; ++q) {
-        for (int j = 0; j < 3; ++j)
-            pl.n[q][j] = cam->R[j] * cn[q][0] + cam->R[3 + j] * cn[q][1] + cam->R[6 + j] * cn[q][2];
-        pl.d[q] = cn[q][0] * cam->t[0] + cn[q][1] * cam->t[1] + cn[q][2] * cam->t[2] + cd[q];
-    }
+    const CamPlanes cp = {{{0, 0, 1}, {-1, 0, limx}, {1, 0, limx}, {0, -1, limy}, {0, 1, limy}},
+                          {-cam->znear, 0, 0, 0, 0}};
+    const Planes pl = world_planes(cp.cn, cp.cd, cam->R, cam->t);
     const unsigned gcl = grid_for(ncl * 32, kThreads);
     count_launch();
-    k_cluster_cull<<<gcl, kThreads, 0, s>>>(g->data, n, g->stride, cs, pl, aabb_out, vis);
+    k_cluster_cull<<<gcl, kThreads, 0, s>>>(g->data, n, g->stride, cs, pl, cp, cam->d_pose,
+                                            aabb_out, vis);
     lgs_status st = check_launch();
     if (st != LGS_OK) return st;
     st = exclusive_scan_u32_to_u64(vis, off, ncl, nullptr, d_nvis, scan_ws, s);

@@ -4,6 +4,7 @@
 // One thread per compacted Gaussian j; row = map[j]. Parameter planes are
 // read with unit stride across the warp: a visible cluster is a run of
 // consecutive rows, so reads through the map stay coalesced.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lgs_internal.cuh"
@@ -125,7 +126,20 @@ struct Fwd {
 struct Cam {
     float R[9], t[3], fx, fy, cx, cy, znear, cc[3], limx, limy;
     int W, H, tw, th, gx, gy;
+    const float *pose;  // optional device pose (R row-major, t) read at run time
 };
+
+// Replaces R, t and the camera centre by the device-resident pose, if any.
+__device__ __forceinline__ void resolve_pose(Cam &K) {
+    if (!K.pose) return;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) K.R[i] = __ldg(K.pose + i);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) K.t[i] = __ldg(K.pose + 9 + i);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        K.cc[i] = -(K.R[i] * K.t[0] + K.R[3 + i] * K.t[1] + K.R[6 + i] * K.t[2]);
+}
 
 Cam make_cam(const lgs_camera *c, int tw, int th) {
     Cam k;
@@ -139,6 +153,7 @@ Cam make_cam(const lgs_camera *c, int tw, int th) {
     k.W = c->width; k.H = c->height; k.tw = tw; k.th = th;
     k.gx = (int)ceil_div(c->width, tw);
     k.gy = (int)ceil_div(c->height, th);
+    k.pose = c->d_pose;
     return k;
 }
 
@@ -245,13 +260,33 @@ __device__ __forceinline__ void color_forward(const float *__restrict__ P, int64
             raw[ch] = __fmaf_rn(P[(11 + 3 * k + ch) * stride + row], Y[k], raw[ch]);
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict__ P, int64_t stride,
+// the same sum with the coefficients stored as 16-bit planes
+template <int DEG, int SHT>
+__device__ __forceinline__ void color_forward16(const uint16_t *__restrict__ sh, int64_t stride,
+                                                int64_t row, const float *Y, float *raw) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
+    raw[0] = raw[1] = raw[2] = 0.5f;
+#pragma unroll
+    for (int k = 0; k < KK; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const uint16_t b = __ldg(sh + (3 * k + ch) * stride + row);
+            const float c = SHT == LGS_SH_BF16 ? __uint_as_float((uint32_t)b << 16)
+                                               : __half2float(__ushort_as_half(b));
+            raw[ch] = __fmaf_rn(c, Y[k], raw[ch]);
+        }
+}
+
+template <int DEG, int SHT>
+__global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict__ P,
+                                                        const uint16_t *__restrict__ sh16,
+                                                        int64_t stride,
                                                         int64_t n, const uint32_t *__restrict__ map,
                                                         const int32_t *d_V, Cam K,
                                                         float *__restrict__ rec,
                                                         float *__restrict__ depth,
                                                         int32_t *__restrict__ radius) {
+    resolve_pose(K);
     const int64_t V = load_count(d_V, n);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -268,7 +303,10 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
         }
         float Y[16], raw[3];
         sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], Y);
-        color_forward<DEG>(P, stride, row, Y, raw);
+        if (SHT == LGS_SH_F32)
+            color_forward<DEG>(P, stride, row, Y, raw);
+        else
+            color_forward16<DEG, SHT>(sh16, stride, row, Y, raw);
         const float o = 1.0f / (1.0f + expf(-f.logit));
         // tau: the largest q = d^T conic d at which alpha = o exp(-q/2) can
         // still reach 1/255, widened by 1e-3 (1 + |tau|), far above the
@@ -643,12 +681,23 @@ lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t
                       cudaStream_t s) {
     const Cam K = make_cam(cam, tw, th);
     const unsigned grid = grid_for(g->n, kThreads, 16);
-    switch (g->sh_degree) {
-    case 0: count_launch(); k_preprocess<0><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
-    case 1: count_launch(); k_preprocess<1><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
-    case 2: count_launch(); k_preprocess<2><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
-    default: count_launch(); k_preprocess<3><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius); break;
+    const uint16_t *sh = static_cast<const uint16_t *>(g->sh16);
+#define LGS_PRE(D, T) k_preprocess<D, T><<<grid, kThreads, 0, s>>>(g->data, sh, g->stride, g->n, map, d_V, K, out->rec, out->depth, out->radius)
+#define LGS_PRE_T(D)                                                       \
+    switch (g->sh_dtype) {                                                 \
+    case LGS_SH_BF16: LGS_PRE(D, LGS_SH_BF16); break;                      \
+    case LGS_SH_F16: LGS_PRE(D, LGS_SH_F16); break;                        \
+    default: LGS_PRE(D, LGS_SH_F32); break;                                \
     }
+    count_launch();
+    switch (g->sh_degree) {
+    case 0: LGS_PRE_T(0); break;
+    case 1: LGS_PRE_T(1); break;
+    case 2: LGS_PRE_T(2); break;
+    default: LGS_PRE_T(3); break;
+    }
+#undef LGS_PRE_T
+#undef LGS_PRE
     return check_launch();
 }
 

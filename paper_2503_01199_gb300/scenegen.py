@@ -63,16 +63,18 @@ def pinhole_camera(width: int, height: int, focal: float, R=None, t=None,
 
 
 def orbit_camera(radius: float, azimuth: float, elevation: float, width: int,
-                 height: int, focal_scale: float = 0.78) -> dict:
-    """Camera on a sphere of the given radius looking at the origin, up = +y.
+                 height: int, focal_scale: float = 0.78, center=(0.0, 0.0, 0.0)) -> dict:
+    """Camera on a sphere of the given radius around `center`, looking at it,
+    up = +y.
 
     Rows of R are the camera's x, y, z axes in world coordinates; the camera
     looks along +z (camera space), so a point in front has z > 0.
     """
-    c = radius * np.array([np.cos(elevation) * np.sin(azimuth),
-                           np.sin(elevation),
-                           np.cos(elevation) * np.cos(azimuth)])
-    fwd = -c / np.linalg.norm(c)
+    off = radius * np.array([np.cos(elevation) * np.sin(azimuth),
+                             np.sin(elevation),
+                             np.cos(elevation) * np.cos(azimuth)])
+    c = np.asarray(center, np.float64) + off
+    fwd = -off / np.linalg.norm(off)
     up = np.array([0.0, 1.0, 0.0])
     right = np.cross(up, fwd)
     right /= np.linalg.norm(right)
@@ -161,11 +163,34 @@ def surface_scene(n: int, sh_degree: int, seed: int, width: int, height: int,
 
 
 def orbit_cameras(seed: int, resolutions, radius: float = 4.0,
-                  elevation: float = 0.3) -> list:
+                  elevation: float = 0.3, center=(0.0, 0.0, 0.0)) -> list:
     """Cameras on a seeded orbit, one per (width, height)."""
     rng = _rng(seed)
     az = rng.uniform(0.0, 2.0 * np.pi, len(resolutions))
-    return [orbit_camera(radius, float(a), elevation, w, h) for a, (w, h) in zip(az, resolutions)]
+    return [orbit_camera(radius, float(a), elevation, w, h, center=center)
+            for a, (w, h) in zip(az, resolutions)]
+
+
+BOX_CENTER = (0.0, 0.0, 4.0)  # centre of the uniform-box scenes
+
+
+def render_requests(seed: int, duration_s: float, rate_hz: float, n_scenes: int,
+                    resolutions, radius: float = 4.0, center=BOX_CENTER) -> list:
+    """A seeded stream of render requests: Poisson arrivals at rate_hz over
+    duration_s seconds, each with a uniform scene index, a uniform
+    resolution from `resolutions` and an orbit camera (uniform azimuth,
+    elevation uniform in [-0.4, 0.4] rad) around `center`."""
+    rng = _rng(seed)
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            return out
+        sc = int(rng.integers(n_scenes))
+        w, h = resolutions[int(rng.integers(len(resolutions)))]
+        az, el = rng.uniform(0.0, 2.0 * np.pi), rng.uniform(-0.4, 0.4)
+        out.append({"arrival": t, "scene": sc, "camera": orbit_camera(radius, az, el, w, h,
+                                                                       center=center)})
 
 
 def random_splats(n: int, seed: int, width: int, height: int, max_radius: int = 40,
