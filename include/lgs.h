@@ -287,6 +287,38 @@ lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
                           int32_t *last_contrib, lgs_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Batched views (a5 / a7 for several cameras in one launch). One persistent
+ * kernel takes the tiles of all views from a shared counter, so views of
+ * different sizes fill the GPU together. The table of views lives in
+ * DEVICE memory (it is read by the kernels; its contents may stay fixed
+ * across replays of a captured graph). Tiles are numbered view after view:
+ * view v owns tiles tile_offset[v] .. tile_offset[v] + tiles(v) - 1, with
+ * tile_offset increasing and tile_offset[0] = 0; total_tiles is the sum.
+ * Each view is rendered exactly as lgs_raster_fwd / lgs_raster_bwd render
+ * it alone (16 x 16 tiles); the backward always adds into grad_acc, which
+ * the caller zeroes. counter: one device uint32 of scratch (zeroed by the
+ * call). n_views <= 1024.
+ * ---------------------------------------------------------------------- */
+typedef struct lgs_view {
+    const float *rec;             /* splat records of this view (lgs_splats.rec) */
+    const uint32_t *vals;         /* tile lists of this view (lgs_bin_sort) */
+    const uint32_t *tile_ranges;  /* [tiles][2] (lgs_bin_sort) */
+    float *image;                 /* forward out: [3][height][width] */
+    float *final_T;               /* forward out, backward in: [height][width] */
+    int32_t *last_contrib;        /* forward out, backward in: [height][width] */
+    const float *dL_dimage;       /* backward in: [3][height][width] */
+    float *grad_acc;              /* backward: rows added as by lgs_raster_bwd */
+    int32_t width, height;
+    uint32_t tile_offset;
+    float bg[3];
+} lgs_view;
+
+lgs_status lgs_raster_fwd_batch(const lgs_view *d_views, int32_t n_views, uint32_t total_tiles,
+                                int32_t precision, uint32_t *d_counter, lgs_stream stream);
+lgs_status lgs_raster_bwd_batch(const lgs_view *d_views, int32_t n_views, uint32_t total_tiles,
+                                int32_t precision, uint32_t *d_counter, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
  * a6. L1 photometric loss (the paper does not state its loss; this is the
  * L1 term of 3DGS): loss = mean |image - target| over n values,
  * dL_dimage = sign(image - target) / n (sign(0) = 0). *d_loss (device) is
@@ -328,13 +360,15 @@ lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,
 
 /* ------------------------------------------------------------------------
  * a9. Preprocess backward: the chain rule through a3 from grad_acc rows
- * 0..8 to the parameter planes. For j < V, writes plane k, row map[j] of
- * grad_planes (stride g->stride, LGS_NUM_PLANES(deg) planes); other rows are
- * not touched. Every clamp passes zero gradient while active.
+ * 0..8 to the parameter planes. For j < V, writes (accumulate = 0) or adds
+ * to (accumulate = 1, e.g. summing the views of a batch) plane k, row map[j]
+ * of grad_planes (stride g->stride, LGS_NUM_PLANES(deg) planes); other rows
+ * are not touched. Every clamp passes zero gradient while active.
  * ---------------------------------------------------------------------- */
 lgs_status lgs_preprocess_bwd(const lgs_gaussians *g, const uint32_t *map,
                               const int32_t *d_num_visible, const lgs_camera *cam,
-                              const float *grad_acc, float *grad_planes, lgs_stream stream);
+                              const float *grad_acc, float *grad_planes, int32_t accumulate,
+                              lgs_stream stream);
 
 /* ------------------------------------------------------------------------
  * a10. Adam on visible rows only (Sec. 3.2.3: sparse update at cluster

@@ -29,7 +29,7 @@ ENTRY_POINTS = (
     "lgs_compact_gather", "lgs_preprocess",
     "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow",
     "lgs_raster_fwd",
-    "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
+    "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
     "lgs_adam_step", "lgs_preprocess_bwd_adam",
 )
 
@@ -56,6 +56,15 @@ class LgsSplats(ctypes.Structure):
                 ("capacity", ctypes.c_int64)]
 
 
+class LgsView(ctypes.Structure):
+    _fields_ = [("rec", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("tile_ranges", ctypes.c_void_p), ("image", ctypes.c_void_p),
+                ("final_T", ctypes.c_void_p), ("last_contrib", ctypes.c_void_p),
+                ("dL_dimage", ctypes.c_void_p), ("grad_acc", ctypes.c_void_p),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("tile_offset", ctypes.c_uint32), ("bg", ctypes.c_float * 3)]
+
+
 class LgsError(RuntimeError):
     pass
 
@@ -79,6 +88,7 @@ def load(build_if_missing: bool = True):
         raise LgsError(f"liblgs.so not found at {path}; run paper_2503_01199_gb300/build.py")
     L = ctypes.CDLL(str(path))
     P, i32, i64, f32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    u32 = ctypes.c_uint32
     sig = {
         "lgs_version": (ctypes.c_char_p, []),
         "lgs_last_cuda_error": (i32, []),
@@ -97,7 +107,9 @@ def load(build_if_missing: bool = True):
         "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
         "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P, i64, i32, P]),
         "lgs_opacity_variance": (i32, [P, P, P, i64, P, P]),
-        "lgs_preprocess_bwd": (i32, [P, P, P, P, P, P, P]),
+        "lgs_preprocess_bwd": (i32, [P, P, P, P, P, P, i32, P]),
+        "lgs_raster_fwd_batch": (i32, [P, i32, u32, i32, P, P]),
+        "lgs_raster_bwd_batch": (i32, [P, i32, u32, i32, P, P]),
         "lgs_adam_step": (i32, [P, P, P, P, i64, i32, P, f32, f32, f32, i32, P, P, i64, P]),
         "lgs_preprocess_bwd_adam": (i32, [P, P, P, P, P, P, P, P, f32, f32, f32, i32, P]),
     }
@@ -275,6 +287,40 @@ def lgs_raster_fwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, til
                             _ptr(last_contrib), _stream(stream)), "lgs_raster_fwd")
 
 
+def view_table(views: list, tile=(16, 16), device="cuda") -> tuple[torch.Tensor, int]:
+    """Device table of lgs_view for the batched raster calls.
+    views: dicts with rec, vals, ranges, image, final_T, last (tensors), and
+    optionally dL_dimage, grad_acc, plus the camera dict 'camera' (width,
+    height, bg). Returns (uint8 CUDA tensor holding the table, total tiles)."""
+    arr = (LgsView * len(views))()
+    off = 0
+    for i, v in enumerate(views):
+        cam = v["camera"]
+        w, h = int(cam["width"]), int(cam["height"])
+        e = arr[i]
+        e.rec, e.vals, e.tile_ranges = _ptr(v["rec"]), _ptr(v["vals"]), _ptr(v["ranges"])
+        e.image, e.final_T, e.last_contrib = _ptr(v["image"]), _ptr(v["final_T"]), _ptr(v["last"])
+        e.dL_dimage, e.grad_acc = _ptr(v.get("dL_dimage")), _ptr(v.get("grad_acc"))
+        e.width, e.height, e.tile_offset = w, h, off
+        e.bg[:] = [float(x) for x in np.asarray(cam["bg"]).reshape(3)]
+        off += -(-w // tile[0]) * -(-h // tile[1])
+    raw = bytes(arr)
+    table = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+    return table, off
+
+
+def lgs_raster_fwd_batch(table, n_views, total_tiles, counter, precision=LGS_FP32, stream=None):
+    L = load()
+    _check(L.lgs_raster_fwd_batch(_ptr(table), int(n_views), int(total_tiles), int(precision),
+                                  _ptr(counter), _stream(stream)), "lgs_raster_fwd_batch")
+
+
+def lgs_raster_bwd_batch(table, n_views, total_tiles, counter, precision=LGS_FP32, stream=None):
+    L = load()
+    _check(L.lgs_raster_bwd_batch(_ptr(table), int(n_views), int(total_tiles), int(precision),
+                                  _ptr(counter), _stream(stream)), "lgs_raster_bwd_batch")
+
+
 def lgs_loss_l1(image, target, dL_dimage, d_loss, stream=None):
     L = load()
     _check(L.lgs_loss_l1(_ptr(image), _ptr(target), image.numel(), _ptr(dL_dimage), _ptr(d_loss),
@@ -298,11 +344,11 @@ def lgs_opacity_variance(grad_acc, map_, d_num_visible, max_rows, metric, stream
 
 
 def lgs_preprocess_bwd(g: LgsGaussians, map_, d_num_visible, cam: LgsCamera, grad_acc,
-                       grad_planes, stream=None):
+                       grad_planes, stream=None, accumulate=False):
     L = load()
     _check(L.lgs_preprocess_bwd(ctypes.byref(g), _ptr(map_), _ptr(d_num_visible),
                                 ctypes.byref(cam), _ptr(grad_acc), _ptr(grad_planes),
-                                _stream(stream)), "lgs_preprocess_bwd")
+                                int(bool(accumulate)), _stream(stream)), "lgs_preprocess_bwd")
 
 
 def _lr_array(lr) -> ctypes.Array:

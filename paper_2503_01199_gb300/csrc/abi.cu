@@ -26,7 +26,8 @@ lgs_status cluster_cull_compact_noalloc(const lgs_gaussians *g, const lgs_camera
 lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
                       const lgs_camera *cam, int tw, int th, const lgs_splats *out, cudaStream_t s);
 lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
-                          const lgs_camera *cam, const float *gacc, float *gout, cudaStream_t s);
+                          const lgs_camera *cam, const float *gacc, float *gout, int accumulate,
+                          cudaStream_t s);
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
                                const int32_t *d_V, const lgs_camera *cam, float *gacc,
                                const float *lr, float b1, float b2, float eps, int step,
@@ -48,6 +49,8 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
                       int accumulate, cudaStream_t s);
 lgs_status loss_l1(const float *img, const float *tgt, int64_t n, float *g, float *loss,
                    cudaStream_t s);
+lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles, int precision,
+                        uint32_t *counter, int backward, cudaStream_t s);
 lgs_status opacity_variance(const float *gacc, const uint32_t *map, const int32_t *d_V,
                             int64_t max_rows, float *out, cudaStream_t s);
 
@@ -224,6 +227,22 @@ lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
                       last_contrib, as_stream(stream));
 }
 
+lgs_status lgs_raster_fwd_batch(const lgs_view *d_views, int32_t n_views, uint32_t total_tiles,
+                                int32_t precision, uint32_t *d_counter, lgs_stream stream) {
+    if (!d_views || n_views < 1 || n_views > 1024 || !d_counter || precision < LGS_FP32 ||
+        precision > LGS_MIXED_BF16)
+        return LGS_ERR_INVALID_ARG;
+    return raster_batch(d_views, n_views, total_tiles, precision, d_counter, 0, as_stream(stream));
+}
+
+lgs_status lgs_raster_bwd_batch(const lgs_view *d_views, int32_t n_views, uint32_t total_tiles,
+                                int32_t precision, uint32_t *d_counter, lgs_stream stream) {
+    if (!d_views || n_views < 1 || n_views > 1024 || !d_counter || precision < LGS_FP32 ||
+        precision > LGS_MIXED_BF16)
+        return LGS_ERR_INVALID_ARG;
+    return raster_batch(d_views, n_views, total_tiles, precision, d_counter, 1, as_stream(stream));
+}
+
 lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float *dL_dimage,
                        float *d_loss, lgs_stream stream) {
     if (!image || !target || !dL_dimage || !d_loss || n <= 0) return LGS_ERR_INVALID_ARG;
@@ -253,12 +272,14 @@ lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,
 
 lgs_status lgs_preprocess_bwd(const lgs_gaussians *g, const uint32_t *map,
                               const int32_t *d_num_visible, const lgs_camera *cam,
-                              const float *grad_acc, float *grad_planes, lgs_stream stream) {
+                              const float *grad_acc, float *grad_planes, int32_t accumulate,
+                              lgs_stream stream) {
     if (bad_gaussians(g) || bad_camera(cam) || !grad_acc || !grad_planes || !aligned16(grad_acc) ||
         training_only(g, cam))
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
-    return preprocess_bwd(g, map, d_num_visible, cam, grad_acc, grad_planes, as_stream(stream));
+    return preprocess_bwd(g, map, d_num_visible, cam, grad_acc, grad_planes, accumulate,
+                          as_stream(stream));
 }
 
 lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, int64_t stride,

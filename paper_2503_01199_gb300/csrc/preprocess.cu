@@ -505,7 +505,11 @@ __device__ __forceinline__ void adam_update(float &p, float &m, float &v, float 
 struct GradSink {
     float *__restrict__ out;
     int64_t stride, row;
-    __device__ __forceinline__ void operator()(int k, float g) { out[k * stride + row] = g; }
+    bool add;
+    __device__ __forceinline__ void operator()(int k, float g) {
+        float &o = out[k * stride + row];
+        o = add ? o + g : g;
+    }
 };
 
 template <int DEG>
@@ -514,12 +518,13 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__rest
                                                             const uint32_t *__restrict__ map,
                                                             const int32_t *d_V, Cam K,
                                                             const float *__restrict__ gacc,
-                                                            float *__restrict__ gout) {
+                                                            float *__restrict__ gout,
+                                                            int accumulate) {
     const int64_t V = load_count(d_V, n);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = map ? map[j] : j;
-        GradSink sink{gout, stride, row};
+        GradSink sink{gout, stride, row, accumulate != 0};
         backward<DEG>(K, P, stride, row, gacc + 16 * j, sink);
     }
 }
@@ -702,14 +707,15 @@ lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t
 }
 
 lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
-                          const lgs_camera *cam, const float *gacc, float *gout, cudaStream_t s) {
+                          const lgs_camera *cam, const float *gacc, float *gout, int accumulate,
+                          cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const unsigned grid = grid_for(g->n, kThreads, 16);
     switch (g->sh_degree) {
-    case 0: count_launch(); k_preprocess_bwd<0><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
-    case 1: count_launch(); k_preprocess_bwd<1><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
-    case 2: count_launch(); k_preprocess_bwd<2><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
-    default: count_launch(); k_preprocess_bwd<3><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout); break;
+    case 0: count_launch(); k_preprocess_bwd<0><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout, accumulate); break;
+    case 1: count_launch(); k_preprocess_bwd<1><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout, accumulate); break;
+    case 2: count_launch(); k_preprocess_bwd<2><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout, accumulate); break;
+    default: count_launch(); k_preprocess_bwd<3><<<grid, kThreads, 0, s>>>(g->data, g->stride, g->n, map, d_V, K, gacc, gout, accumulate); break;
     }
     return check_launch();
 }

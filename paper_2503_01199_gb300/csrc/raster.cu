@@ -138,16 +138,14 @@ __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, floa
     }
 }
 
+// One tile of the forward pass, by the whole CTA.
 template <int PREC>
-__global__ void __launch_bounds__(kBatch) k_raster_fwd(const float *__restrict__ rec,
-                                                     const uint32_t *__restrict__ vals,
-                                                     const uint32_t *__restrict__ ranges, RCam K,
-                                                     float *__restrict__ image,
-                                                     float *__restrict__ finalT,
-                                                     int32_t *__restrict__ last) {
-    __shared__ SplatS s_sp[kBatch];
-    __shared__ uint8_t s_fl[kBatch];
-    const int tile = blockIdx.x;
+__device__ __forceinline__ void fwd_tile(const float *__restrict__ rec,
+                                         const uint32_t *__restrict__ vals,
+                                         const uint32_t *__restrict__ ranges, const RCam &K,
+                                         int tile, float *__restrict__ image,
+                                         float *__restrict__ finalT, int32_t *__restrict__ last,
+                                         SplatS *s_sp, uint8_t *s_fl) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
     const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
@@ -210,6 +208,18 @@ __global__ void __launch_bounds__(kBatch) k_raster_fwd(const float *__restrict__
     }
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(kBatch) k_raster_fwd(const float *__restrict__ rec,
+                                                     const uint32_t *__restrict__ vals,
+                                                     const uint32_t *__restrict__ ranges, RCam K,
+                                                     float *__restrict__ image,
+                                                     float *__restrict__ finalT,
+                                                     int32_t *__restrict__ last) {
+    __shared__ SplatS s_sp[kBatch];
+    __shared__ uint8_t s_fl[kBatch];
+    fwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, image, finalT, last, s_sp, s_fl);
+}
+
 // Reduce-scatter of 16 values across the warp: on return v[0] of lanes 2i
 // and 2i + 1 holds the warp sum of input value i.
 __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
@@ -243,16 +253,16 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// One tile of the backward pass, by the whole CTA.
 template <int PREC>
-__global__ void __launch_bounds__(kBatch) k_raster_bwd(
-    const float *__restrict__ rec, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ ranges, RCam K, const float *__restrict__ finalT,
-    const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc) {
-    __shared__ SplatS s_sp[kBatch];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ uint8_t s_fl[kBatch];
-    __shared__ int s_maxlast;
-    const int tile = blockIdx.x;
+__device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
+                                         const uint32_t *__restrict__ vals,
+                                         const uint32_t *__restrict__ ranges, const RCam &K,
+                                         int tile, const float *__restrict__ finalT,
+                                         const int32_t *__restrict__ last,
+                                         const float *__restrict__ dLdI, float *__restrict__ gacc,
+                                         SplatS *s_sp, uint32_t *s_id, uint8_t *s_fl,
+                                         int &s_maxlast) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
     const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
@@ -378,6 +388,85 @@ __global__ void __launch_bounds__(kBatch) k_raster_bwd(
     }
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(kBatch) k_raster_bwd(
+    const float *__restrict__ rec, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ ranges, RCam K, const float *__restrict__ finalT,
+    const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc) {
+    __shared__ SplatS s_sp[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ uint8_t s_fl[kBatch];
+    __shared__ int s_maxlast;
+    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, s_sp, s_id, s_fl,
+                   s_maxlast);
+}
+
+// ---------------------------------------------------------------------------
+// Batched views: persistent CTAs take tiles of all views from one atomic
+// counter (tiles numbered view by view from each view's tile_offset).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int view_of(const lgs_view *views, int n_views, uint32_t t) {
+    int v = 0;
+    while (v + 1 < n_views && views[v + 1].tile_offset <= t) ++v;
+    return v;
+}
+
+__device__ __forceinline__ RCam view_rcam(const lgs_view &V) {
+    RCam K;
+    K.W = V.width;
+    K.H = V.height;
+    K.gx = (V.width + kTile - 1) / kTile;
+    K.ntiles = K.gx * ((V.height + kTile - 1) / kTile);
+    K.bg[0] = V.bg[0];
+    K.bg[1] = V.bg[1];
+    K.bg[2] = V.bg[2];
+    return K;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kBatch) k_raster_fwd_batch(const lgs_view *__restrict__ views,
+                                                           int n_views, uint32_t total_tiles,
+                                                           uint32_t *counter) {
+    __shared__ SplatS s_sp[kBatch];
+    __shared__ uint8_t s_fl[kBatch];
+    __shared__ uint32_t s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= total_tiles) break;
+        const int v = view_of(views, n_views, t);
+        const lgs_view &V = views[v];
+        const RCam K = view_rcam(V);
+        fwd_tile<PREC>(V.rec, V.vals, V.tile_ranges, K, (int)(t - V.tile_offset), V.image,
+                       V.final_T, V.last_contrib, s_sp, s_fl);
+        __syncthreads();
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kBatch) k_raster_bwd_batch(const lgs_view *__restrict__ views,
+                                                           int n_views, uint32_t total_tiles,
+                                                           uint32_t *counter) {
+    __shared__ SplatS s_sp[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ uint8_t s_fl[kBatch];
+    __shared__ int s_maxlast;
+    __shared__ uint32_t s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= total_tiles) break;
+        const int v = view_of(views, n_views, t);
+        const lgs_view &V = views[v];
+        const RCam K = view_rcam(V);
+        bwd_tile<PREC>(V.rec, V.vals, V.tile_ranges, K, (int)(t - V.tile_offset), V.final_T,
+                       V.last_contrib, V.dL_dimage, V.grad_acc, s_sp, s_id, s_fl, s_maxlast);
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) k_loss_l1(const float *__restrict__ img,
                                                 const float *__restrict__ tgt, int64_t n,
                                                 float *__restrict__ g, float *loss) {
@@ -470,6 +559,29 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
             k_raster_bwd<LGS_MIXED_BF16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
             break;
     }
+    return check_launch();
+}
+
+lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles, int precision,
+                        uint32_t *counter, int backward, cudaStream_t s) {
+    cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    int per_sm = 0;
+    if (backward)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd_batch<LGS_FP32>, kBatch, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd_batch<LGS_FP32>, kBatch, 0);
+    const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(total_tiles < cap ? total_tiles : cap);
+    if (grid == 0) return LGS_OK;
+    count_launch();
+#define LGS_RB(P) do { if (backward) k_raster_bwd_batch<P><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); \
+                       else k_raster_fwd_batch<P><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); } while (0)
+    switch (precision) {
+        case LGS_MIXED_FP16: LGS_RB(LGS_MIXED_FP16); break;
+        case LGS_MIXED_BF16: LGS_RB(LGS_MIXED_BF16); break;
+        default: LGS_RB(LGS_FP32); break;
+    }
+#undef LGS_RB
     return check_launch();
 }
 

@@ -198,3 +198,110 @@ class Trainer:
         self.backward(cs, target)
         self.optimize(cs, fused=fused)
         return self.loss
+
+
+class MultiView:
+    """Forward + backward of one scene for several cameras at once.
+
+    Per view: cluster cull + compaction, preprocess and binning (each view
+    keeps its own map, splats and tile lists); then ONE batched raster
+    forward over the tiles of all views, the L1 loss gradient of each view,
+    ONE batched raster backward, and per view the preprocess backward adding
+    into one gradient buffer (the parameters' gradient summed over views).
+    `capture()` records the whole sequence as one CUDA graph; `run_sequential`
+    is the same work with one plain launch sequence per view.
+    """
+
+    def __init__(self, planes: torch.Tensor, n: int, sh_degree: int, cams: list, targets: list,
+                 pair_capacity: int, tile=(16, 16), cluster: int = 128, device="cuda"):
+        self.planes, self.n, self.deg = planes, int(n), int(sh_degree)
+        self.cams = cams
+        self.tile, self.cluster = tuple(tile), int(cluster)
+        self.cap = int(pair_capacity)
+        dev = self.dev = torch.device(device)
+        tw, th = self.tile
+        self.g = B.gaussians_struct(planes, n, sh_degree)
+        self.cs = [B.camera_struct(c) for c in cams]
+        nt = [-(-c["width"] // tw) * -(-c["height"] // th) for c in cams]
+        self.ws_ccc = torch.empty(B.lgs_ccc_workspace_size(n, cluster), dtype=torch.uint8,
+                                  device=dev)
+        self.ws_bin = torch.empty(B.lgs_bin_sort_workspace_size(n, self.cap, max(nt)),
+                                  dtype=torch.uint8, device=dev)
+        self.cluster_visible = torch.empty(-(-n // cluster), dtype=torch.int32, device=dev)
+        self.gacc = torch.zeros((len(cams), n, B.GRAD_FLOATS), dtype=torch.float32, device=dev)
+        self.grad = torch.zeros_like(planes)
+        self.counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.views = []
+        for k, (c, tgt) in enumerate(zip(cams, targets)):
+            W, H = int(c["width"]), int(c["height"])
+            v = {"camera": c,
+                 "rowmap": torch.empty(n, dtype=torch.int32, device=dev),
+                 "d_V": torch.zeros(1, dtype=torch.int32, device=dev),
+                 "rec": torch.empty((n, B.SPLAT_FLOATS), dtype=torch.float32, device=dev),
+                 "depth": torch.empty(n, dtype=torch.float32, device=dev),
+                 "radius": torch.empty(n, dtype=torch.int32, device=dev),
+                 "vals": torch.empty(self.cap, dtype=torch.int32, device=dev),
+                 "d_P": torch.zeros(1, dtype=torch.int64, device=dev),
+                 "ranges": torch.empty((nt[k], 2), dtype=torch.int32, device=dev),
+                 "image": torch.empty((3, H, W), dtype=torch.float32, device=dev),
+                 "final_T": torch.empty((H, W), dtype=torch.float32, device=dev),
+                 "last": torch.empty((H, W), dtype=torch.int32, device=dev),
+                 "dL_dimage": torch.empty((3, H, W), dtype=torch.float32, device=dev),
+                 "loss": torch.zeros(1, dtype=torch.float32, device=dev),
+                 "target": tgt, "grad_acc": self.gacc[k]}
+            v["splats"] = B.splats_struct(v["rec"], v["depth"], v["radius"])
+            self.views.append(v)
+        self.table, self.total_tiles = B.view_table(self.views, self.tile, device=dev)
+        self.graph = None
+
+    def _front(self, k: int):
+        v, cs = self.views[k], self.cs[k]
+        tw, th = self.tile
+        B.lgs_cluster_cull_compact(self.g, cs, self.cluster, None, self.cluster_visible,
+                                   v["rowmap"], v["d_V"], self.ws_ccc)
+        B.lgs_preprocess(self.g, v["rowmap"], v["d_V"], cs, tw, th, v["splats"])
+        B.lgs_bin_sort(v["splats"], v["d_V"], self.n, cs, tw, th, v["vals"], v["d_P"],
+                       v["ranges"], self.ws_bin)
+
+    def run_batched(self, precision=B.LGS_FP32):
+        for k in range(len(self.views)):
+            self._front(k)
+        B.lgs_raster_fwd_batch(self.table, len(self.views), self.total_tiles, self.counter,
+                               precision=precision)
+        for v in self.views:
+            B.lgs_loss_l1(v["image"], v["target"], v["dL_dimage"], v["loss"])
+        self.gacc.zero_()
+        B.lgs_raster_bwd_batch(self.table, len(self.views), self.total_tiles, self.counter,
+                               precision=precision)
+        for k, v in enumerate(self.views):
+            B.lgs_preprocess_bwd(self.g, v["rowmap"], v["d_V"], self.cs[k], v["grad_acc"],
+                                 self.grad, accumulate=k > 0)
+
+    def run_sequential(self, precision=B.LGS_FP32):
+        tw, th = self.tile
+        for k, v in enumerate(self.views):
+            cs = self.cs[k]
+            self._front(k)
+            B.lgs_raster_fwd(v["splats"], v["vals"], v["ranges"], cs, tw, th, v["image"],
+                             v["final_T"], v["last"], precision=precision)
+            B.lgs_loss_l1(v["image"], v["target"], v["dL_dimage"], v["loss"])
+            B.lgs_raster_bwd(v["splats"], v["vals"], v["ranges"], cs, tw, th, v["final_T"],
+                             v["last"], v["dL_dimage"], v["grad_acc"], precision=precision)
+            B.lgs_preprocess_bwd(self.g, v["rowmap"], v["d_V"], cs, v["grad_acc"], self.grad,
+                                 accumulate=k > 0)
+
+    def capture(self, precision=B.LGS_FP32):
+        """Records run_batched as one CUDA graph (after one eager run)."""
+        side = torch.cuda.Stream(device=self.dev)
+        side.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(side):
+            self.run_batched(precision)
+        side.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=side):
+            self.run_batched(precision)
+        torch.cuda.current_stream(self.dev).wait_stream(side)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
