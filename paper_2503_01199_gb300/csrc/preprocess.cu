@@ -559,7 +559,7 @@ struct GeomSink {
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(kThreads) k_bwd_adam_geom(
+__global__ void __launch_bounds__(kThreads, 6) k_bwd_adam_geom(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
     int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
     float *__restrict__ gacc, AdamArgs a) {
@@ -601,7 +601,7 @@ __device__ __forceinline__ float sh_single(int k, float x, float y, float z) {
 constexpr int kChunk = 2048;
 
 template <int DEG>
-__global__ void __launch_bounds__(256) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
+__global__ void __launch_bounds__(256, 6) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
                                                     float *__restrict__ Vo, int64_t stride,
                                                     int64_t n, const uint32_t *__restrict__ map,
                                                     const int32_t *d_V,
@@ -629,22 +629,21 @@ __global__ void __launch_bounds__(256) k_bwd_adam_sh(float *__restrict__ P, floa
         const float4 s1 = reinterpret_cast<const float4 *>(gacc + 16 * j)[3];
         const float grgb[3] = {s0.x, s0.y, s1.x};
         const float yk = sh_single(k, s1.y, s1.z, s1.w);
+        const int64_t at = (11 + 3 * k) * stride + row;
+        float *pp = P + at, *pm = Mo + at, *pv = Vo + at;
         float p[3], m[3], v[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const int64_t i = (11 + 3 * k + ch) * stride + row;
-            p[ch] = P[i];
-            m[ch] = Mo[i];
-            v[ch] = Vo[i];
+            p[ch] = pp[ch * stride];
+            m[ch] = pm[ch * stride];
+            v[ch] = pv[ch * stride];
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const int pl = 11 + 3 * k + ch;
-            adam_update(p[ch], m[ch], v[ch], grgb[ch] * yk, a.lr[pl], a);
-            const int64_t i = pl * stride + row;
-            P[i] = p[ch];
-            Mo[i] = m[ch];
-            Vo[i] = v[ch];
+            adam_update(p[ch], m[ch], v[ch], grgb[ch] * yk, a.lr[11 + 3 * k + ch], a);
+            pp[ch * stride] = p[ch];
+            pm[ch * stride] = m[ch];
+            pv[ch * stride] = v[ch];
         }
     }
 }
