@@ -103,6 +103,9 @@ def lib():
             "or_opacity_variance": (None, [i64, P, P, P, P]),
             "or_preprocess_bwd": (None, [i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]),
             "or_adam": (None, [i64, i32, P, P, P, P, P, f64, f64, f64, i32, P, i64]),
+            "or_densify": (i64, [i64, i32, i64, P, P, P, P, i64, f64, P, P]),
+            "or_opacity_decay": (None, [i64, P]),
+            "or_moments_accumulate": (None, [i64, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -354,6 +357,40 @@ def adam(param, grad, m, v, lr, step: int, rows, beta1=0.9, beta2=0.999, eps=1e-
 # --------------------------------------------------------------------------
 # parameter planes (the order the step uses for Adam and the reorder)
 # --------------------------------------------------------------------------
+def densify(planes, m, v, metric, K: int, split_scale: float, normals) -> dict:
+    """Variance-driven clone / split (Sec. 3.3, readings in lgs_oracle.c).
+    planes, m, v: float64 [nplanes, stride] with stride >= n + K (copied);
+    metric: C Var per Gaussian [n]; normals: standard normal samples
+    [K, 2, 3]. Returns the new planes, m, v, the new count and the selected
+    rows in selection order."""
+    planes = np.array(planes, np.float64, order="C", copy=True)
+    m = np.array(m, np.float64, order="C", copy=True)
+    v = np.array(v, np.float64, order="C", copy=True)
+    metric = _c(metric, np.float64)
+    normals = _c(normals, np.float64)
+    n = metric.shape[0]
+    assert planes.shape[1] >= n + K and normals.size >= 6 * K
+    sel = np.zeros(max(K, 1), np.int64)
+    n_new = lib().or_densify(n, planes.shape[0], planes.shape[1], _p(planes), _p(m), _p(v),
+                             _p(metric), K, float(split_scale), _p(normals), _p(sel))
+    return {"planes": planes, "m": m, "v": v, "n": int(n_new), "selected": sel[:n_new - n]}
+
+
+def opacity_decay(logit) -> np.ndarray:
+    out = np.array(logit, np.float64, copy=True)
+    lib().or_opacity_decay(out.size, _p(out))
+    return out
+
+
+def moments_accumulate(rows, S, M, C, S_acc, M_acc, C_acc):
+    """Adds one view's moments of its visible rows into per-Gaussian sums (in place)."""
+    rows, S, M, C = _c(rows, np.uint32), _c(S, np.float64), _c(M, np.float64), _c(C, np.int64)
+    for a, t in ((S_acc, np.float64), (M_acc, np.float64), (C_acc, np.int64)):
+        assert a.dtype == t and a.flags.c_contiguous
+    lib().or_moments_accumulate(rows.size, _p(rows), _p(S), _p(M), _p(C), _p(S_acc), _p(M_acc),
+                                _p(C_acc))
+
+
 def scene_planes(scene: dict) -> np.ndarray:
     """Stack a scene into planes [11 + 3K, N]: mean(3), log-scale(3),
     quat(4), logit, then SH coefficient k channel c at 11 + 3k + c."""

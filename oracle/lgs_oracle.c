@@ -983,3 +983,110 @@ void or_adam(int64_t nrows, int nplanes, double *param, const double *grad, doub
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Densification by the opacity-gradient variance (Sec. 3.3).               */
+/* The paper gives the criterion (C Var = S - M^2 / C, sums over the views  */
+/* of the interval) and says high-variance Gaussians are split or cloned,   */
+/* inheriting the mechanics of 3DGS without restating them. Readings:       */
+/*  - candidates are Gaussians with C Var > 0; the K largest are taken      */
+/*    (ties: lower index first);                                            */
+/*  - a selected Gaussian whose largest scale exceeds split_scale is split: */
+/*    two samples x = p + R(q) (s * z) with z ~ N(0, I) (drawn by the       */
+/*    caller and passed in, two per selection), both with scales s / 1.6;   */
+/*    the first replaces the original row, the second is appended;          */
+/*  - otherwise it is cloned: an exact copy is appended;                    */
+/*  - appended rows and split rows start with zero Adam moments; the        */
+/*    original row of a clone keeps its moments.                            */
+/* Planes are [nplanes][stride] with stride >= n + K. Returns the new count. */
+/* ------------------------------------------------------------------------ */
+static const double OR_SPLIT_SCALE_DIV = 1.6;
+
+int64_t or_densify(int64_t n, int nplanes, int64_t stride, double *planes, double *m, double *v,
+                   const double *metric, int64_t K, double split_scale, const double *normals,
+                   int64_t *selected) {
+    /* selection: candidates in index order, then a stable merge sort by
+     * descending metric (ties keep index order) */
+    int64_t nc = 0;
+    for (int64_t i = 0; i < n; ++i) nc += metric[i] > 0.0;
+    uint32_t *idx = (uint32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(uint32_t));
+    uint32_t *tmp = (uint32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(uint32_t));
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (metric[i] > 0.0) idx[c++] = (uint32_t)i;
+    for (int64_t w = 1; w < nc; w *= 2) {
+        for (int64_t lo = 0; lo < nc; lo += 2 * w) {
+            int64_t mid = lo + w < nc ? lo + w : nc, hi = lo + 2 * w < nc ? lo + 2 * w : nc;
+            int64_t a = lo, b = mid, o = lo;
+            while (a < mid && b < hi) tmp[o++] = metric[idx[b]] > metric[idx[a]] ? idx[b++] : idx[a++];
+            while (a < mid) tmp[o++] = idx[a++];
+            while (b < hi) tmp[o++] = idx[b++];
+        }
+        memcpy(idx, tmp, (size_t)nc * sizeof(uint32_t));
+    }
+    int64_t kk = K < nc ? K : nc;
+    for (int64_t r = 0; r < kk; ++r) {
+        int64_t i = idx[r], j = n + r;
+        if (selected) selected[r] = i;
+        double s[3], ls[3], q[4], R[9];
+        for (int a = 0; a < 3; ++a) {
+            ls[a] = planes[(3 + a) * stride + i];
+            s[a] = exp(ls[a]);
+        }
+        double smax = s[0] > s[1] ? (s[0] > s[2] ? s[0] : s[2]) : (s[1] > s[2] ? s[1] : s[2]);
+        for (int pl = 0; pl < nplanes; ++pl) {
+            planes[pl * stride + j] = planes[pl * stride + i];
+            m[pl * stride + j] = 0.0;
+            v[pl * stride + j] = 0.0;
+        }
+        if (smax > split_scale) {
+            double qn = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                q[a] = planes[(6 + a) * stride + i];
+                qn += q[a] * q[a];
+            }
+            qn = sqrt(qn);
+            for (int a = 0; a < 4; ++a) q[a] /= qn;
+            quat_to_rot(q, R);
+            double p[3] = {planes[i], planes[stride + i], planes[2 * stride + i]};
+            for (int h = 0; h < 2; ++h) {
+                const double *z = normals + 6 * r + 3 * h;
+                int64_t row = h == 0 ? i : j;
+                for (int a = 0; a < 3; ++a) {
+                    double x = p[a];
+                    for (int b = 0; b < 3; ++b) x += R[3 * a + b] * s[b] * z[b];
+                    planes[a * stride + row] = x;
+                    planes[(3 + a) * stride + row] = ls[a] - log(OR_SPLIT_SCALE_DIV);
+                }
+            }
+            for (int pl = 0; pl < nplanes; ++pl) {
+                m[pl * stride + i] = 0.0;
+                v[pl * stride + i] = 0.0;
+            }
+        }
+    }
+    free(idx);
+    free(tmp);
+    return n + kk;
+}
+
+/* Opacity decay (Sec. 3.3): the activated opacity is halved,
+ * sigmoid(logit') = sigmoid(logit) / 2, i.e. logit' = -log(1 + 2 exp(-logit)). */
+void or_opacity_decay(int64_t n, double *logit) {
+    for (int64_t i = 0; i < n; ++i) {
+        double o = 1.0 / (1.0 + exp(-logit[i]));
+        double h = 0.5 * o;
+        logit[i] = log(h / (1.0 - h));
+    }
+}
+
+/* Moments summed over views (Sec. 3.3: S, M, C are sums over the views of
+ * the interval): S[row] += S_j etc. for the visible rows of one view. */
+void or_moments_accumulate(int64_t nvis, const uint32_t *rows, const double *S, const double *M,
+                           const int64_t *C, double *S_acc, double *M_acc, int64_t *C_acc) {
+    for (int64_t j = 0; j < nvis; ++j) {
+        S_acc[rows[j]] += S[j];
+        M_acc[rows[j]] += M[j];
+        C_acc[rows[j]] += C[j];
+    }
+}
