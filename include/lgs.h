@@ -397,6 +397,43 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Densification (Sec. 3.3; the step after a8 that consumes its metric).
+ *
+ * lgs_moments_accumulate adds one view's moments to per-Gaussian sums over
+ * the views of an interval (S, M float, C uint32, indexed by row; the
+ * caller zeroes them at the start of the interval):
+ *   S[map[j]] += grad_acc[j].S, M[map[j]] += grad_acc[j].M, C[...] += .C.
+ * lgs_moments_metric: metric[i] = S - M^2 / C (0 if C = 0), i < n.
+ *
+ * lgs_densify: candidates are Gaussians with metric > 0; the max_new with
+ * the largest metric are selected (ties: lower index first). A selected
+ * Gaussian whose largest scale exp(log-scale) exceeds split_scale is split
+ * (the readings of the 3DGS mechanics the paper inherits): two samples
+ * p + R(q) (s * z), z from `normals` (device, [max_new][2][3] standard
+ * normal values, drawn by the caller), both with log-scales - ln 1.6; the
+ * first replaces the original row, the second is appended. Otherwise an
+ * exact copy is appended. Appended and split rows get zero m and v.
+ * g->data, m and v must have room for g->n + max_new rows (stride). The
+ * new count n + added is written to *d_n_out (device); selected_out
+ * (device, optional, [max_new]) receives the selected rows in order.
+ * Workspace: lgs_densify_workspace_size(g->n).
+ *
+ * lgs_opacity_decay halves every activated opacity in place:
+ * sigmoid(logit') = sigmoid(logit) / 2, rows < g->n.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_moments_accumulate(const float *grad_acc, const uint32_t *map,
+                                  const int32_t *d_num_visible, int64_t max_rows, float *S,
+                                  float *M, uint32_t *C, lgs_stream stream);
+lgs_status lgs_moments_metric(const float *S, const float *M, const uint32_t *C, int64_t n,
+                              float *metric, lgs_stream stream);
+size_t lgs_densify_workspace_size(int64_t n);
+lgs_status lgs_densify(const lgs_gaussians *g, float *m, float *v, const float *metric,
+                       int64_t max_new, float split_scale, const float *normals,
+                       int64_t *d_n_out, uint32_t *selected_out, void *workspace,
+                       size_t workspace_bytes, lgs_stream stream);
+lgs_status lgs_opacity_decay(const lgs_gaussians *g, lgs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

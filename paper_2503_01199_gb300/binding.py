@@ -30,7 +30,8 @@ ENTRY_POINTS = (
     "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow",
     "lgs_raster_fwd",
     "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
-    "lgs_adam_step", "lgs_preprocess_bwd_adam",
+    "lgs_adam_step", "lgs_preprocess_bwd_adam", "lgs_moments_accumulate", "lgs_moments_metric",
+    "lgs_densify_workspace_size", "lgs_densify", "lgs_opacity_decay",
 )
 
 
@@ -112,6 +113,11 @@ def load(build_if_missing: bool = True):
         "lgs_raster_bwd_batch": (i32, [P, i32, u32, i32, P, P]),
         "lgs_adam_step": (i32, [P, P, P, P, i64, i32, P, f32, f32, f32, i32, P, P, i64, P]),
         "lgs_preprocess_bwd_adam": (i32, [P, P, P, P, P, P, P, P, f32, f32, f32, i32, P]),
+        "lgs_moments_accumulate": (i32, [P, P, P, i64, P, P, P, P]),
+        "lgs_moments_metric": (i32, [P, P, P, i64, P, P]),
+        "lgs_densify_workspace_size": (sz, [i64]),
+        "lgs_densify": (i32, [P, P, P, P, i64, f32, P, P, P, P, sz, P]),
+        "lgs_opacity_decay": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -374,3 +380,33 @@ def lgs_preprocess_bwd_adam(g: LgsGaussians, m, v, map_, d_num_visible, cam: Lgs
                                      _ptr(d_num_visible), ctypes.byref(cam), _ptr(grad_acc), arr,
                                      beta1, beta2, eps, step, _stream(stream)),
            "lgs_preprocess_bwd_adam")
+
+
+def lgs_moments_accumulate(grad_acc, map_, d_num_visible, max_rows, S, M, C, stream=None):
+    L = load()
+    _check(L.lgs_moments_accumulate(_ptr(grad_acc), _ptr(map_), _ptr(d_num_visible), max_rows,
+                                    _ptr(S), _ptr(M), _ptr(C), _stream(stream)),
+           "lgs_moments_accumulate")
+
+
+def lgs_moments_metric(S, M, C, n, metric, stream=None):
+    L = load()
+    _check(L.lgs_moments_metric(_ptr(S), _ptr(M), _ptr(C), n, _ptr(metric), _stream(stream)),
+           "lgs_moments_metric")
+
+
+def lgs_densify_workspace_size(n: int) -> int:
+    return int(load().lgs_densify_workspace_size(n))
+
+
+def lgs_densify(g: LgsGaussians, m, v, metric, max_new, split_scale, normals, d_n_out,
+                selected_out, workspace, stream=None):
+    L = load()
+    _check(L.lgs_densify(ctypes.byref(g), _ptr(m), _ptr(v), _ptr(metric), int(max_new),
+                         float(split_scale), _ptr(normals), _ptr(d_n_out), _ptr(selected_out),
+                         _ptr(workspace), workspace.numel(), _stream(stream)), "lgs_densify")
+
+
+def lgs_opacity_decay(g: LgsGaussians, stream=None):
+    L = load()
+    _check(L.lgs_opacity_decay(ctypes.byref(g), _stream(stream)), "lgs_opacity_decay")

@@ -51,6 +51,15 @@ lgs_status loss_l1(const float *img, const float *tgt, int64_t n, float *g, floa
                    cudaStream_t s);
 lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles, int precision,
                         uint32_t *counter, int backward, cudaStream_t s);
+size_t densify_workspace_size(int64_t n);
+lgs_status densify(const lgs_gaussians *g, float *m, float *v, const float *metric, int64_t K,
+                   float split_scale, const float *normals, int64_t *d_n_out,
+                   uint32_t *selected, void *ws, size_t ws_bytes, cudaStream_t s);
+lgs_status opacity_decay(const lgs_gaussians *g, cudaStream_t s);
+lgs_status moments_accumulate(const float *gacc, const uint32_t *map, const int32_t *d_V,
+                              int64_t max_rows, float *S, float *M, uint32_t *C, cudaStream_t s);
+lgs_status moments_metric(const float *S, const float *M, const uint32_t *C, int64_t n,
+                          float *metric, cudaStream_t s);
 lgs_status opacity_variance(const float *gacc, const uint32_t *map, const int32_t *d_V,
                             int64_t max_rows, float *out, cudaStream_t s);
 
@@ -305,6 +314,42 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
     if (g->n == 0) return LGS_OK;
     return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, grad_acc, lr, beta1, beta2, eps,
                                step, as_stream(stream));
+}
+
+lgs_status lgs_moments_accumulate(const float *grad_acc, const uint32_t *map,
+                                  const int32_t *d_num_visible, int64_t max_rows, float *S,
+                                  float *M, uint32_t *C, lgs_stream stream) {
+    if (!grad_acc || !aligned16(grad_acc) || !S || !M || !C || max_rows < 0)
+        return LGS_ERR_INVALID_ARG;
+    if (max_rows == 0) return LGS_OK;
+    return moments_accumulate(grad_acc, map, d_num_visible, max_rows, S, M, C, as_stream(stream));
+}
+
+lgs_status lgs_moments_metric(const float *S, const float *M, const uint32_t *C, int64_t n,
+                              float *metric, lgs_stream stream) {
+    if (!S || !M || !C || !metric || n < 0) return LGS_ERR_INVALID_ARG;
+    if (n == 0) return LGS_OK;
+    return moments_metric(S, M, C, n, metric, as_stream(stream));
+}
+
+size_t lgs_densify_workspace_size(int64_t n) { return n < 0 ? 0 : densify_workspace_size(n); }
+
+lgs_status lgs_densify(const lgs_gaussians *g, float *m, float *v, const float *metric,
+                       int64_t max_new, float split_scale, const float *normals,
+                       int64_t *d_n_out, uint32_t *selected_out, void *workspace,
+                       size_t workspace_bytes, lgs_stream stream) {
+    if (bad_gaussians(g) || g->sh_dtype != LGS_SH_F32 || !m || !v || !metric || !d_n_out ||
+        max_new < 0 || (max_new > 0 && !normals) || g->stride < g->n + max_new || !workspace ||
+        workspace_bytes < densify_workspace_size(g->n) || g->n + max_new > 0x7fffffffLL)
+        return LGS_ERR_INVALID_ARG;
+    return densify(g, m, v, metric, max_new, split_scale, normals, d_n_out, selected_out,
+                   workspace, workspace_bytes, as_stream(stream));
+}
+
+lgs_status lgs_opacity_decay(const lgs_gaussians *g, lgs_stream stream) {
+    if (bad_gaussians(g) || g->sh_dtype != LGS_SH_F32) return LGS_ERR_INVALID_ARG;
+    if (g->n == 0) return LGS_OK;
+    return opacity_decay(g, as_stream(stream));
 }
 
 }  // extern "C"

@@ -77,23 +77,25 @@ class Trainer:
     """Device-resident scene + all step buffers for one camera size."""
 
     def __init__(self, scene: dict, width: int, height: int, cfg: StepConfig | None = None,
-                 device: str = "cuda"):
+                 device: str = "cuda", capacity: int | None = None):
         self.cfg = cfg or StepConfig()
         self.dev = torch.device(device)
         self.sh_degree = int(scene["sh_degree"])
         self.n = int(scene["mean"].shape[0])
         self.np_ = B.num_planes(self.sh_degree)
-        self.stride = round_up(max(self.n, 1), 128)
+        # rows available for densification; every per-Gaussian buffer is sized for it
+        self.capacity = max(int(capacity or self.n), self.n)
+        self.stride = round_up(max(self.capacity, 1), 128)
         self.W, self.H = int(width), int(height)
         tw, th = self.cfg.tile
         self.gx, self.gy = -(-self.W // tw), -(-self.H // th)
         self.ntiles = self.gx * self.gy
-        n, dev = self.n, self.dev
+        n, dev = self.capacity, self.dev
         # [buffer][params, m, v][plane][row]
         self.state = torch.zeros((2, 3, self.np_, self.stride), dtype=torch.float32, device=dev)
         self.cur = 0
         planes = torch.from_numpy(pack_planes(scene))
-        self.state[0, 0, :, :n].copy_(planes.to(dev))
+        self.state[0, 0, :, :self.n].copy_(planes.to(dev))
         self.codes = torch.zeros(n, dtype=torch.int64, device=dev)
         self.perm = torch.zeros(n, dtype=torch.int32, device=dev)
         self.ws_morton = torch.empty(B.lgs_morton_workspace_size(n), dtype=torch.uint8, device=dev)
@@ -120,6 +122,11 @@ class Trainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.gacc = torch.zeros((n, B.GRAD_FLOATS), dtype=torch.float32, device=dev)
         self.metric = torch.zeros(n, dtype=torch.float32, device=dev)
+        # opacity-gradient moments summed over the views of a densification interval
+        self.S_acc = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.M_acc = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.C_acc = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.track_moments = False
         self.grad_planes = None
         self.lr = lr_per_plane(self.sh_degree, self.cfg.lr)
         self.step_count = 0
@@ -170,6 +177,34 @@ class Trainer:
         B.lgs_raster_bwd(self.splats, self.vals, self.ranges, cs, tw, th, self.finalT, self.last,
                          self.dLdI, self.gacc, accumulate=accumulate)
         B.lgs_opacity_variance(self.gacc, self.rowmap, self.d_V, self.n, self.metric)
+        if self.track_moments:
+            B.lgs_moments_accumulate(self.gacc, self.rowmap, self.d_V, self.n, self.S_acc,
+                                     self.M_acc, self.C_acc)
+
+    # -- densification (Sec. 3.3) --------------------------------------------
+    def densify(self, max_new: int, split_scale: float, seed: int = 0) -> int:
+        """Clone / split the Gaussians with the largest opacity-gradient
+        variance summed over the views since the last call, then Morton
+        re-sort (Sec. 3.2.1). Returns the number of Gaussians added."""
+        max_new = min(int(max_new), self.capacity - self.n)
+        g = self.gaussians()
+        B.lgs_moments_metric(self.S_acc, self.M_acc, self.C_acc, self.n, self.metric)
+        gen = torch.Generator(device=self.dev).manual_seed(seed)
+        normals = torch.randn((max(max_new, 1), 2, 3), generator=gen, device=self.dev)
+        d_n = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        ws = torch.empty(B.lgs_densify_workspace_size(self.n), dtype=torch.uint8, device=self.dev)
+        B.lgs_densify(g, self.m, self.v, self.metric, max_new, split_scale, normals, d_n, None, ws)
+        new_n = int(d_n.item())
+        added = new_n - self.n
+        self.n = new_n
+        for t in (self.S_acc, self.M_acc, self.C_acc):
+            t.zero_()
+        self.morton_reorder()
+        return added
+
+    def opacity_decay(self):
+        """Halves every activated opacity (Sec. 3.3)."""
+        B.lgs_opacity_decay(self.gaussians())
 
     def optimize(self, cs: B.LgsCamera, fused=True):
         """a9 + a10: preprocess backward and Adam on the visible rows."""
