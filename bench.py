@@ -309,7 +309,8 @@ def run_gpu(args) -> dict | None:
     e2e_ms = e0.elapsed_time(e1)
     # ---- the same step with the mixed-precision raster (FP16 / BF16 blend)
     mixed = {}
-    for name, prec in (("fp16", B.LGS_MIXED_FP16), ("bf16", B.LGS_MIXED_BF16)):
+    for name, prec in (("fp16", B.LGS_MIXED_FP16), ("bf16", B.LGS_MIXED_BF16),
+                       ("fp32_warp_reduce_int", B.LGS_FP32 | B.LGS_WARP_REDUCE_INT)):
         for _ in range(2):
             step(precision=prec)
         mev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]

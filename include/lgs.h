@@ -269,6 +269,13 @@ lgs_status lgs_get_overflow(int64_t *needed);
 #define LGS_FP32 0
 #define LGS_MIXED_FP16 1
 #define LGS_MIXED_BF16 2
+/* OR-ed into the precision of lgs_raster_bwd / lgs_raster_bwd_batch: each
+ * warp sums its gradient terms by the integer warp reduction of Sec. 3.1
+ * (warp max of the exponents, values aligned to it as 26-bit integers, an
+ * exact integer warp sum, the float rebuilt): the per-warp sum does not
+ * depend on lane order; each term loses at most 2^-25 of the warp's largest
+ * term. The forward calls ignore it. */
+#define LGS_WARP_REDUCE_INT 16
 
 /* ------------------------------------------------------------------------
  * a5. Forward rasterisation (Eq. 1-2, Alg. 1). Per pixel, front to back
@@ -342,7 +349,8 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
  *   11 C = count of included fragments as uint32, 12..15 zero (slots 10..15
  *   are rewritten by lgs_preprocess_bwd_adam).
  * accumulate = 0 zeroes rows j < max_splats first; 1 adds to them.
- * precision must be the one the forward used.
+ * precision must be the one the forward used, optionally with
+ * LGS_WARP_REDUCE_INT.
  * ---------------------------------------------------------------------- */
 lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
                           const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,

@@ -17,6 +17,7 @@ from . import build as _build
 LGS_OK, LGS_ERR_INVALID_ARG, LGS_ERR_CAPACITY, LGS_ERR_CUDA, LGS_ERR_TIMEOUT = 0, 1, 2, 3, 4
 LGS_ERR_TOO_LARGE = 5
 LGS_FP32, LGS_MIXED_FP16, LGS_MIXED_BF16 = 0, 1, 2
+LGS_WARP_REDUCE_INT = 16
 LGS_SH_F32, LGS_SH_BF16, LGS_SH_F16 = 0, 1, 2
 NOALLOC_MAX_CLUSTERS = 65536
 SPLAT_FLOATS = 12

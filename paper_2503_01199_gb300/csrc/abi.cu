@@ -229,15 +229,18 @@ lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
                           int32_t tile_h, int32_t precision, float *image, float *final_T,
                           int32_t *last_contrib, lgs_stream stream) {
     if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !image || !final_T ||
-        !last_contrib || bad_tiles(cam, tile_w, tile_h) || precision < LGS_FP32 ||
-        precision > LGS_MIXED_BF16)
+        !last_contrib || bad_tiles(cam, tile_w, tile_h) ||
+        (precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 ||
+        (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
-    return raster_fwd(sp, vals, tile_ranges, cam, tile_w, tile_h, precision, image, final_T,
-                      last_contrib, as_stream(stream));
+    return raster_fwd(sp, vals, tile_ranges, cam, tile_w, tile_h,
+                      precision & ~LGS_WARP_REDUCE_INT, image, final_T, last_contrib,
+                      as_stream(stream));
 }
 
 lgs_status lgs_raster_fwd_batch(const lgs_view *d_views, int32_t n_views, uint32_t total_tiles,
                                 int32_t precision, uint32_t *d_counter, lgs_stream stream) {
+    precision &= ~LGS_WARP_REDUCE_INT;
     if (!d_views || n_views < 1 || n_views > 1024 || !d_counter || precision < LGS_FP32 ||
         precision > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
@@ -246,8 +249,9 @@ lgs_status lgs_raster_fwd_batch(const lgs_view *d_views, int32_t n_views, uint32
 
 lgs_status lgs_raster_bwd_batch(const lgs_view *d_views, int32_t n_views, uint32_t total_tiles,
                                 int32_t precision, uint32_t *d_counter, lgs_stream stream) {
-    if (!d_views || n_views < 1 || n_views > 1024 || !d_counter || precision < LGS_FP32 ||
-        precision > LGS_MIXED_BF16)
+    if (!d_views || n_views < 1 || n_views > 1024 || !d_counter ||
+        (precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 ||
+        (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
     return raster_batch(d_views, n_views, total_tiles, precision, d_counter, 1, as_stream(stream));
 }
@@ -265,7 +269,8 @@ lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
                           int64_t max_splats, int32_t accumulate, lgs_stream stream) {
     if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !final_T ||
         !last_contrib || !dL_dimage || !grad_acc || !aligned16(grad_acc) || max_splats < 0 ||
-        bad_tiles(cam, tile_w, tile_h) || precision < LGS_FP32 || precision > LGS_MIXED_BF16)
+        bad_tiles(cam, tile_w, tile_h) || (precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 ||
+        (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
     return raster_bwd(sp, vals, tile_ranges, cam, tile_w, tile_h, precision, final_T,
                       last_contrib, dL_dimage, grad_acc, max_splats, accumulate,

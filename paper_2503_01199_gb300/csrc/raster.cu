@@ -46,12 +46,17 @@ struct RCam {
     float bg[3];
 };
 
+// PREC = blend precision (LGS_FP32 / LGS_MIXED_FP16 / LGS_MIXED_BF16),
+// optionally | LGS_WARP_REDUCE_INT for the backward's warp sums.
+constexpr int blend_of(int prec) { return prec & 3; }
+constexpr bool int_reduce(int prec) { return (prec & LGS_WARP_REDUCE_INT) != 0; }
+
 template <int PREC>
 __device__ __forceinline__ uint32_t pack_pair(float x) {
-    if constexpr (PREC == LGS_MIXED_FP16) {
+    if constexpr (blend_of(PREC) == LGS_MIXED_FP16) {
         const __half2 h = __float2half2_rn(x);
         return *reinterpret_cast<const uint32_t *>(&h);
-    } else if constexpr (PREC == LGS_MIXED_BF16) {
+    } else if constexpr (blend_of(PREC) == LGS_MIXED_BF16) {
         const __nv_bfloat162 h = __float2bfloat162_rn(x);
         return *reinterpret_cast<const uint32_t *>(&h);
     } else {
@@ -103,7 +108,7 @@ __device__ __forceinline__ void power2(const SplatS &s, float fx, float fy, floa
 template <int PREC>
 __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, float &G0, float &G1,
                                        float &a0, float &a1, bool &cl0, bool &cl1) {
-    if constexpr (PREC == LGS_FP32) {
+    if constexpr (blend_of(PREC) == LGS_FP32) {
         G0 = __expf(p0);
         G1 = __expf(p1);
         const float q0 = s.o * G0, q1 = s.o * G1;
@@ -111,7 +116,7 @@ __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, floa
         a1 = fminf(kAlphaMax, q1);
         cl0 = q0 >= kAlphaMax;
         cl1 = q1 >= kAlphaMax;
-    } else if constexpr (PREC == LGS_MIXED_FP16) {
+    } else if constexpr (blend_of(PREC) == LGS_MIXED_FP16) {
         const __half2 G = h2exp(__floats2half2_rn(p0, p1));
         const __half2 q = __hmul2(*reinterpret_cast<const __half2 *>(&s.oh), G);
         const __half2 cap = __float2half2_rn(kAlphaMax);
@@ -253,6 +258,21 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Warp sum by the integer warp reduction of Sec. 3.1: the largest exponent
+// (warp max), every value scaled to an integer aligned to it (26 bits, so
+// that 32 of them cannot overflow 32 bits), an exact integer warp sum, and
+// the float result rebuilt. Truncation costs at most 2^-25 of the largest
+// term per lane; the sum does not depend on the order of the lanes.
+__device__ __forceinline__ float warp_sum_int(float x) {
+    const uint32_t e = (__float_as_uint(x) >> 23) & 0xffu;
+    const uint32_t emax = __reduce_max_sync(0xffffffffu, e);
+    if (emax < 26u) return 0.0f;  // every |x| < 2^-100
+    const float up = __uint_as_float((279u - emax) << 23);  // 2^(152 - emax)
+    const int q = __float2int_rz(x * up);
+    const int tot = __reduce_add_sync(0xffffffffu, q);
+    return (float)tot * __uint_as_float((emax - 25u) << 23);  // 2^(emax - 152)
+}
+
 // One tile of the backward pass, by the whole CTA.
 template <int PREC>
 __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
@@ -372,15 +392,31 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                     v[9] = S;
                     v[10] = dO;
                     v[11] = n;
-                    const float red = warp_reduce_scatter16(v, lane);
                     float *row = gacc + 16 * (int64_t)s_id[k];
                     const int vi = lane >> 1;
-                    if ((lane & 1) == 0) {
-                        if (vi < 11)
-                            atomicAdd(row + vi, red);
-                        else if (vi == 11)
-                            atomicAdd(reinterpret_cast<unsigned int *>(row + 11),
-                                      (unsigned int)(red + 0.5f));
+                    if constexpr (int_reduce(PREC)) {
+                        float mine = 0.f;
+#pragma unroll
+                        for (int i = 0; i < 10; ++i) {
+                            const float t = warp_sum_int(v[i]);
+                            if (vi == i || (i == 5 && vi == 10)) mine = t;  // M = the opacity sum
+                        }
+                        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)v[11]);
+                        if ((lane & 1) == 0) {
+                            if (vi < 11)
+                                atomicAdd(row + vi, mine);
+                            else if (vi == 11)
+                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11), c);
+                        }
+                    } else {
+                        const float red = warp_reduce_scatter16(v, lane);
+                        if ((lane & 1) == 0) {
+                            if (vi < 11)
+                                atomicAdd(row + vi, red);
+                            else if (vi == 11)
+                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11),
+                                          (unsigned int)(red + 0.5f));
+                        }
                     }
                 }
             }
@@ -543,22 +579,22 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
                       const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
                       int accumulate, cudaStream_t s) {
     if (tw != kTile || th != kTile) return LGS_ERR_INVALID_ARG;
-    if (precision < LGS_FP32 || precision > LGS_MIXED_BF16) return LGS_ERR_INVALID_ARG;
+    if ((precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 || (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
+        return LGS_ERR_INVALID_ARG;
     if (!accumulate) cudaMemsetAsync(gacc, 0, (size_t)max_splats * 16 * sizeof(float), s);
     const RCam K = make_rcam(cam, tw, th);
     const unsigned grid = (unsigned)K.ntiles;
     count_launch();
+#define LGS_RBW(P) k_raster_bwd<P><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc)
     switch (precision) {
-        case LGS_FP32:
-            k_raster_bwd<LGS_FP32><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
-            break;
-        case LGS_MIXED_FP16:
-            k_raster_bwd<LGS_MIXED_FP16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
-            break;
-        default:
-            k_raster_bwd<LGS_MIXED_BF16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc);
-            break;
+        case LGS_FP32: LGS_RBW(LGS_FP32); break;
+        case LGS_MIXED_FP16: LGS_RBW(LGS_MIXED_FP16); break;
+        case LGS_MIXED_BF16: LGS_RBW(LGS_MIXED_BF16); break;
+        case LGS_FP32 | LGS_WARP_REDUCE_INT: LGS_RBW(LGS_FP32 | LGS_WARP_REDUCE_INT); break;
+        case LGS_MIXED_FP16 | LGS_WARP_REDUCE_INT: LGS_RBW(LGS_MIXED_FP16 | LGS_WARP_REDUCE_INT); break;
+        default: LGS_RBW(LGS_MIXED_BF16 | LGS_WARP_REDUCE_INT); break;
     }
+#undef LGS_RBW
     return check_launch();
 }
 
@@ -575,10 +611,13 @@ lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles
     if (grid == 0) return LGS_OK;
     count_launch();
 #define LGS_RB(P) do { if (backward) k_raster_bwd_batch<P><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); \
-                       else k_raster_fwd_batch<P><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); } while (0)
+                       else k_raster_fwd_batch<blend_of(P)><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); } while (0)
     switch (precision) {
         case LGS_MIXED_FP16: LGS_RB(LGS_MIXED_FP16); break;
         case LGS_MIXED_BF16: LGS_RB(LGS_MIXED_BF16); break;
+        case LGS_FP32 | LGS_WARP_REDUCE_INT: LGS_RB(LGS_FP32 | LGS_WARP_REDUCE_INT); break;
+        case LGS_MIXED_FP16 | LGS_WARP_REDUCE_INT: LGS_RB(LGS_MIXED_FP16 | LGS_WARP_REDUCE_INT); break;
+        case LGS_MIXED_BF16 | LGS_WARP_REDUCE_INT: LGS_RB(LGS_MIXED_BF16 | LGS_WARP_REDUCE_INT); break;
         default: LGS_RB(LGS_FP32); break;
     }
 #undef LGS_RB

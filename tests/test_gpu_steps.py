@@ -294,3 +294,23 @@ def test_raster_dense_opaque_stack(orc, shared_margins):
     # two clamped splats leave T = (1 - 0.99)^2, exactly the 1e-4 stop
     # threshold, which rounding decides: those pixels are flagged
     _raster_case(orc, sp, cam, min_ok=0.9)
+
+
+def test_raster_backward_integer_warp_reduction(orc, shared_margins):
+    # the integer warp sums (Sec. 3.1) give the oracle's gradients within the
+    # FP32 tolerance and the float warp sums within the truncation bound
+    cam = scenegen.pinhole_camera(200, 150, 200.0, bg=(0.1, 0.2, 0.3))
+    sp = U.random_splat_dict(3000, 27, 200, 150, max_radius=30)
+    W, H = cam["width"], cam["height"]
+    w = np.random.default_rng(28).standard_normal((3, H, W)).astype(np.float32) * 1e-3
+    f = U.gpu_raster(sp, cam, dLdI=w)
+    g = U.gpu_raster(sp, cam, dLdI=w, precision=B.LGS_WARP_REDUCE_INT)
+    np.testing.assert_array_equal(f["image"], g["image"])
+    vals, ranges, P = orc.bin_splats(sp["uv"][:, 0], sp["uv"][:, 1], sp["radius"], sp["depth"], W, H,
+                                     (16, 16), conic=sp["conic"], tau=sp["tau"])
+    ob = orc.render_bwd(sp, vals, ranges, cam, w, (16, 16))
+    for q in range(9):
+        assert U.rel_l2(g["grad9"][:, q], ob["grad9"][:, q]) < 1e-3, q
+        assert U.rel_l2(g["grad9"][:, q], f["grad9"][:, q]) < 1e-5, q
+    assert U.rel_l2(g["S"], ob["S"]) < 1e-3 and U.rel_l2(g["M"], ob["M"]) < 1e-3
+    np.testing.assert_array_equal(g["C"], f["C"])
