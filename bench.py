@@ -191,6 +191,54 @@ def run_multiview(tr, steps: int, warmup: int) -> dict:
             "pairs_per_view": pairs}
 
 
+def run_ccc_ablation(steps: int = 8, warmup: int = 2) -> dict:
+    """Iteration time (a2-a10) with Cluster-Cull-Compact on / off and with
+    Morton-sorted / randomly shuffled storage (Sec. 3.2; the E3/E6 analogue),
+    on the 500K surface scene with its orbit camera and on interior scenes
+    (a camera inside a cube of side 12, about a tenth of it in view) of 500K
+    and 3M Gaussians."""
+    import torch
+    from paper_2503_01199_gb300 import binding as B
+    from paper_2503_01199_gb300 import pipeline as PL
+    from paper_2503_01199_gb300 import scenegen
+    cases = {}
+    d2 = scenegen.surface_scene(500_000, SH_DEG, 1, W_IMG, H_IMG)
+    cases["surface_500k_1297x840"] = (d2["scene"], d2["camera"], d2["target"])
+    for n, label in ((500_000, "500k"), (3_000_000, "3m")):
+        d = scenegen.interior_scene(n, SH_DEG, 5, W_IMG, H_IMG)
+        cases[f"interior_{label}_1297x840"] = (d["scene"], d["camera"], d["target"])
+    out = {}
+    for name, (sc, cam, tgt) in cases.items():
+        n = sc["mean"].shape[0]
+        perm = np.random.default_rng(9).permutation(n)
+        shuffled = {k: (np.asarray(v)[perm] if k != "sh_degree" else v) for k, v in sc.items()}
+        res = {}
+        for order, scene in (("morton", sc), ("shuffled", shuffled)):
+            for ccc in (True, False):
+                tr = PL.Trainer(scene, cam["width"], cam["height"],
+                                PL.StepConfig(tile=TILE, pair_capacity=128_000_000, ccc=ccc))
+                if order == "morton":
+                    tr.morton_reorder()
+                target = torch.from_numpy(tgt).to(tr.dev)
+                cs = B.camera_struct(cam)
+                for _ in range(warmup):
+                    tr.step(cs, target, reorder=False)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    tr.step(cs, target, reorder=False)
+                e1.record()
+                torch.cuda.synchronize()
+                V = int(tr.d_V.item()) if ccc else n
+                res[f"{order}_{'ccc' if ccc else 'no_ccc'}"] = {
+                    "ms_per_iter": round(e0.elapsed_time(e1) / steps, 4), "rows_processed": V}
+                del tr
+                torch.cuda.empty_cache()
+        out[name] = res
+    return out
+
+
 STAGES = ["a1_morton", "a2_cull", "a3_preprocess", "a4_bin_sort", "a5_raster_fwd", "a6_loss",
           "a7_raster_bwd", "a8_variance", "a9a10_bwd_adam"]
 
@@ -566,6 +614,8 @@ def main():
                     help="smaller scene for profiling captures (not a bench line)")
     ap.add_argument("--serve-seconds", type=float, default=15.0,
                     help="length of the served-render request stream (0: skip)")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the Cluster-Cull-Compact / storage-order ablation")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -580,6 +630,8 @@ def main():
             "3M Gaussians", f"{args.n_gaussians} Gaussians")
     out["serving"] = (run_serving(args.serve_seconds)
                       if args.serve_seconds > 0 and not args.n_gaussians else None)
+    out["ccc_ablation"] = (run_ccc_ablation()
+                           if not args.no_ablation and not args.n_gaussians else None)
     if out["n_gpus"] == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(make_workload())
     else:

@@ -71,6 +71,9 @@ class StepConfig:
     beta2: float = 0.999
     eps: float = 1e-15
     lr: dict = field(default_factory=dict)
+    # Cluster-Cull-Compact (Sec. 3.2.2); off: every row is processed each
+    # step (culled Gaussians get zero gradients, Adam touches every row)
+    ccc: bool = True
 
 
 class Trainer:
@@ -133,6 +136,12 @@ class Trainer:
         self.splats = B.splats_struct(self.rec, self.depth, self.radius)
 
     # -- views ------------------------------------------------------------
+    def _map(self):
+        return self.rowmap if self.cfg.ccc else None
+
+    def _dV(self):
+        return self.d_V if self.cfg.ccc else None
+
     @property
     def params(self) -> torch.Tensor:
         return self.state[self.cur, 0]
@@ -161,10 +170,11 @@ class Trainer:
         cs = camst or B.camera_struct(cam)
         tw, th = self.cfg.tile
         g = self.gaussians()
-        B.lgs_cluster_cull_compact(g, cs, self.cfg.cluster, None, self.cluster_visible,
-                                   self.rowmap, self.d_V, self.ws_ccc)
-        B.lgs_preprocess(g, self.rowmap, self.d_V, cs, tw, th, self.splats)
-        B.lgs_bin_sort(self.splats, self.d_V, self.n, cs, tw, th, self.vals, self.d_P,
+        if self.cfg.ccc:
+            B.lgs_cluster_cull_compact(g, cs, self.cfg.cluster, None, self.cluster_visible,
+                                       self.rowmap, self.d_V, self.ws_ccc)
+        B.lgs_preprocess(g, self._map(), self._dV(), cs, tw, th, self.splats)
+        B.lgs_bin_sort(self.splats, self._dV(), self.n, cs, tw, th, self.vals, self.d_P,
                        self.ranges, self.ws_bin)
         B.lgs_raster_fwd(self.splats, self.vals, self.ranges, cs, tw, th, self.image, self.finalT,
                          self.last)
@@ -176,9 +186,9 @@ class Trainer:
         B.lgs_loss_l1(self.image, target, self.dLdI, self.loss)
         B.lgs_raster_bwd(self.splats, self.vals, self.ranges, cs, tw, th, self.finalT, self.last,
                          self.dLdI, self.gacc, accumulate=accumulate)
-        B.lgs_opacity_variance(self.gacc, self.rowmap, self.d_V, self.n, self.metric)
+        B.lgs_opacity_variance(self.gacc, self._map(), self._dV(), self.n, self.metric)
         if self.track_moments:
-            B.lgs_moments_accumulate(self.gacc, self.rowmap, self.d_V, self.n, self.S_acc,
+            B.lgs_moments_accumulate(self.gacc, self._map(), self._dV(), self.n, self.S_acc,
                                      self.M_acc, self.C_acc)
 
     # -- densification (Sec. 3.3) --------------------------------------------
@@ -212,15 +222,15 @@ class Trainer:
         c = self.cfg
         g = self.gaussians()
         if fused:
-            B.lgs_preprocess_bwd_adam(g, self.m, self.v, self.rowmap, self.d_V, cs, self.gacc,
+            B.lgs_preprocess_bwd_adam(g, self.m, self.v, self._map(), self._dV(), cs, self.gacc,
                                       self.lr, c.beta1, c.beta2, c.eps, self.step_count)
         else:
             if self.grad_planes is None:
                 self.grad_planes = torch.zeros((self.np_, self.stride), dtype=torch.float32,
                                                device=self.dev)
-            B.lgs_preprocess_bwd(g, self.rowmap, self.d_V, cs, self.gacc, self.grad_planes)
+            B.lgs_preprocess_bwd(g, self._map(), self._dV(), cs, self.gacc, self.grad_planes)
             B.lgs_adam_step(self.params, self.grad_planes, self.m, self.v, self.np_, self.lr,
-                            c.beta1, c.beta2, c.eps, self.step_count, self.rowmap, self.d_V,
+                            c.beta1, c.beta2, c.eps, self.step_count, self._map(), self._dV(),
                             self.n)
 
     def step(self, cam: dict | B.LgsCamera, target: torch.Tensor, reorder: bool = True,

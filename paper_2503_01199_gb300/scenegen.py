@@ -107,6 +107,26 @@ def uniform_box_scene(n: int, sh_degree: int, seed: int, width: int, height: int
     return {"scene": scene, "camera": cam, "target": target}
 
 
+def interior_scene(n: int, sh_degree: int, seed: int, width: int, height: int,
+                   half: float = 6.0) -> dict:
+    """Means uniform in the cube [-half, half]^3 around an identity camera at
+    the origin (a view from inside a large scene: about a tenth of it lies
+    in the frustum). Log-scales N(-3.5 + ln(half), 0.5), so the ratio of
+    Gaussian size to spacing matches the unit box of uniform_box_scene;
+    rotations, opacities and SH as there; fx = fy = W."""
+    rng = _rng(seed)
+    mean = rng.uniform(-half, half, (n, 3)).astype(np.float32)
+    log_scale = rng.normal(-3.5 + np.log(half), 0.5, (n, 3)).astype(np.float32)
+    quat = _unit_quats(rng, n)
+    logit = rng.normal(0.0, 1.0, n).astype(np.float32)
+    sh = _sh(rng, n, sh_degree, 0.5, 0.1)
+    scene = {"mean": mean, "log_scale": log_scale, "quat": quat, "logit": logit,
+             "sh": sh, "sh_degree": sh_degree}
+    cam = pinhole_camera(width, height, float(width))
+    target = rng.uniform(0.0, 1.0, (3, height, width)).astype(np.float32)
+    return {"scene": scene, "camera": cam, "target": target}
+
+
 def surface_scene(n: int, sh_degree: int, seed: int, width: int, height: int,
                   n_planes: int = 32, n_spheres: int = 32, shell_fraction: float = 0.1,
                   shell_radius: float = 20.0, jitter: float = 0.01) -> dict:
