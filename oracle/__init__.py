@@ -104,6 +104,7 @@ def lib():
             "or_preprocess_bwd": (None, [i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]),
             "or_adam": (None, [i64, i32, P, P, P, P, P, f64, f64, f64, i32, P, i64]),
             "or_densify": (i64, [i64, i32, i64, P, P, P, P, i64, f64, P, P]),
+            "or_tile_reachable": (None, [i64, P, P, P, P, P, P, i32, i32, P]),
             "or_opacity_decay": (None, [i64, P]),
             "or_moments_accumulate": (None, [i64, P, P, P, P, P, P, P]),
         }
@@ -374,6 +375,17 @@ def densify(planes, m, v, metric, K: int, split_scale: float, normals) -> dict:
     n_new = lib().or_densify(n, planes.shape[0], planes.shape[1], _p(planes), _p(m), _p(v),
                              _p(metric), K, float(split_scale), _p(normals), _p(sel))
     return {"planes": planes, "m": m, "v": v, "n": int(n_new), "selected": sel[:n_new - n]}
+
+
+def tile_reachable(u, v, conic, tau, tx, ty, tile=(16, 16)) -> np.ndarray:
+    """The single-precision tile-culling decision for each (splat, tile) query."""
+    u, v, tau = _c(u, np.float32), _c(v, np.float32), _c(tau, np.float32)
+    conic = _c(conic, np.float32)
+    tx, ty = _c(tx, np.int32), _c(ty, np.int32)
+    out = np.zeros(u.size, np.uint8)
+    lib().or_tile_reachable(u.size, _p(u), _p(v), _p(conic), _p(tau), _p(tx), _p(ty), tile[0],
+                            tile[1], _p(out))
+    return out.astype(bool)
 
 
 def opacity_decay(logit) -> np.ndarray:

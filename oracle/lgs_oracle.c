@@ -355,7 +355,7 @@ static float quad_form_f32(float A, float B, float C, float dx, float dy) {
     return (t1 + t2) + t3;
 }
 
-static int tile_reachable_f32(float u, float v, float A, float B, float C, float tau, int tx,
+static int tile_box_f32(float u, float v, float A, float B, float C, float tau, int tx,
                               int ty, int tw, int th) {
     float xl = (float)(tx * tw) + 0.5f, xh = (float)(tx * tw + tw) + -0.5f;
     float yl = (float)(ty * th) + 0.5f, yh = (float)(ty * th + th) + -0.5f;
@@ -373,6 +373,38 @@ static int tile_reachable_f32(float u, float v, float A, float B, float C, float
     d = fminf(fmaxf(-((B * by) * rA), ax), bx);
     q = fminf(q, quad_form_f32(A, B, C, d, by));
     return q <= tau;
+}
+
+/* Whether the minimum of q(d) = d^T [[A, B], [B, C]] d over the tile's box of
+ * pixel centres is at most tau (App. A.1's tile culling), decided row-wise:
+ * within the tile row's slab of offsets d_y = v - y in [ay, by], the ellipse
+ * q <= tau covers one interval [L, U] of d_x = u - x, whose ends are the
+ * ellipse's extreme d_x (at d_y = -/+ B e_x / C, e_x = sqrt(tau C / det)) or,
+ * when those lie outside the slab, the roots of the ellipse's quadratic in
+ * d_x at the nearest slab edge; the tile is reachable when [u - xh, u - xl]
+ * meets [L, U]. Exact in real arithmetic (the same predicate as the box
+ * minimum); taken in single precision in this operation order because the
+ * listing is an integer decision [reading: App. A.1, tile culling]. A conic
+ * whose det rounds to <= 0 falls back to the box's edge minima. */
+static int tile_reachable_f32(float u, float v, float A, float B, float C, float tau, int tx,
+                              int ty, int tw, int th) {
+    float det = A * C - B * B;
+    if (!(det > 0.0f)) return tile_box_f32(u, v, A, B, C, tau, tx, ty, tw, th);
+    if (!(tau >= 0.0f)) return 0;
+    float ex = sqrtf((tau * C) / det), ey = sqrtf((tau * A) / det);
+    float dyU = -((B * ex) / C);
+    float yl = (float)(ty * th) + 0.5f, yh = (float)(ty * th + th) + -0.5f;
+    float ay = v - yh, by = v - yl;
+    if (ay > ey || by < -ey) return 0;
+    float At = A * tau;
+    float d = fminf(fmaxf(dyU, ay), by);
+    float D = fmaxf(At - det * (d * d), 0.0f);
+    float U = (sqrtf(D) - B * d) / A;
+    d = fminf(fmaxf(-dyU, ay), by);
+    D = fmaxf(At - det * (d * d), 0.0f);
+    float L = -(sqrtf(D) + B * d) / A;
+    float xl = (float)(tx * tw) + 0.5f, xh = (float)(tx * tw + tw) + -0.5f;
+    return (u - xh) <= U && (u - xl) >= L;
 }
 
 static int frac_near_int(double x, double margin) {
@@ -1089,4 +1121,13 @@ void or_moments_accumulate(int64_t nvis, const uint32_t *rows, const double *S, 
         M_acc[rows[j]] += M[j];
         C_acc[rows[j]] += C[j];
     }
+}
+
+/* The tile-culling decision for a list of (splat, tile) queries (testing). */
+void or_tile_reachable(int64_t n, const float *u, const float *v, const float *conic,
+                       const float *tau, const int32_t *tx, const int32_t *ty, int tw, int th,
+                       uint8_t *out) {
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = (uint8_t)tile_reachable_f32(u[i], v[i], conic[3 * i], conic[3 * i + 1],
+                                             conic[3 * i + 2], tau[i], tx[i], ty[i], tw, th);
 }

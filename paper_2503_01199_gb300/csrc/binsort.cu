@@ -273,11 +273,23 @@ __global__ void __launch_bounds__(kThreads) k_chunk_masks(const float *__restric
                 const SplatGeom sg = splat_geom(rec, radius, svals[i], G);
                 const int tx0 = max(sg.rc.x, sx * kSX), tx1 = min(sg.rc.z, sx * kSX + kSX);
                 const int ty0 = max(sg.rc.y, sy * kSY), ty1 = min(sg.rc.w, sy * kSY + kSY);
-                for (int ty = ty0; ty < ty1; ++ty)
-                    for (int tx = tx0; tx < tx1; ++tx)
-                        if (!cull || tile_reachable(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC,
-                                                    sg.tau, tx, ty, G.tw, G.th))
-                            mask |= 1u << ((ty - sy * kSY) * kSX + (tx - sx * kSX));
+                const RowCull rcl = row_cull(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau);
+                for (int ty = ty0; ty < ty1; ++ty) {
+                    const uint32_t rowbit = (uint32_t)(ty - sy * kSY) * kSX - sx * kSX;
+                    if (!cull) {
+                        for (int tx = tx0; tx < tx1; ++tx) mask |= 1u << (rowbit + tx);
+                    } else if (rcl.degenerate) {
+                        for (int tx = tx0; tx < tx1; ++tx)
+                            if (tile_reachable(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau,
+                                               tx, ty, G.tw, G.th))
+                                mask |= 1u << (rowbit + tx);
+                    } else {
+                        float L, U;
+                        if (!row_interval(rcl, ty, G.th, L, U)) continue;
+                        for (int tx = tx0; tx < tx1; ++tx)
+                            if (tile_in_row(rcl, tx, G.tw, L, U)) mask |= 1u << (rowbit + tx);
+                    }
+                }
                 masks[i] = mask;
             }
 #pragma unroll

@@ -112,6 +112,55 @@ __device__ __forceinline__ bool tile_reachable(float u, float v, float A, float 
     return box_reachable(u, v, A, B, C, rA, rC, tau, xl, xh, yl, yh);
 }
 
+// Row form of the same test. Within a tile row (pixel-centre offsets
+// d_y = v - y in [ay, by]) the ellipse q(d) <= tau covers one interval
+// [L, U] of d_x = u - x: U is the largest d_x on the ellipse, reached at
+// d_y = -B e_x / C (e_x = sqrt(tau C / det), det = AC - B^2) or, when that
+// lies outside the slab, at the slab edge nearest to it, where the ellipse's
+// quadratic in d_x gives U = (sqrt(A tau - det d_y^2) - B d_y) / A; L
+// likewise with the signs flipped. A tile of the row is reachable when its
+// offsets [u - xh, u - xl] meet [L, U]. Exact in real arithmetic, the same
+// decision as the box minimum; evaluated with explicitly rounded single
+// precision operations, in this order, by every implementation.
+struct RowCull {
+    float u, v, A, B, C, rA, rC, tau, det, ey, dyU;
+    bool degenerate;  // det <= 0 after rounding: the box test decides
+};
+
+__device__ __forceinline__ RowCull row_cull(float u, float v, float A, float B, float C, float rA,
+                                            float rC, float tau) {
+    RowCull r;
+    r.u = u; r.v = v; r.A = A; r.B = B; r.C = C; r.rA = rA; r.rC = rC; r.tau = tau;
+    r.det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+    r.degenerate = !(r.det > 0.0f);
+    const float ex = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau, C), r.det));
+    r.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau, A), r.det));
+    r.dyU = -__fdiv_rn(__fmul_rn(B, ex), C);
+    return r;
+}
+
+// [L, U] for the slab of tile row ty; false if the slab misses the ellipse.
+__device__ __forceinline__ bool row_interval(const RowCull &r, int ty, int th, float &L, float &U) {
+    if (!(r.tau >= 0.0f)) return false;
+    const float yl = __fadd_rn((float)(ty * th), 0.5f), yh = __fadd_rn((float)(ty * th + th), -0.5f);
+    const float ay = __fsub_rn(r.v, yh), by = __fsub_rn(r.v, yl);
+    if (ay > r.ey || by < -r.ey) return false;
+    const float At = __fmul_rn(r.A, r.tau);
+    float d = fminf(fmaxf(r.dyU, ay), by);
+    float D = fmaxf(__fsub_rn(At, __fmul_rn(r.det, __fmul_rn(d, d))), 0.0f);
+    U = __fdiv_rn(__fsub_rn(__fsqrt_rn(D), __fmul_rn(r.B, d)), r.A);
+    d = fminf(fmaxf(-r.dyU, ay), by);
+    D = fmaxf(__fsub_rn(At, __fmul_rn(r.det, __fmul_rn(d, d))), 0.0f);
+    L = __fdiv_rn(-__fadd_rn(__fsqrt_rn(D), __fmul_rn(r.B, d)), r.A);
+    return true;
+}
+
+// Whether tile tx of a row with interval [L, U] is reachable.
+__device__ __forceinline__ bool tile_in_row(const RowCull &r, int tx, int tw, float L, float U) {
+    const float xl = __fadd_rn((float)(tx * tw), 0.5f), xh = __fadd_rn((float)(tx * tw + tw), -0.5f);
+    return __fsub_rn(r.u, xh) <= U && __fsub_rn(r.u, xl) >= L;
+}
+
 // ---------------------------------------------------------------------------
 // host-side building blocks implemented in sort.cu
 // ---------------------------------------------------------------------------

@@ -231,3 +231,50 @@ def test_tile_culling_leaves_the_image_unchanged(orc):
     np.testing.assert_array_equal(a["image"], b["image"])
     np.testing.assert_array_equal(a["T"], b["T"])
     assert b["P"] < a["P"]
+
+
+def _box_min_q(u, v, A, B, C, xl, xh, yl, yh):
+    """Exact minimum over the box of q(d) = A dx^2 + 2B dx dy + C dy^2,
+    d = (u - x, v - y), in double precision: 0 if the box holds the centre,
+    else the least of the four edge minima (a convex quadratic restricted to
+    a segment is minimised at its clamped stationary point)."""
+    ax, bx, ay, by = u - xh, u - xl, v - yh, v - yl
+    inside = (ax <= 0) & (bx >= 0) & (ay <= 0) & (by >= 0)
+    q = lambda dx, dy: A * dx * dx + 2 * B * dx * dy + C * dy * dy
+    best = np.full(u.shape, np.inf)
+    for dx in (ax, bx):
+        best = np.minimum(best, q(dx, np.clip(-B * dx / C, ay, by)))
+    for dy in (ay, by):
+        best = np.minimum(best, q(np.clip(-B * dy / A, ax, bx), dy))
+    return np.where(inside, 0.0, best)
+
+
+def test_tile_culling_decision_is_the_box_minimum(orc):
+    # the oracle's single-precision row-interval decision agrees with the
+    # exact box minimum of the quadratic form wherever that minimum is not
+    # within rounding of tau; checked on random anisotropic splats and tiles
+    rng = np.random.default_rng(44)
+    n = 200000
+    sp = scenegen.random_splats(n, 45, 400, 300, max_radius=60)
+    tau = (2.0 * np.log(255.0 * sp["opacity"].astype(np.float64)))
+    tau = (tau + 1e-3 * (1 + np.abs(tau))).astype(np.float32)
+    # tiles around each splat's centre, up to 3 tiles away
+    tx = (np.floor(sp["u"] / 16) + rng.integers(-3, 4, n)).astype(np.int32)
+    ty = (np.floor(sp["v"] / 16) + rng.integers(-3, 4, n)).astype(np.int32)
+    got = orc.tile_reachable(sp["u"], sp["v"], sp["conic"], tau, tx, ty)
+    u, v = sp["u"].astype(np.float64), sp["v"].astype(np.float64)
+    A, B, C = (sp["conic"][:, k].astype(np.float64) for k in range(3))
+    qmin = _box_min_q(u, v, A, B, C, tx * 16 + 0.5, tx * 16 + 15.5, ty * 16 + 0.5, ty * 16 + 15.5)
+    t = tau.astype(np.float64)
+    clear = np.abs(qmin - t) > 1e-4 * (1 + np.abs(t))
+    assert clear.mean() > 0.99
+    np.testing.assert_array_equal(got[clear], (qmin <= t)[clear])
+    assert 0.05 < got.mean() < 0.95          # both outcomes are exercised
+    # the exact minimum is a lower bound of a dense sampling of the box
+    for i in rng.choice(n, 50, replace=False):
+        xs = np.linspace(tx[i] * 16 + 0.5, tx[i] * 16 + 15.5, 61)
+        ys = np.linspace(ty[i] * 16 + 0.5, ty[i] * 16 + 15.5, 61)
+        X, Y = np.meshgrid(xs, ys)
+        dx, dy = u[i] - X, v[i] - Y
+        dense = (A[i] * dx * dx + 2 * B[i] * dx * dy + C[i] * dy * dy).min()
+        assert qmin[i] <= dense + 1e-9 * (1 + dense)
