@@ -139,10 +139,11 @@ __device__ __forceinline__ RowCull row_cull(float u, float v, float A, float B, 
     return r;
 }
 
-// [L, U] for the slab of tile row ty; false if the slab misses the ellipse.
-__device__ __forceinline__ bool row_interval(const RowCull &r, int ty, int th, float &L, float &U) {
+// [L, U] for the slab of pixel-centre rows [yl, yh]; false if the slab
+// misses the ellipse.
+__device__ __forceinline__ bool slab_interval(const RowCull &r, float yl, float yh, float &L,
+                                              float &U) {
     if (!(r.tau >= 0.0f)) return false;
-    const float yl = __fadd_rn((float)(ty * th), 0.5f), yh = __fadd_rn((float)(ty * th + th), -0.5f);
     const float ay = __fsub_rn(r.v, yh), by = __fsub_rn(r.v, yl);
     if (ay > r.ey || by < -r.ey) return false;
     const float At = __fmul_rn(r.A, r.tau);
@@ -153,6 +154,12 @@ __device__ __forceinline__ bool row_interval(const RowCull &r, int ty, int th, f
     D = fmaxf(__fsub_rn(At, __fmul_rn(r.det, __fmul_rn(d, d))), 0.0f);
     L = __fdiv_rn(-__fadd_rn(__fsqrt_rn(D), __fmul_rn(r.B, d)), r.A);
     return true;
+}
+
+// [L, U] for tile row ty (pixel-centre rows ty th + 0.5 .. ty th + th - 0.5).
+__device__ __forceinline__ bool row_interval(const RowCull &r, int ty, int th, float &L, float &U) {
+    const float yl = __fadd_rn((float)(ty * th), 0.5f), yh = __fadd_rn((float)(ty * th + th), -0.5f);
+    return slab_interval(r, yl, yh, L, U);
 }
 
 // Whether tile tx of a row with interval [L, U] is reachable.

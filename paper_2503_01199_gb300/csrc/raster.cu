@@ -5,9 +5,10 @@
 // the tile and every thread a horizontal pair of pixels. The tile's sorted
 // splats are staged through shared memory 128 at a time (one per thread).
 // While staging, each thread tests its splat against the four quadrants
-// with the same conservative test the binning uses per tile (the minimum of
-// the exponent's quadratic form over the quadrant's pixel centres against
-// tau), so each warp walks only the splats that can reach its quadrant.
+// with the test the binning uses per tile (the minimum of the exponent's
+// quadratic form over the quadrant's pixel centres against tau, in its row
+// form: one x interval per 8-row slab), so each warp walks only the splats
+// that can reach its quadrant.
 // In the backward each thread first sums a splat's per-pixel terms over its
 // two pixels, the warp reduces the 12 sums with a reduce-scatter butterfly
 // (16 shuffles; value i ends on lanes 2i, 2i + 1) and lanes 0, 2, .., 22
@@ -83,12 +84,27 @@ __device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_
     s.bl = z.x;
     s.oh = pack_pair<PREC>(y.y);
     const float rA = __frcp_rn(x.z), rC = __frcp_rn(y.x);
+    const RowCull rc = row_cull(x.x, x.y, x.z, x.w, y.x, rA, rC, z.y);
     uint32_t m = 0;
+    if (rc.degenerate) {
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const float xl = x0 + 8.0f * (w & 1), yl = y0 + 8.0f * (w >> 1);
-        if (box_reachable(x.x, x.y, x.z, x.w, y.x, rA, rC, z.y, xl, xl + 7.0f, yl, yl + 7.0f))
-            m |= 1u << w;
+        for (int w = 0; w < 4; ++w) {
+            const float xl = x0 + 8.0f * (w & 1), yl = y0 + 8.0f * (w >> 1);
+            if (box_reachable(x.x, x.y, x.z, x.w, y.x, rA, rC, z.y, xl, xl + 7.0f, yl, yl + 7.0f))
+                m |= 1u << w;
+        }
+    } else {
+#pragma unroll
+        for (int qr = 0; qr < 2; ++qr) {
+            float L, U;
+            const float yl = y0 + 8.0f * qr;
+            if (!slab_interval(rc, yl, yl + 7.0f, L, U)) continue;
+#pragma unroll
+            for (int qc = 0; qc < 2; ++qc) {
+                const float xl = x0 + 8.0f * qc;
+                if (__fsub_rn(x.x, xl + 7.0f) <= U && __fsub_rn(x.x, xl) >= L) m |= 1u << (2 * qr + qc);
+            }
+        }
     }
     return m;
 }
