@@ -146,6 +146,24 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(values, device) -> list:
+    """Elementwise maximum of every rank's values (the slowest rank's times),
+    over the initialised process group; the values themselves with none."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in values]
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_rate(world: int, steps: int, ms: float) -> float:
+    """Whole-job iterations/s: the iterations of all ranks (independent
+    replicas) over the slowest rank's time."""
+    return world * steps / (ms / 1e3)
+
+
 MV_RES = ((640, 360), (960, 540), (1297, 840), (1600, 1063)) * 2
 
 
@@ -382,15 +400,13 @@ def run_gpu(args) -> dict | None:
     clk = clocks.stop()
     loss_val = float(loss_host.item())
     if world > 1:
-        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+        ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
         dist.destroy_process_group()
     if rank != 0:
         return None
     ms_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
-    e2e_value = world * args.steps / (e2e_ms / 1e3)
+    value = job_rate(world, args.steps, ms)
+    e2e_value = job_rate(world, args.steps, e2e_ms)
     # ---- roofline of the dominant HBM-bound call: the fused preprocess
     # backward + Adam (k_bwd_adam_geom + k_bwd_adam_sh), 1468 B per visible
     # Gaussian at SH3: params, m, v read and written (6 x 59 x 4 B), the
