@@ -408,7 +408,7 @@ def run_gpu(args) -> dict | None:
     value = job_rate(world, args.steps, ms)
     e2e_value = job_rate(world, args.steps, e2e_ms)
     # ---- roofline of the dominant HBM-bound call: the fused preprocess
-    # backward + Adam (k_bwd_adam_geom + k_bwd_adam_sh), 1468 B per visible
+    # backward + Adam (k_bwd_adam_fused), 1468 B per visible
     # Gaussian at SH3: params, m, v read and written (6 x 59 x 4 B), the
     # 9 gradients + S, M, C of its grad row (48 B) and its map entry (4 B)
     peaks = measured_peaks()
@@ -422,7 +422,7 @@ def run_gpu(args) -> dict | None:
     tr_rec = traffic_record().get(dom, {})
     traffic = (round(tr_rec["bytes_per_unit"] * V) if tr_rec.get("source") == source_digest()
                and "bytes_per_unit" in tr_rec else None)
-    roofline = {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_geom<3> + k_bwd_adam_sh<3>)",
+    roofline = {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_fused<3>)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "peak_source": "measured" if hbm else "fallback",
                 "frac": round(achieved / peak, 4), "traffic": traffic,

@@ -346,8 +346,7 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
  * grad_acc (device) [max_splats][16] floats, row j:
  *   0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 do (activated opacity), 6..8 dr dg db,
  *   9 S = sum of (dL/do per pixel)^2, 10 M = sum of dL/do per pixel,
- *   11 C = count of included fragments as uint32, 12..15 zero (slots 10..15
- *   are rewritten by lgs_preprocess_bwd_adam).
+ *   11 C = count of included fragments as uint32, 12..15 zero.
  * accumulate = 0 zeroes rows j < max_splats first; 1 adds to them.
  * precision must be the one the forward used, optionally with
  * LGS_WARP_REDUCE_INT.
@@ -394,11 +393,7 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
 /* a9 + a10 without a gradient buffer: each parameter's gradient is applied
  * by Adam as soon as it is computed. m and v are planes with the stride of g;
  * g->data is updated in place. Same results as lgs_preprocess_bwd followed by
- * lgs_adam_step up to rounding. grad_acc rows are used as scratch between
- * the two kernels of this call: slots 10..12 receive the colour gradient
- * with clamped channels zeroed and slots 13..15 the view direction (zeros
- * for culled Gaussians), so the moments M and C must be consumed (by
- * lgs_opacity_variance) before this call; slots 0..9 are not modified. */
+ * lgs_adam_step up to rounding. grad_acc is read only. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
                                    const lgs_camera *cam, float *grad_acc,

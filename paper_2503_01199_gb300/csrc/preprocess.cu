@@ -529,17 +529,14 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__rest
     }
 }
 
-// Fused backward + Adam in two passes over the visible Gaussians.
+// Fused backward + Adam over the visible Gaussians, in chunks of 256.
 // Part A (one thread per Gaussian): the whole backward; Adam on the planes
 // 0..10 (centre, scales, rotation, opacity) as their gradients are known.
 // The SH planes' gradients are (colour gradient masked by the clamp) x
-// Y_k(view direction): part A leaves the masked colour gradient in slots
-// 10..12 and the view direction in slots 13..15 of the gradient row (one
-// 32-byte sector; zeros if the Gaussian is culled).
-// Part B (one thread per SH coefficient k and Gaussian): Adam on the three
-// planes of coefficient k. Threads run coefficient-major within chunks of
-// 2048 Gaussians, so a warp streams 32 consecutive rows of the same planes
-// and a chunk's gradient-row sectors stay in L2 across its coefficients.
+// Y_k(view direction); part A hands the masked colour gradient and the view
+// direction to part B through shared memory.
+// Part B (same thread, coefficient by coefficient): Adam on the three planes
+// of each SH coefficient; a warp streams 32 consecutive rows of one plane.
 struct GeomSink {
     float *__restrict__ P;
     float *__restrict__ M;
@@ -558,25 +555,7 @@ struct GeomSink {
     }
 };
 
-template <int DEG>
-__global__ void __launch_bounds__(kThreads, 6) k_bwd_adam_geom(
-    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
-    int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
-    float *__restrict__ gacc, AdamArgs a) {
-    const int64_t V = load_count(d_V, n);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = map ? map[j] : j;
-        float *g16 = gacc + 16 * j;
-        GeomSink sink{P, Mo, Vo, stride, row, &a};
-        float dir[3], grgb[3];
-        backward<DEG>(K, P, stride, row, g16, sink, dir, grgb);
-        reinterpret_cast<float2 *>(g16)[5] = make_float2(grgb[0], grgb[1]);
-        reinterpret_cast<float4 *>(g16)[3] = make_float4(grgb[2], dir[0], dir[1], dir[2]);
-    }
-}
-
-// Y_k alone (k warp-uniform in part B), same expressions as sh_basis.
+// Y_k alone (k uniform across the CTA in part B), same expressions as sh_basis.
 __device__ __forceinline__ float sh_single(int k, float x, float y, float z) {
     switch (k) {
         case 0: return Y0;
@@ -598,53 +577,60 @@ __device__ __forceinline__ float sh_single(int k, float x, float y, float z) {
     }
 }
 
-constexpr int kChunk = 2048;
-
+// A CTA runs part A for its chunk, then part B; CTAs in different phases
+// overlap part A's arithmetic with part B's memory traffic. Bounded to four
+// CTAs per SM (64 registers): occupancy matters more than the few spills.
 template <int DEG>
-__global__ void __launch_bounds__(256, 6) k_bwd_adam_sh(float *__restrict__ P, float *__restrict__ Mo,
-                                                    float *__restrict__ Vo, int64_t stride,
-                                                    int64_t n, const uint32_t *__restrict__ map,
-                                                    const int32_t *d_V,
-                                                    const float *__restrict__ gacc, AdamArgs a) {
+__global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
+    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
+    int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
+    const float *__restrict__ gacc, AdamArgs a) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
+    __shared__ float s_g[3][256], s_d[3][256];
+    __shared__ int64_t s_row[256];
+    const int tid = threadIdx.x;
     const int64_t V = load_count(d_V, n);
-    const int64_t total = V * KK;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = t / (KK * kChunk);
-        const int64_t base = c * kChunk;
-        const int64_t r = t - c * (KK * kChunk);
-        int k;
-        int64_t j;
-        if (V - base >= kChunk) {
-            k = (int)(r / kChunk);
-            j = base + (r - (int64_t)k * kChunk);
-        } else {  // the last, partial chunk
-            const int64_t len = V - base;
-            k = (int)(r / len);
-            j = base + (r - (int64_t)k * len);
-        }
-        const int64_t row = map ? map[j] : j;
-        const float2 s0 = reinterpret_cast<const float2 *>(gacc + 16 * j)[5];
-        const float4 s1 = reinterpret_cast<const float4 *>(gacc + 16 * j)[3];
-        const float grgb[3] = {s0.x, s0.y, s1.x};
-        const float yk = sh_single(k, s1.y, s1.z, s1.w);
-        const int64_t at = (11 + 3 * k) * stride + row;
-        float *pp = P + at, *pm = Mo + at, *pv = Vo + at;
-        float p[3], m[3], v[3];
+    for (int64_t c0 = (int64_t)blockIdx.x * 256; c0 < V; c0 += (int64_t)gridDim.x * 256) {
+        const int64_t j = c0 + tid;
+        if (j < V) {
+            const int64_t row = map ? map[j] : j;
+            GeomSink sink{P, Mo, Vo, stride, row, &a};
+            float dir[3], grgb[3];
+            backward<DEG>(K, P, stride, row, gacc + 16 * j, sink, dir, grgb);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            p[ch] = pp[ch * stride];
-            m[ch] = pm[ch * stride];
-            v[ch] = pv[ch * stride];
+            for (int c = 0; c < 3; ++c) {
+                s_g[c][tid] = grgb[c];
+                s_d[c][tid] = dir[c];
+            }
+            s_row[tid] = row;
         }
+        __syncthreads();
+        if (j < V) {
+            const int64_t row = s_row[tid];
+            const float gr[3] = {s_g[0][tid], s_g[1][tid], s_g[2][tid]};
+            const float dx = s_d[0][tid], dy = s_d[1][tid], dz = s_d[2][tid];
+#pragma unroll 2
+            for (int k = 0; k < KK; ++k) {
+                const float yk = sh_single(k, dx, dy, dz);
+                const int64_t at = (11 + 3 * k) * stride + row;
+                float *pp = P + at, *pm = Mo + at, *pv = Vo + at;
+                float p[3], m[3], v[3];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            adam_update(p[ch], m[ch], v[ch], grgb[ch] * yk, a.lr[11 + 3 * k + ch], a);
-            pp[ch * stride] = p[ch];
-            pm[ch * stride] = m[ch];
-            pv[ch * stride] = v[ch];
+                for (int ch = 0; ch < 3; ++ch) {
+                    p[ch] = pp[ch * stride];
+                    m[ch] = pm[ch * stride];
+                    v[ch] = pv[ch * stride];
+                }
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    adam_update(p[ch], m[ch], v[ch], gr[ch] * yk, a.lr[11 + 3 * k + ch], a);
+                    pp[ch * stride] = p[ch];
+                    pm[ch * stride] = m[ch];
+                    pv[ch * stride] = v[ch];
+                }
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -725,26 +711,13 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
                                cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
-    const unsigned ga = grid_for(g->n, kThreads, 16);
-    const int kk = (g->sh_degree + 1) * (g->sh_degree + 1);
-    const unsigned gb = grid_for(g->n * kk, 256, 16);
+    const unsigned gf = grid_for(g->n, 256, 8);
+    count_launch();
     switch (g->sh_degree) {
-    case 0:
-        count_launch(); k_bwd_adam_geom<0><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<0><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
-        break;
-    case 1:
-        count_launch(); k_bwd_adam_geom<1><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<1><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
-        break;
-    case 2:
-        count_launch(); k_bwd_adam_geom<2><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<2><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
-        break;
-    default:
-        count_launch(); k_bwd_adam_geom<3><<<ga, kThreads, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a);
-        count_launch(); k_bwd_adam_sh<3><<<gb, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, gacc, a);
-        break;
+    case 0: k_bwd_adam_fused<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
+    case 1: k_bwd_adam_fused<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
+    case 2: k_bwd_adam_fused<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
+    default: k_bwd_adam_fused<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
     }
     return check_launch();
 }
