@@ -258,6 +258,13 @@ lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int6
  * clears the flag), else LGS_OK with *needed = 0. */
 lgs_status lgs_get_overflow(int64_t *needed);
 
+/* Synchronises the device; *count receives the number of bounded device-side
+ * waits that gave up since the last query (the radix sorts' look-back over
+ * earlier tiles; a wait that gives up leaves that sort's order wrong instead
+ * of hanging), and the count is cleared. Returns LGS_ERR_TIMEOUT if it was
+ * non-zero, else LGS_OK. */
+lgs_status lgs_get_wait_timeouts(uint32_t *count);
+
 /* Arithmetic of the per-pixel blend in lgs_raster_fwd / lgs_raster_bwd.
  * LGS_FP32: everything in FP32. LGS_MIXED_FP16 / LGS_MIXED_BF16 (the
  * mixed-precision raster of Sec. 3.1, with BF16 as a second 16-bit type):

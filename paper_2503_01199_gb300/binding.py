@@ -28,7 +28,7 @@ ENTRY_POINTS = (
     "lgs_version", "lgs_last_cuda_error", "lgs_kernel_launches", "lgs_morton_workspace_size", "lgs_morton_reorder",
     "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_cluster_cull_compact_noalloc",
     "lgs_compact_gather", "lgs_preprocess",
-    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow",
+    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_get_wait_timeouts",
     "lgs_raster_fwd",
     "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
     "lgs_adam_step", "lgs_preprocess_bwd_adam", "lgs_moments_accumulate", "lgs_moments_metric",
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
         "lgs_bin_sort_workspace_size": (sz, [i64, i64, i32]),
         "lgs_bin_sort": (i32, [P, P, i64, P, i32, i32, i32, P, i64, P, P, P, sz, P]),
         "lgs_get_overflow": (i32, [P]),
+        "lgs_get_wait_timeouts": (i32, [P]),
         "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P]),
         "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
         "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P, i64, i32, P]),
@@ -284,6 +285,16 @@ def lgs_get_overflow() -> int:
     if st not in (LGS_OK, LGS_ERR_CAPACITY):
         _check(st, "lgs_get_overflow")
     return int(needed.value)
+
+
+def lgs_get_wait_timeouts() -> int:
+    """Bounded device waits that gave up since the last query (0 if none)."""
+    L = load()
+    count = ctypes.c_uint32(0)
+    st = L.lgs_get_wait_timeouts(ctypes.byref(count))
+    if st not in (LGS_OK, LGS_ERR_TIMEOUT):
+        _check(st, "lgs_get_wait_timeouts")
+    return int(count.value)
 
 
 def lgs_raster_fwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h, image,

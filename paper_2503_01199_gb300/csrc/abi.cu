@@ -224,6 +224,11 @@ lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int6
 
 lgs_status lgs_get_overflow(int64_t *needed) { return get_overflow(needed); }
 
+lgs_status lgs_get_wait_timeouts(uint32_t *count) {
+    if (!count) return LGS_ERR_INVALID_ARG;
+    return sort_wait_timeouts(count);
+}
+
 lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,
                           const uint32_t *tile_ranges, const lgs_camera *cam, int32_t tile_w,
                           int32_t tile_h, int32_t precision, float *image, float *final_T,

@@ -96,7 +96,7 @@ Layout layout(void *base, int64_t maxV, int64_t cap, int ns) {
     L.tstart = reinterpret_cast<uint32_t *>(take((size_t)ns * 32 * 4));
     L.ttotal = reinterpret_cast<uint32_t *>(take((size_t)ns * 32 * 4));
     L.d_psup = reinterpret_cast<int64_t *>(take(8));
-    L.hist = take(radix_hist_bytes());
+    L.hist = take(radix_hist_bytes(maxV > cap ? maxV : cap));
     L.scan = take(scan_scratch_bytes());
     L.bytes = (size_t)(w - static_cast<unsigned char *>(base));
     return L;

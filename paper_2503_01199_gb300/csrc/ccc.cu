@@ -214,7 +214,7 @@ lgs_status morton_reorder(const float *src, float *dst, int64_t n, int64_t strid
     keys[1] = reinterpret_cast<uint64_t *>(w); w += al256((size_t)n * 8);
     vals[0] = reinterpret_cast<uint32_t *>(w); w += al256((size_t)n * 4);
     vals[1] = reinterpret_cast<uint32_t *>(w); w += al256((size_t)n * 4);
-    void *hist = w; w += al256(radix_hist_bytes());
+    void *hist = w; w += al256(radix_hist_bytes(n));
     uint32_t *bb = reinterpret_cast<uint32_t *>(w);
     count_launch();
     k_bbox_init<<<1, 32, 0, s>>>(bb);

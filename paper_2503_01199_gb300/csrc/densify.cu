@@ -150,7 +150,7 @@ lgs_status densify(const lgs_gaussians *g, float *m, float *v, const float *metr
     for (int k = 0; k < 2; ++k) keys[k] = reinterpret_cast<uint32_t *>(take((size_t)n * 4));
     for (int k = 0; k < 2; ++k) vals[k] = reinterpret_cast<uint32_t *>(take((size_t)n * 4));
     uint32_t *d_cand = reinterpret_cast<uint32_t *>(take(4));
-    void *hist = take(radix_hist_bytes());
+    void *hist = take(radix_hist_bytes(n));
     if ((size_t)(w - static_cast<unsigned char *>(ws)) > ws_bytes) return LGS_ERR_INVALID_ARG;
     cudaMemsetAsync(d_cand, 0, 4, s);
     count_launch();

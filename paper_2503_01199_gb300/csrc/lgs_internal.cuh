@@ -180,8 +180,11 @@ size_t radix_sort_workspace(int64_t n, int key_bytes);
 // the key. The count is *d_n (device; NULL means n_max). The pairs start in
 // (keys[0], vals[0]); keys[1] / vals[1] are the alternate buffers. Returns
 // the index (0 or 1) of the buffers holding the result in *out_buf.
-// `scratch` holds the histograms (radix_hist_bytes()).
-size_t radix_hist_bytes();
+// `scratch` holds the digit histograms and the tiles' look-back status
+// (radix_hist_bytes(n_max)). Bounded look-back waits that give up are
+// counted; sort_wait_timeouts() reads and clears the count.
+size_t radix_hist_bytes(int64_t n_max);
+lgs_status sort_wait_timeouts(uint32_t *count);
 lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
                           const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                           cudaStream_t s);

@@ -2,20 +2,21 @@
 // both with the element count read on the device, so that they can sit in a
 // captured CUDA graph behind kernels that produce the count.
 //
-// Radix sort, one 8-bit digit per pass, reduce-then-scan:
-//   upsweep   - a fixed grid of G CTAs, CTA b owns a contiguous run of
-//               4096-item tiles and counts its digits;
-//   scan      - one block per digit scans that digit's row of the [256][G]
-//               counts (its start within the digit for each CTA) and
-//               records the digit's total;
-//   downsweep - each CTA scans the 256 digit totals into digit starts,
-//               walks its tiles in order, ranks the items of a
-//               tile stably with a warp multisplit (peer masks from
-//               per-bit ballots), stages them
-//               in shared memory in local digit order and writes them out
-//               at its running per-digit offsets.
-// A CTA handles its tiles in input order and ranks are stable inside a
-// tile, so every pass is stable.
+// Radix sort, one 8-bit digit per pass, "onesweep" with decoupled look-back:
+//   histogram - one read of the keys counts the digits of every pass;
+//   per pass  - CTAs take 4096-item tiles in launch order from an atomic
+//               counter, rank each tile's items stably with a warp
+//               multisplit (peer masks from per-bit ballots), publish the
+//               tile's per-digit counts, and obtain the exclusive prefix of
+//               each digit over earlier tiles by looking back at their
+//               published counts (a tile that has its own prefix publishes
+//               it, so look-backs stop early); then the tile is staged in
+//               shared memory in local digit order and written out.
+// A tile only waits on tiles handed out before it, whose CTAs are resident
+// or finished, so the look-back always progresses; it is still bounded, and
+// a wait that gives up is counted (lgs_get_wait_timeouts) instead of hanging.
+// Output positions depend on tile indices only, and ranks are stable inside
+// a tile, so every pass is stable.
 #include <cuda_runtime.h>
 
 #include "lgs_internal.cuh"
@@ -96,93 +97,81 @@ __device__ uint64_t block_exclusive_scan(uint64_t x, uint64_t *smem /* [33] */, 
     return r;
 }
 
+constexpr uint32_t kFlagAgg = 1u << 30;   // tile's own counts published
+constexpr uint32_t kFlagPre = 2u << 30;   // inclusive prefix over tiles <= t published
+constexpr uint32_t kCountMask = (1u << 30) - 1u;
+constexpr uint32_t kMaxSpin = 1u << 22;
+constexpr int kMaxPasses = 8;
+
+__device__ unsigned int g_sort_wait_timeouts;
+
+// Digit counts of every pass in one read of the keys (hist zeroed).
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const K *__restrict__ keys,
-                                                               int64_t n_max, const int64_t *d_n64,
-                                                               const int32_t *d_n32, int shift,
-                                                               uint32_t *__restrict__ counts) {
-    __shared__ uint32_t s_cnt[kSortWarps][kRadix];
-    const int G = gridDim.x, b = blockIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const K *__restrict__ keys,
+                                                            int64_t n_max, const int64_t *d_n64,
+                                                            const int32_t *d_n32, int passes,
+                                                            uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_h[kMaxPasses][kRadix];
+    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = read_count(n_max, d_n64, d_n32);
-    const int64_t tiles = (n + kTile - 1) / kTile;
-    const int64_t t0 = tiles * b / G, t1 = tiles * (b + 1) / G;
-    const int64_t lo = t0 * kTile, hi = min(t1 * kTile, n);
-    for (int64_t base = lo; base < hi; base += kSortThreads) {
-        const int64_t i = base + threadIdx.x;
-        const bool ok = i < hi;
-        const int d = ok ? digit_of(keys[i], shift) : -1;
-        const uint32_t act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const uint32_t peers = digit_peers(act, d);
-            if (lane == __ffs(peers) - 1) s_cnt[wid][d] += __popc(peers);
-        }
-        __syncwarp();
+    for (int64_t i = blockIdx.x * (int64_t)kSortThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSortThreads) {
+        const K k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][digit_of(k, 8 * p)], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-        uint32_t s = 0;
-        for (int w = 0; w < kSortWarps; ++w) s += s_cnt[w][d];
-        counts[(int64_t)d * G + b] = s;
+    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
+        const uint32_t c = (&s_h[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
     }
 }
 
-// Per digit d (one block each): exclusive scan of counts[d][0..G) in place,
-// and totals[d] = the row's sum. The digits' bases are scanned by each
-// downsweep CTA from the 256 totals.
-__global__ void __launch_bounds__(1024) k_scan_digit_rows(uint32_t *counts, int G,
-                                                         uint32_t *totals) {
-    __shared__ uint64_t s_tmp[33];
-    uint32_t *row = counts + (int64_t)blockIdx.x * G;
-    uint64_t carry = 0;
-    for (int base = 0; base < G; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const uint32_t x = i < G ? row[i] : 0u;
-        uint64_t tot;
-        const uint64_t ex = block_exclusive_scan(x, s_tmp, &tot);
-        if (i < G) row[i] = (uint32_t)(carry + ex);
-        carry += tot;
-    }
-    if (threadIdx.x == 0) totals[blockIdx.x] = (uint32_t)carry;
+// Clears the tile status words of the current count and the tile counter.
+__global__ void __launch_bounds__(256) k_onesweep_reset(uint32_t *__restrict__ status,
+                                                       uint32_t *__restrict__ counter,
+                                                       int64_t n_max, const int64_t *d_n64,
+                                                       const int32_t *d_n32) {
+    const int64_t n = read_count(n_max, d_n64, d_n32);
+    const int64_t words = (n + kTile - 1) / kTile * kRadix;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        status[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
-    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ offsets,
-    const uint32_t *__restrict__ totals, int64_t n_max, const int64_t *d_n64, const int32_t *d_n32,
-    int shift) {
+    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ hist, uint32_t *status,
+    uint32_t *counter, int64_t n_max, const int64_t *d_n64, const int32_t *d_n32, int shift) {
     __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
-    __shared__ uint32_t s_run[kRadix];
+    __shared__ uint32_t s_gstart[kRadix];
     __shared__ uint32_t s_start[kRadix];
-    __shared__ uint32_t s_tcnt[kRadix];
+    __shared__ uint32_t s_base[kRadix];
     __shared__ uint64_t s_scan[33];
-    // staging of one tile in local digit order (dynamic: above the 48 KB
-    // static limit for 64-bit keys)
+    __shared__ uint32_t s_tile;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     K *s_keys = reinterpret_cast<K *>(s_dyn);
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_dyn + sizeof(K) * kTile);
 
-    const int G = gridDim.x, b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t n = read_count(n_max, d_n64, d_n32);
     const int64_t tiles = (n + kTile - 1) / kTile;
-    const int64_t t0 = tiles * b / G, t1 = tiles * (b + 1) / G;
     {
-        // global start of each digit, then of this CTA's share of it
-        const uint64_t tot = threadIdx.x < kRadix ? totals[threadIdx.x] : 0u;
-        const uint64_t base = block_exclusive_scan(tot, s_scan, nullptr);
-        if (threadIdx.x < kRadix)
-            s_run[threadIdx.x] = (uint32_t)base + offsets[(int64_t)threadIdx.x * G + b];
+        // global start of each digit
+        const uint64_t h = threadIdx.x < kRadix ? hist[threadIdx.x] : 0u;
+        const uint64_t st = block_exclusive_scan(h, s_scan, nullptr);
+        if (threadIdx.x < kRadix) s_gstart[threadIdx.x] = (uint32_t)st;
     }
     const uint32_t lt = lanemask_lt();
-
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        const int64_t base = tile * kTile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
         for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
         __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= tiles) break;
+        const int64_t base = tile * kTile;
         K key[kItemsPerThread];
         uint32_t val[kItemsPerThread], rank[kItemsPerThread];
         int dig[kItemsPerThread];
@@ -208,7 +197,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
             __syncwarp();
         }
         __syncthreads();
-        // per digit: exclusive scan over warps, then over digits
+        // per digit: exclusive scan over warps (the tile's count in tcnt)
         uint32_t tcnt = 0;
         if (threadIdx.x < kRadix) {
             const int d = threadIdx.x;
@@ -218,11 +207,36 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
                 tcnt += c;
             }
         }
-        // block scan over the first 256 threads (all threads take part)
         const uint64_t st = block_exclusive_scan(threadIdx.x < kRadix ? tcnt : 0u, s_scan, nullptr);
         if (threadIdx.x < kRadix) {
-            s_start[threadIdx.x] = (uint32_t)st;
-            s_tcnt[threadIdx.x] = tcnt;
+            const int d = threadIdx.x;
+            s_start[d] = (uint32_t)st;
+            volatile uint32_t *mine = status + tile * kRadix + d;
+            uint32_t excl = 0;
+            if (tile == 0) {
+                *mine = kFlagPre | tcnt;
+            } else {
+                *mine = kFlagAgg | tcnt;
+                int64_t k = tile - 1;
+                uint32_t spins = 0;
+                for (;;) {
+                    const uint32_t w = *(volatile const uint32_t *)(status + k * kRadix + d);
+                    const uint32_t fl = w & ~kCountMask;
+                    if (fl == 0u) {
+                        if (++spins > kMaxSpin) {
+                            atomicAdd(&g_sort_wait_timeouts, 1u);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    excl += w & kCountMask;
+                    if (fl == kFlagPre || k == 0) break;
+                    --k;
+                }
+                *mine = kFlagPre | ((excl + tcnt) & kCountMask);
+            }
+            s_base[d] = s_gstart[d] + excl;
         }
         __syncthreads();
 #pragma unroll
@@ -238,17 +252,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
         for (int i = threadIdx.x; i < ntile; i += kSortThreads) {
             const K k = s_keys[i];
             const int d = digit_of(k, shift);
-            const uint32_t o = s_run[d] + (uint32_t)i - s_start[d];
+            const uint32_t o = s_base[d] + (uint32_t)i - s_start[d];
             keys_out[o] = k;
             vals_out[o] = s_vals[i];
         }
         __syncthreads();
-        if (threadIdx.x < kRadix) s_run[threadIdx.x] += s_tcnt[threadIdx.x];
-        __syncthreads();
     }
 }
 
-int sort_grid() { return num_sms() * 2; }
+int64_t sort_tiles(int64_t n_max) { return (n_max + kTile - 1) / kTile; }
 
 template <typename K>
 lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
@@ -258,30 +270,38 @@ lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const i
         *out_buf = 0;
         return LGS_OK;
     }
-    if (n_max > 0xffffffffLL) return LGS_ERR_INVALID_ARG;
-    const int G = sort_grid();
-    uint32_t *counts = static_cast<uint32_t *>(scratch);
-    uint32_t *totals = counts + (size_t)kRadix * G;
-    const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * kTile;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_radix_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)dyn);
-        attr_set = true;
-    }
-    int cur = 0;
+    if (n_max > (int64_t)kCountMask) return LGS_ERR_INVALID_ARG;
     const int passes = radix_passes(bits);
+    if (passes > kMaxPasses) return LGS_ERR_INVALID_ARG;
+    uint32_t *hist = static_cast<uint32_t *>(scratch);             // [kMaxPasses][256]
+    uint32_t *counter = hist + kMaxPasses * kRadix;                 // 64 words
+    uint32_t *status = counter + 64;                                // [tiles][256]
+    const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * kTile;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, kSortThreads, dyn);
+    const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int64_t tmax = sort_tiles(n_max);
+    const unsigned grid = (unsigned)(tmax < cap ? tmax : cap);
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kRadix * passes, s);
+    count_launch();
+    k_digit_hist<K><<<grid_for(n_max, kSortThreads, 4), kSortThreads, 0, s>>>(
+        keys[0], n_max, d_n64, d_n32, passes, hist);
+    int cur = 0;
     for (int p = 0; p < passes; ++p) {
-        const int shift = p * 8;
         count_launch();
-        k_radix_upsweep<K><<<G, kSortThreads, 0, s>>>(keys[cur], n_max, d_n64, d_n32, shift, counts);
+        k_onesweep_reset<<<grid_for(tmax * kRadix, 256, 4), 256, 0, s>>>(status, counter, n_max,
+                                                                      d_n64, d_n32);
         count_launch();
-        k_scan_digit_rows<<<kRadix, (G + 31) / 32 * 32 < 1024 ? (G + 31) / 32 * 32 : 1024, 0, s>>>(
-            counts, G, totals);
-        count_launch();
-        k_radix_downsweep<K><<<G, kSortThreads, dyn, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
-                                                       vals[cur ^ 1], counts, totals, n_max, d_n64,
-                                                       d_n32, shift);
+        k_onesweep<K><<<grid, kSortThreads, dyn, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
+                                                      vals[cur ^ 1], hist + p * kRadix, status,
+                                                      counter, n_max, d_n64, d_n32, p * 8);
         cur ^= 1;
     }
     *out_buf = cur;
@@ -341,11 +361,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *__r
 
 int radix_passes(int bits) { return bits <= 0 ? 1 : (bits + 7) / 8; }
 
-size_t radix_hist_bytes() { return (size_t)kRadix * (sort_grid() + 1) * sizeof(uint32_t); }
+size_t radix_hist_bytes(int64_t n_max) {
+    return sizeof(uint32_t) * ((size_t)kMaxPasses * kRadix + 64 +
+                               (size_t)sort_tiles(n_max > 0 ? n_max : 1) * kRadix);
+}
+
+lgs_status sort_wait_timeouts(uint32_t *count) {
+    unsigned int h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_sort_wait_timeouts, sizeof(h)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_sort_wait_timeouts, &zero, sizeof(zero)) != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    *count = h;
+    return h ? LGS_ERR_TIMEOUT : LGS_OK;
+}
 
 size_t radix_sort_workspace(int64_t n, int key_bytes) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return 2 * al((size_t)n * key_bytes) + 2 * al((size_t)n * 4) + al(radix_hist_bytes());
+    return 2 * al((size_t)n * key_bytes) + 2 * al((size_t)n * 4) + al(radix_hist_bytes(n));
 }
 
 lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
