@@ -471,18 +471,34 @@ SERVE_SLOTS = 4  # the HBM budget pays for scratch of about 4 concurrent 1080p r
 
 
 def run_serving(seconds: float) -> dict:
+    import gc
+
     import torch
     from paper_2503_01199_gb300 import scenegen
     from paper_2503_01199_gb300 import serving as SV
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     scenes = [SV.ResidentScene(scenegen.uniform_box_scene(n, SH_DEG, seed, 64, 64,
                                                           with_target=False)["scene"])
               for n, seed in SERVE_SCENES]
     need = SV.slot_bytes(max(n for n, _ in SERVE_SCENES), 1920, 1080, SERVE_PAIR_CAPACITY)
     budget = int(SERVE_SLOTS * need + need // 5)
+    # a short discarded stream first (process warm-up after the training runs)
+    SV.serve(scenes, scenegen.render_requests(21, 1.0, SERVE_RATE, len(scenes), list(SERVE_RES)),
+             budget, list(SERVE_RES), SERVE_PAIR_CAPACITY)
+    gc.collect()
+    torch.cuda.empty_cache()
     reqs = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES))
     served = SV.serve(scenes, reqs, budget, list(SERVE_RES), SERVE_PAIR_CAPACITY)
     st = served["stats"]
     del served
+    torch.cuda.empty_cache()
+    reqs_g = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES))
+    grouped = SV.serve(scenes, reqs_g, budget, list(SERVE_RES), SERVE_PAIR_CAPACITY,
+                       grouped=True)
+    gst = grouped["stats"]
+    del grouped
     torch.cuda.empty_cache()
     reqs2 = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES))
     plain = SV.plain_loop(scenes, reqs2, list(SERVE_RES), SERVE_PAIR_CAPACITY)["stats"]
@@ -494,6 +510,8 @@ def run_serving(seconds: float) -> dict:
                                                                "frames_per_s", "requests",
                                                                "slots", "max_inflight",
                                                                "pair_overflow")},
+            "grouped_batched_raster": {k: gst[k] for k in ("p50_ms", "p99_ms", "mean_ms",
+                                                           "frames_per_s", "max_group")},
             "plain_loop": {k: plain[k] for k in ("p50_ms", "p99_ms", "mean_ms", "frames_per_s")}}
 
 

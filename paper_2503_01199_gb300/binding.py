@@ -310,6 +310,13 @@ def view_table(views: list, tile=(16, 16), device="cuda") -> tuple[torch.Tensor,
     views: dicts with rec, vals, ranges, image, final_T, last (tensors), and
     optionally dL_dimage, grad_acc, plus the camera dict 'camera' (width,
     height, bg). Returns (uint8 CUDA tensor holding the table, total tiles)."""
+    raw, off = view_table_bytes(views, tile)
+    table = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+    return table, off
+
+
+def view_table_bytes(views: list, tile=(16, 16)) -> tuple[bytes, int]:
+    """The bytes of an lgs_view table (see view_table) and the total tiles."""
     arr = (LgsView * len(views))()
     off = 0
     for i, v in enumerate(views):
@@ -322,9 +329,7 @@ def view_table(views: list, tile=(16, 16), device="cuda") -> tuple[torch.Tensor,
         e.width, e.height, e.tile_offset = w, h, off
         e.bg[:] = [float(x) for x in np.asarray(cam["bg"]).reshape(3)]
         off += -(-w // tile[0]) * -(-h // tile[1])
-    raw = bytes(arr)
-    table = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
-    return table, off
+    return bytes(arr), off
 
 
 def lgs_raster_fwd_batch(table, n_views, total_tiles, counter, precision=LGS_FP32, stream=None):

@@ -46,6 +46,7 @@ class Scheduler:
         self.inflight = {}
         self.completed = []
         self.max_inflight = 0
+        self.max_group = 0
 
     def submit(self, req: dict, now: float):
         req["t_submit"] = now
@@ -59,13 +60,21 @@ class Scheduler:
                 del self.inflight[slot]
                 self.free.append(slot)
                 self.completed.append(req)
+        group = []
         while self.queue and self.free:
             slot = self.free.pop()
             req = self.queue.popleft()
             req["t_start"] = now
             req["slot"] = slot
-            self.ex.start(slot, req)
+            group.append((slot, req))
             self.inflight[slot] = req
+        if group:
+            if getattr(self.ex, "grouped", False):
+                self.ex.start_group(group)   # one launch renders the whole group
+            else:
+                for slot, req in group:
+                    self.ex.start(slot, req)
+            self.max_group = max(self.max_group, len(group))
         self.max_inflight = max(self.max_inflight, len(self.inflight))
 
     def idle(self) -> bool:
@@ -165,14 +174,20 @@ class _Slot:
 class GpuExecutor:
     """Runs requests {'scene': index, 'camera': scenegen camera dict} on slots.
     With use_graphs each request is one replay of a graph captured per
-    (slot, scene, resolution); without, the calls are issued one by one."""
+    (slot, scene, resolution); without, the calls are issued one by one.
+    With grouped, the requests admitted together run their front ends (pose
+    upload, cull + compaction, preprocess, binning: graphs per slot, scene
+    and resolution) on their slots' streams and are then rendered by ONE
+    persistent batched raster launch over all their tiles
+    (lgs_raster_fwd_batch); each image is copied back on its slot's stream."""
 
     def __init__(self, scenes: list, n_slots: int, resolutions, pair_capacity: int,
                  tile=(16, 16), cluster: int = 128, use_graphs: bool = True,
-                 keep_images: bool = False, device="cuda"):
+                 keep_images: bool = False, grouped: bool = False, device="cuda"):
         self.scenes = scenes
         self.tile, self.cluster = tuple(tile), int(cluster)
-        self.use_graphs, self.keep_images = use_graphs, keep_images
+        self.use_graphs, self.keep_images = use_graphs or grouped, keep_images
+        self.grouped = grouped
         self.dev = torch.device(device)
         self.max_n = max(s.n for s in scenes)
         self.max_w = max(w for w, _ in resolutions)
@@ -181,15 +196,25 @@ class GpuExecutor:
         self.slots = [_Slot(self.max_n, self.max_w, self.max_h, self.cap, self.tile, self.cluster,
                             self.dev) for _ in range(n_slots)]
         self.structs = [s.struct() for s in scenes]
-        if use_graphs:
+        if grouped:
+            self.gstream = torch.cuda.Stream(device=self.dev)
+            self.gevent = torch.cuda.Event()
+            self.counter = torch.zeros(1, dtype=torch.int32, device=self.dev)
+            self.table_dev = torch.empty(n_slots * ctypes_sizeof_view(), dtype=torch.uint8,
+                                         device=self.dev)
+            self.table_host = torch.empty(n_slots * ctypes_sizeof_view(),
+                                          dtype=torch.uint8).pin_memory()
+            self.table_copied = torch.cuda.Event()
+            self.table_copied.record(self.gstream)
+        if self.use_graphs:
             for k, slot in enumerate(self.slots):
                 for si in range(len(scenes)):
                     for (w, h) in resolutions:
-                        self._capture(slot, si, w, h)
+                        self._capture(slot, si, w, h, front_only=grouped)
         torch.cuda.synchronize()
 
     # -- the calls of one request on the slot's current stream ---------------
-    def _issue(self, slot: _Slot, si: int, cs: B.LgsCamera):
+    def _issue(self, slot: _Slot, si: int, cs: B.LgsCamera, front_only: bool = False):
         tw, th = self.tile
         g = self.structs[si]
         W, H = cs.width, cs.height
@@ -199,10 +224,11 @@ class GpuExecutor:
         ntiles = -(-W // tw) * -(-H // th)
         B.lgs_bin_sort(slot.splats, slot.d_V, self.scenes[si].n, cs, tw, th, slot.vals,
                        slot.d_P, slot.ranges[:ntiles], slot.ws_bin)
-        B.lgs_raster_fwd(slot.splats, slot.vals, slot.ranges[:ntiles], cs, tw, th,
-                         slot.image[:3 * W * H], slot.finalT[:W * H], slot.last[:W * H])
+        if not front_only:
+            B.lgs_raster_fwd(slot.splats, slot.vals, slot.ranges[:ntiles], cs, tw, th,
+                             slot.image[:3 * W * H], slot.finalT[:W * H], slot.last[:W * H])
 
-    def _capture(self, slot: _Slot, si: int, w: int, h: int):
+    def _capture(self, slot: _Slot, si: int, w: int, h: int, front_only: bool = False):
         from . import scenegen
         cam = scenegen.orbit_camera(4.0, 0.0, 0.0, w, h, center=scenegen.BOX_CENTER)
         cs = B.camera_struct(cam, d_pose=slot.d_pose)
@@ -214,9 +240,51 @@ class GpuExecutor:
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=slot.stream):
             slot.d_pose.copy_(slot.h_pose, non_blocking=True)
-            self._issue(slot, si, cs)
-            slot.h_image[:3 * w * h].copy_(slot.image[:3 * w * h], non_blocking=True)
+            self._issue(slot, si, cs, front_only=front_only)
+            if not front_only:
+                slot.h_image[:3 * w * h].copy_(slot.image[:3 * w * h], non_blocking=True)
+        # one replay now, so that no request pays for the graph's first upload
+        slot.h_pose.copy_(slot.d_pose.cpu())
+        with torch.cuda.stream(slot.stream):
+            graph.replay()
+        slot.stream.synchronize()
         slot.graphs[(si, w, h)] = (graph, cs)
+
+    def start_group(self, group: list):
+        """Front ends of every request of the group on their slots' streams,
+        one batched raster over all their tiles, images back per slot."""
+        views = []
+        for k, req in group:
+            slot = self.slots[k]
+            cam = req["camera"]
+            w, h = int(cam["width"]), int(cam["height"])
+            graph, _ = slot.graphs[(req["scene"], w, h)]
+            slot.h_pose.numpy()[:] = np.concatenate([np.asarray(cam["R"], np.float32).reshape(9),
+                                                     np.asarray(cam["t"], np.float32).reshape(3)])
+            with torch.cuda.stream(slot.stream):
+                graph.replay()
+                slot.event.record(slot.stream)
+            self.gstream.wait_event(slot.event)
+            ntiles = -(-w // self.tile[0]) * -(-h // self.tile[1])
+            views.append({"camera": cam, "rec": slot.rec, "vals": slot.vals,
+                          "ranges": slot.ranges[:ntiles], "image": slot.image[:3 * w * h],
+                          "final_T": slot.finalT[:w * h], "last": slot.last[:w * h]})
+        raw, total = B.view_table_bytes(views, self.tile)
+        self.table_copied.synchronize()   # the previous group's table has left the pinned buffer
+        with torch.cuda.stream(self.gstream):
+            self.table_host.numpy()[:len(raw)] = np.frombuffer(raw, np.uint8)
+            self.table_dev[:len(raw)].copy_(self.table_host[:len(raw)], non_blocking=True)
+            self.table_copied.record(self.gstream)
+            B.lgs_raster_fwd_batch(self.table_dev, len(views), total, self.counter)
+            self.gevent.record(self.gstream)
+        for k, req in group:
+            slot = self.slots[k]
+            cam = req["camera"]
+            w, h = int(cam["width"]), int(cam["height"])
+            slot.stream.wait_event(self.gevent)
+            with torch.cuda.stream(slot.stream):
+                slot.h_image[:3 * w * h].copy_(slot.image[:3 * w * h], non_blocking=True)
+                slot.event.record(slot.stream)
 
     # -- executor interface ----------------------------------------------------
     def start(self, k: int, req: dict):
@@ -248,9 +316,14 @@ class GpuExecutor:
         return B.lgs_get_overflow()
 
 
+def ctypes_sizeof_view() -> int:
+    import ctypes
+    return ctypes.sizeof(B.LgsView)
+
+
 def serve(scenes: list, requests: list, hbm_budget_bytes: int, resolutions,
           pair_capacity: int, use_graphs: bool = True, keep_images: bool = False,
-          max_slots: int | None = None) -> dict:
+          max_slots: int | None = None, grouped: bool = False) -> dict:
     """Builds the server for the budget, replays the request stream in real
     time and returns latency / throughput statistics."""
     need = slot_bytes(max(s.n for s in scenes), max(w for w, _ in resolutions),
@@ -259,13 +332,13 @@ def serve(scenes: list, requests: list, hbm_budget_bytes: int, resolutions,
     if max_slots:
         n_slots = min(n_slots, max_slots)
     ex = GpuExecutor(scenes, n_slots, resolutions, pair_capacity, use_graphs=use_graphs,
-                     keep_images=keep_images)
+                     keep_images=keep_images, grouped=grouped)
     sch = Scheduler(n_slots, ex)
     wall = replay(sch, requests)
     torch.cuda.synchronize()
     stats = latency_stats(sch.completed, wall)
     stats.update({"slots": n_slots, "slot_bytes": need, "max_inflight": sch.max_inflight,
-                  "pair_overflow": ex.overflow()})
+                  "max_group": sch.max_group, "pair_overflow": ex.overflow()})
     return {"stats": stats, "completed": sch.completed, "executor": ex}
 
 

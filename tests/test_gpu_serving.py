@@ -36,14 +36,18 @@ def scenes():
             for n, seed in ((20000, 10), (50000, 11))]
 
 
-def test_each_request_same_alone_and_in_the_mix(scenes):
+@pytest.mark.parametrize("grouped", [False, True])
+def test_each_request_same_alone_and_in_the_mix(scenes, grouped):
+    # grouped: requests admitted together share one batched raster launch
     reqs = scenegen.render_requests(7, 0.04, 1500.0, len(scenes), RES)
     assert len(reqs) > 30
     mix = SV.serve(scenes, reqs, hbm_budget_bytes=1 << 40, resolutions=RES,
-                   pair_capacity=4_000_000, keep_images=True, max_slots=4)
+                   pair_capacity=4_000_000, keep_images=True, max_slots=4, grouped=grouped)
     st = mix["stats"]
     assert st["requests"] == len(reqs) and st["pair_overflow"] == 0
     assert st["max_inflight"] > 1          # requests did overlap
+    if grouped:
+        assert st["max_group"] > 1         # and some shared a launch
     alone = SV.GpuExecutor(scenes, 1, RES, 4_000_000, use_graphs=False, keep_images=True)
     for r in mix["completed"]:
         q = {"scene": r["scene"], "camera": r["camera"]}
