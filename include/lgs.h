@@ -243,7 +243,11 @@ lgs_status lgs_preprocess(const lgs_gaussians *g, const uint32_t *map,
  * vals (row-major tile id t = ty * grid_w + tx); *d_num_pairs = P.
  * If P > pair_capacity only the first pair_capacity pairs are written, the
  * device overflow flag is raised and lgs_get_overflow() reports the size
- * needed; the image is then incomplete.
+ * needed; the image is then incomplete. The workspace sized by
+ * pair_capacity also holds one item per (super-tile of 8 x 4 tiles, splat
+ * listed in one of its tiles), never more than P; a count above
+ * pair_capacity overflows the same way. The tile grid may have at most
+ * 65536 tiles and 65535 columns (LGS_ERR_INVALID_ARG otherwise).
  * ---------------------------------------------------------------------- */
 /* n_tiles: the tile count of the largest image the workspace will serve. */
 size_t lgs_bin_sort_workspace_size(int64_t max_splats, int64_t pair_capacity, int32_t n_tiles);
@@ -260,8 +264,9 @@ lgs_status lgs_get_overflow(int64_t *needed);
 
 /* Synchronises the device; *count receives the number of bounded device-side
  * waits that gave up since the last query (the radix sorts' look-back over
- * earlier tiles; a wait that gives up leaves that sort's order wrong instead
- * of hanging), and the count is cleared. Returns LGS_ERR_TIMEOUT if it was
+ * earlier tiles and the binning's look-back over earlier groups of splats; a
+ * wait that gives up leaves that result wrong instead of hanging), and the
+ * count is cleared. Returns LGS_ERR_TIMEOUT if it was
  * non-zero, else LGS_OK. */
 lgs_status lgs_get_wait_timeouts(uint32_t *count);
 

@@ -226,7 +226,12 @@ lgs_status lgs_get_overflow(int64_t *needed) { return get_overflow(needed); }
 
 lgs_status lgs_get_wait_timeouts(uint32_t *count) {
     if (!count) return LGS_ERR_INVALID_ARG;
-    return sort_wait_timeouts(count);
+    uint32_t a = 0, b = 0;
+    const lgs_status sa = sort_wait_timeouts(&a);
+    const lgs_status sb = bin_wait_timeouts(&b);
+    *count = a + b;
+    if (sa == LGS_ERR_CUDA || sb == LGS_ERR_CUDA) return LGS_ERR_CUDA;
+    return *count ? LGS_ERR_TIMEOUT : LGS_OK;
 }
 
 lgs_status lgs_raster_fwd(const lgs_splats *sp, const uint32_t *vals,

@@ -8,14 +8,16 @@
 //
 // Two levels instead of one sort over all (tile, splat) pairs:
 //   1. the splats are sorted by depth (32-bit keys);
-//   2. each splat is binned into the super-tiles (8 x 4 tiles) its rectangle
-//      meets, in depth order, and the (super-tile, splat) items are sorted
-//      stably by super-tile (one 8-bit pass for up to 256 super-tiles);
-//   3. each super-tile's items, in chunks of 1024, get a 32-bit mask of the
-//      tiles they are listed in (rectangle and culling test per tile); one
-//      ballot per tile per warp gives every item its rank among the earlier
-//      items of the chunk listed in the same tile, so each tile's list is
-//      written in depth order without sorting the pairs themselves.
+//   2. each splat, in depth order, finds the tiles it is listed in (its
+//      rectangle and, per tile row, the interval kept by the culling test)
+//      and emits one item per super-tile (8 x 4 tiles) holding any of them,
+//      with a 32-bit mask of those tiles; the items are sorted stably by
+//      super-tile (one 8-bit pass for up to 256 super-tiles);
+//   3. each super-tile's items are taken in chunks of 1024; a warp-wide bit
+//      transpose of 32 items' masks gives every tile's ballot, hence the
+//      counts per chunk and tile and every item's rank among the earlier
+//      items listed in the same tile, so each tile's list is written in
+//      depth order without sorting the pairs themselves.
 // Tiles' lists are laid out super-tile by super-tile, tile by tile.
 #include <cuda_runtime.h>
 
@@ -60,18 +62,18 @@ int64_t max_chunks(int ns, int64_t cap) { return ns + ceil_div(cap, kChunk); }
 
 struct Layout {
     uint32_t *dkeys[2], *dvals[2];
-    uint32_t *scnt;
-    uint64_t *soff;
+    uint64_t *gstatus;    // look-back status per group of 32 splats
+    uint32_t *gcounter;   // next group id (follows gstatus)
+    size_t gstatus_bytes; // both, cleared before stage 2
     uint16_t *skeys[2];
-    uint32_t *svals[2];
-    uint32_t *masks;
+    uint64_t *svals[2];   // tile mask << 32 | splat
     uint32_t *seg;        // [ns][2]
     uint32_t *cbase;      // [ns + 1]
     uint32_t *ccount;     // [max_chunks][32]
     uint32_t *tstart;     // [ns * 32]
     uint32_t *ttotal;     // [ns * 32]
     int64_t *d_psup;
-    void *hist, *scan;
+    void *hist;
     size_t bytes;
 };
 
@@ -85,11 +87,12 @@ Layout layout(void *base, int64_t maxV, int64_t cap, int ns) {
     };
     for (int k = 0; k < 2; ++k) L.dkeys[k] = reinterpret_cast<uint32_t *>(take((size_t)maxV * 4));
     for (int k = 0; k < 2; ++k) L.dvals[k] = reinterpret_cast<uint32_t *>(take((size_t)maxV * 4));
-    L.scnt = reinterpret_cast<uint32_t *>(take((size_t)maxV * 4));
-    L.soff = reinterpret_cast<uint64_t *>(take((size_t)maxV * 8));
+    L.gstatus_bytes = (size_t)ceil_div(maxV > 0 ? maxV : 1, 32) * 8 + 8;
+    L.gstatus = reinterpret_cast<uint64_t *>(take(L.gstatus_bytes));
+    L.gcounter = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(L.gstatus) +
+                                              L.gstatus_bytes - 8);
     for (int k = 0; k < 2; ++k) L.skeys[k] = reinterpret_cast<uint16_t *>(take((size_t)cap * 2));
-    for (int k = 0; k < 2; ++k) L.svals[k] = reinterpret_cast<uint32_t *>(take((size_t)cap * 4));
-    L.masks = reinterpret_cast<uint32_t *>(take((size_t)cap * 4));
+    for (int k = 0; k < 2; ++k) L.svals[k] = reinterpret_cast<uint64_t *>(take((size_t)cap * 8));
     L.seg = reinterpret_cast<uint32_t *>(take((size_t)ns * 8));
     L.cbase = reinterpret_cast<uint32_t *>(take((size_t)(ns + 1) * 4));
     L.ccount = reinterpret_cast<uint32_t *>(take((size_t)max_chunks(ns, cap) * 32 * 4));
@@ -97,7 +100,6 @@ Layout layout(void *base, int64_t maxV, int64_t cap, int ns) {
     L.ttotal = reinterpret_cast<uint32_t *>(take((size_t)ns * 32 * 4));
     L.d_psup = reinterpret_cast<int64_t *>(take(8));
     L.hist = take(radix_hist_bytes(maxV > cap ? maxV : cap));
-    L.scan = take(scan_scratch_bytes());
     L.bytes = (size_t)(w - static_cast<unsigned char *>(base));
     return L;
 }
@@ -143,54 +145,324 @@ __device__ __forceinline__ SplatGeom splat_geom(const float *__restrict__ rec,
     return s;
 }
 
-// Stage 2: the super-tiles of each splat (depth order r), one thread per
-// splat. A super-tile is kept when the box of pixel centres of the
-// rectangle's tiles inside it passes the culling test with tau widened once
-// more by 1e-3 (1 + |tau|), so that it never drops a super-tile holding a
-// tile the per-tile test keeps.
-template <bool kEmit>
-__global__ void __launch_bounds__(kThreads) k_super_walk(const float *__restrict__ rec,
-                                                        const int32_t *__restrict__ radius,
-                                                        const uint32_t *__restrict__ order,
-                                                        int64_t maxV, const int32_t *d_V, Geo G,
-                                                        int cull, uint32_t *__restrict__ cnt,
-                                                        const uint64_t *__restrict__ off,
-                                                        int64_t cap, uint16_t *__restrict__ skeys,
-                                                        uint32_t *__restrict__ svals) {
-    const int64_t V = load_count(d_V, maxV);
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < V;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t g = order[r];
-        const SplatGeom sg = splat_geom(rec, radius, g, G);
-        uint64_t o = kEmit ? off[r] : 0ull;
-        uint32_t n = 0;
-        if (sg.rc.z > sg.rc.x) {
-            const int sx0 = sg.rc.x / kSX, sx1 = (sg.rc.z - 1) / kSX + 1;
-            const int sy0 = sg.rc.y / kSY, sy1 = (sg.rc.w - 1) / kSY + 1;
-            const float tw_ = __fmaf_rn(1e-3f, 1.0f + fabsf(sg.tau), sg.tau);
-            for (int sy = sy0; sy < sy1; ++sy)
-                for (int sx = sx0; sx < sx1; ++sx) {
-                    bool keep = true;
-                    if (cull) {
-                        const int tx0 = max(sg.rc.x, sx * kSX), tx1 = min(sg.rc.z, sx * kSX + kSX);
-                        const int ty0 = max(sg.rc.y, sy * kSY), ty1 = min(sg.rc.w, sy * kSY + kSY);
-                        keep = box_reachable(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, tw_,
-                                             (float)(tx0 * G.tw) + 0.5f, (float)(tx1 * G.tw) - 0.5f,
-                                             (float)(ty0 * G.th) + 0.5f, (float)(ty1 * G.th) - 0.5f);
-                    }
-                    if (!keep) continue;
-                    if (kEmit) {
-                        if (o < (uint64_t)cap) {
-                            skeys[o] = (uint16_t)(sy * G.sgx + sx);
-                            svals[o] = g;
-                        }
-                        ++o;
-                    } else {
-                        ++n;
-                    }
-                }
+// Tiles [a, b] of a tile row (a > b: none) that the row form of the culling
+// test keeps, within the rectangle's columns [x0, x1): the test
+// u - xh(tx) <= U only gets truer as tx grows and u - xl(tx) >= L only
+// falser (correctly rounded differences are monotone), so the kept tiles
+// form one interval, found from an estimate (rtw = 1 / tw) and a few exact
+// tests -- the same tests, operation for operation, as tile_in_row.
+__device__ __forceinline__ bool right_ok(float u, int tx, int tw, float U) {
+    const float xh = __fadd_rn((float)(tx * tw + tw), -0.5f);
+    return __fsub_rn(u, xh) <= U;
+}
+__device__ __forceinline__ bool left_ok(float u, int tx, int tw, float L) {
+    const float xl = __fadd_rn((float)(tx * tw), 0.5f);
+    return __fsub_rn(u, xl) >= L;
+}
+__device__ __forceinline__ void row_span(float u, int x0, int x1, int tw, float rtw, float L,
+                                         float U, int &a, int &b) {
+    int t1 = (int)fminf(fmaxf(ceilf((u - U + 0.5f) * rtw - 1.0f), (float)x0), (float)x1);
+    while (t1 > x0 && right_ok(u, t1 - 1, tw, U)) --t1;
+    while (t1 < x1 && !right_ok(u, t1, tw, U)) ++t1;
+    int t2 = (int)fminf(fmaxf(floorf((u - L - 0.5f) * rtw), (float)(x0 - 1)), (float)(x1 - 1));
+    while (t2 < x1 - 1 && left_ok(u, t2 + 1, tw, L)) ++t2;
+    while (t2 >= x0 && !left_ok(u, t2, tw, L)) --t2;
+    a = t1;
+    b = t2;
+}
+
+constexpr uint32_t kEmptySpan = 1u;  // packed span (a, b) = (1, 0)
+constexpr int kSpanCap = 512;        // row spans per warp held in shared memory
+
+// Packed kept span (a | b << 16) of tile row ty of a splat with rectangle
+// columns [x0, x1): with the row test, the tiles whose offsets meet the
+// row's interval; without it, the whole rectangle row.
+__device__ __forceinline__ uint32_t row_span_of(const RowCull &q, int x0, int x1, int ty,
+                                                bool row_test, const Geo &G, float rtw) {
+    int a = x0, b = x1 - 1;
+    if (row_test) {
+        a = 1;
+        b = 0;
+        float L, U;
+        if (row_interval(q, ty, G.th, L, U)) row_span(q.u, x0, x1, G.tw, rtw, L, U, a, b);
+    }
+    return a <= b ? ((uint32_t)a | ((uint32_t)b << 16)) : kEmptySpan;
+}
+
+// Calls f(super-tile id, 32-bit tile mask) for every super-tile in which the
+// splat is listed in at least one tile, in row-major super-tile order, from
+// the kept span of every tile row of its rectangle (span_of(k) for row
+// rc.y + k). With per_tile (degenerate conic under culling) the spans are
+// the rectangle's and each tile takes the box test.
+template <class S, class F>
+__device__ __forceinline__ void for_each_super(const int4 rc, S &&span_of, bool per_tile,
+                                               const SplatGeom &sg, const Geo &G, F &&f) {
+    if (rc.z <= rc.x || rc.w <= rc.y) return;
+    for (int sy = rc.y / kSY; sy <= (rc.w - 1) / kSY; ++sy) {
+        int a[kSY], b[kSY];
+        int amin = rc.z, bmax = rc.x - 1;
+#pragma unroll
+        for (int k = 0; k < kSY; ++k) {
+            const int ty = sy * kSY + k;
+            const uint32_t w = (ty >= rc.y && ty < rc.w) ? span_of(ty - rc.y) : kEmptySpan;
+            a[k] = (int)(w & 0xffffu);
+            b[k] = (int)(w >> 16);
+            if (a[k] <= b[k]) {
+                amin = min(amin, a[k]);
+                bmax = max(bmax, b[k]);
+            }
         }
-        if (!kEmit) cnt[r] = n;
+        if (bmax < amin) continue;
+        for (int sx = amin / kSX; sx <= bmax / kSX; ++sx) {
+            uint32_t mask = 0;
+#pragma unroll
+            for (int k = 0; k < kSY; ++k) {
+                const int lo = max(a[k], sx * kSX), hi = min(b[k], sx * kSX + kSX - 1);
+                if (lo <= hi) mask |= ((2u << (hi - lo)) - 1u) << (lo - sx * kSX + k * kSX);
+            }
+            if (per_tile) {
+                uint32_t kept = 0;
+                for (uint32_t m = mask; m; m &= m - 1) {
+                    const int bit = __ffs(m) - 1;
+                    if (tile_reachable(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau,
+                                       sx * kSX + bit % kSX, sy * kSY + bit / kSX, G.tw, G.th))
+                        kept |= 1u << bit;
+                }
+                mask = kept;
+            }
+            if (mask) f(sy * G.sgx + sx, mask);
+        }
+    }
+}
+
+// Number of super-tiles holding at least one of the splat's tiles: per
+// super-tile row, the super-columns covered by the union of its (up to 4)
+// tile rows' spans. Exact unless the box test refines tiles (per_tile).
+template <class S>
+__device__ __forceinline__ uint32_t super_count(const int4 rc, S &&span_of) {
+    if (rc.z <= rc.x || rc.w <= rc.y) return 0u;
+    uint32_t n = 0;
+    for (int sy = rc.y / kSY; sy <= (rc.w - 1) / kSY; ++sy) {
+        int a[kSY], b[kSY];
+        int amin = rc.z, bmax = rc.x - 1;
+#pragma unroll
+        for (int k = 0; k < kSY; ++k) {
+            const int ty = sy * kSY + k;
+            const uint32_t w = (ty >= rc.y && ty < rc.w) ? span_of(ty - rc.y) : kEmptySpan;
+            a[k] = (int)(w & 0xffffu);
+            b[k] = (int)(w >> 16);
+            if (a[k] <= b[k]) {
+                amin = min(amin, a[k]);
+                bmax = max(bmax, b[k]);
+            }
+        }
+        if (bmax < amin) continue;
+        const int base = amin / kSX, last = bmax / kSX;
+        if (last - base < 32) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < kSY; ++k)
+                if (a[k] <= b[k]) {
+                    const int p = a[k] / kSX - base, q = b[k] / kSX - base;
+                    m |= ((2u << (q - p)) - 1u) << p;
+                }
+            n += __popc(m);
+        } else {
+            for (int sx = base; sx <= last; ++sx) {
+                bool hit = false;
+#pragma unroll
+                for (int k = 0; k < kSY; ++k)
+                    hit |= a[k] <= b[k] && a[k] / kSX <= sx && sx <= b[k] / kSX;
+                n += hit ? 1u : 0u;
+            }
+        }
+    }
+    return n;
+}
+
+// Look-back status of a group of 32 splats: flag in the top two bits, the
+// group's item count (AGG) or the inclusive item count of groups <= it (PRE).
+constexpr uint64_t kGrpAgg = 1ull << 62, kGrpPre = 2ull << 62, kGrpVal = (1ull << 62) - 1ull;
+constexpr uint32_t kGrpMaxSpin = 1u << 22;
+constexpr int kItemCap = 384;  // items per warp staged in shared memory
+
+__device__ unsigned int g_bin_wait_timeouts;
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+#pragma unroll
+    for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+}
+
+// Lane owning position p of a warp's concatenated per-lane runs: the
+// number of lanes whose inclusive end `incl` is <= p (32 if p is past the
+// last run).
+__device__ __forceinline__ int run_owner(uint32_t incl, uint32_t p) {
+    int j = 0;
+#pragma unroll
+    for (int st = 16; st; st >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, j + st - 1) <= p) j += st;
+    return j;
+}
+
+// Stage 2: the (super-tile, splat) items in depth order, written as
+// (super-tile id, mask << 32 | splat). Each warp takes the next group of 32
+// consecutive splats (group ids from an atomic counter, so a group only
+// waits on groups already being processed):
+//   - the tile rows of the group's rectangles are spread evenly over the
+//     lanes (a row's owner found by a binary search over the warp's
+//     inclusive row counts, its test parameters read from shared memory)
+//     and each row's kept span goes to shared memory; a group with more
+//     rows than fit computes each splat's rows in its own lane instead;
+//   - each lane counts its items from the spans, the group's item offset
+//     comes from a decoupled look-back over earlier groups (32 predecessors
+//     per step, bounded wait), the items are assembled in shared memory in
+//     output order and copied out with coalesced stores (written directly
+//     when they do not fit).
+__global__ void __launch_bounds__(kThreads) k_super_items(
+    const float *__restrict__ rec, const int32_t *__restrict__ radius,
+    const uint32_t *__restrict__ order, int64_t maxV, const int32_t *d_V, Geo G, int cull,
+    uint32_t *counter, uint64_t *status, int64_t cap, uint16_t *__restrict__ skeys,
+    uint64_t *__restrict__ svals, int64_t *d_psup) {
+    __shared__ uint32_t s_span[kWarps][kSpanCap];
+    __shared__ uint32_t s_imask[kWarps][kItemCap];
+    __shared__ uint16_t s_isid[kWarps][kItemCap];
+    __shared__ float4 s_par[kWarps][32][3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t V = load_count(d_V, maxV);
+    const int64_t groups = (V + 31) / 32;
+    const float rtw = div_by_size(1.0f, G.tw);
+    if (groups == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_psup = 0;
+    for (;;) {
+        uint32_t gid = 0;
+        if (lane == 0) gid = atomicAdd(counter, 1u);
+        gid = __shfl_sync(0xffffffffu, gid, 0);
+        if ((int64_t)gid >= groups) break;
+        const int64_t r = (int64_t)gid * 32 + lane;
+        const bool ok = r < V;
+        const uint32_t g = ok ? order[r] : 0u;
+        SplatGeom sg{};
+        if (ok) sg = splat_geom(rec, radius, g, G);
+        const int4 rc = sg.rc;
+        const RowCull rcl = row_cull(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau);
+        const bool per_tile = cull && rcl.degenerate;
+        const bool row_test = cull && !rcl.degenerate;
+        const uint32_t n = (uint32_t)(rc.w - rc.y);
+        uint32_t incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t first = incl - n;
+        const bool staged = T <= (uint32_t)kSpanCap;
+        if (staged) {
+            s_par[wid][lane][0] = make_float4(rcl.u, rcl.v, rcl.A, rcl.B);
+            s_par[wid][lane][1] = make_float4(rcl.tau, rcl.det, rcl.ey, rcl.dyU);
+            s_par[wid][lane][2] = make_float4(__int_as_float(rc.x), __int_as_float(rc.z),
+                                              __int_as_float(rc.y),
+                                              __int_as_float((int)(first << 1) | (row_test ? 1 : 0)));
+            __syncwarp();
+            for (uint32_t c = 0; c < T; c += 32) {
+                const uint32_t p = c + lane;
+                const int j = run_owner(incl, p);
+                if (p < T) {
+                    const float4 P0 = s_par[wid][j][0], P1 = s_par[wid][j][1], P2 = s_par[wid][j][2];
+                    RowCull q;
+                    q.u = P0.x; q.v = P0.y; q.A = P0.z; q.B = P0.w;
+                    q.tau = P1.x; q.det = P1.y; q.ey = P1.z; q.dyU = P1.w;
+                    q.C = q.rA = q.rC = 0.0f;
+                    q.degenerate = false;
+                    const int fl = __float_as_int(P2.w);
+                    const int ty = __float_as_int(P2.z) + (int)(p - ((uint32_t)fl >> 1));
+                    s_span[wid][p] = row_span_of(q, __float_as_int(P2.x), __float_as_int(P2.y), ty,
+                                                 (fl & 1) != 0, G, rtw);
+                }
+            }
+            __syncwarp();
+        }
+        auto span_of = [&](int k) -> uint32_t {
+            return staged ? s_span[wid][first + k]
+                          : row_span_of(rcl, rc.x, rc.z, rc.y + k, row_test, G, rtw);
+        };
+        uint32_t items;
+        if (per_tile) {
+            items = 0;
+            for_each_super(rc, span_of, true, sg, G, [&](int, uint32_t) { ++items; });
+        } else {
+            items = super_count(rc, span_of);
+        }
+        uint32_t iincl = items;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, iincl, d);
+            if (lane >= d) iincl += y;
+        }
+        const uint32_t agg = __shfl_sync(0xffffffffu, iincl, 31);
+        volatile uint64_t *vs = status;
+        if (lane == 0) vs[gid] = (gid == 0 ? kGrpPre : kGrpAgg) | agg;
+        // assemble the group's items in output order while predecessors finish
+        const bool istaged = agg <= (uint32_t)kItemCap;
+        if (istaged) {
+            uint32_t e = iincl - items;
+            for_each_super(rc, span_of, per_tile, sg, G, [&](int sid, uint32_t mask) {
+                s_imask[wid][e] = mask;
+                s_isid[wid][e] = (uint16_t)sid;
+                ++e;
+            });
+            __syncwarp();
+        }
+        uint64_t excl = 0;
+        if (gid > 0) {
+            int64_t k = (int64_t)gid - 1;
+            uint32_t spins = 0;
+            for (;;) {
+                const int64_t idx = k - lane;
+                uint64_t w = kGrpPre;  // before group 0: a prefix of 0
+                if (idx >= 0) w = vs[idx];
+                const uint32_t fl = (uint32_t)(w >> 62);
+                const uint32_t pre = __ballot_sync(0xffffffffu, fl == 2u);
+                const uint32_t wait = __ballot_sync(0xffffffffu, fl == 0u);
+                const int stop = pre ? __ffs(pre) - 1 : 31;
+                const uint32_t need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
+                if (wait & need) {
+                    if (++spins > kGrpMaxSpin) {
+                        if (lane == 0) atomicAdd(&g_bin_wait_timeouts, 1u);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += warp_sum_u64(lane <= stop ? (w & kGrpVal) : 0ull);
+                if (pre) break;
+                k -= 32;
+            }
+            if (lane == 0) vs[gid] = kGrpPre | ((excl + agg) & kGrpVal);
+        }
+        if ((int64_t)gid == groups - 1 && lane == 31) *d_psup = (int64_t)(excl + agg);
+        if (istaged) {
+            for (uint32_t c = 0; c < agg; c += 32) {
+                const uint32_t e = c + lane;
+                const int j = run_owner(iincl, e);
+                const uint32_t gj = __shfl_sync(0xffffffffu, g, j < 32 ? j : 31);
+                const uint64_t o = excl + e;
+                if (e < agg && o < (uint64_t)cap) {
+                    skeys[o] = s_isid[wid][e];
+                    svals[o] = ((uint64_t)s_imask[wid][e] << 32) | gj;
+                }
+            }
+        } else {
+            uint64_t o = excl + iincl - items;
+            for_each_super(rc, span_of, per_tile, sg, G, [&](int sid, uint32_t mask) {
+                if (o < (uint64_t)cap) {
+                    skeys[o] = (uint16_t)sid;
+                    svals[o] = ((uint64_t)mask << 32) | g;
+                }
+                ++o;
+            });
+        }
+        __syncwarp();
     }
 }
 
@@ -212,28 +484,40 @@ __global__ void __launch_bounds__(kThreads) k_seg_ranges(const uint16_t *__restr
 }
 
 // Chunks of every super-tile: cbase[s] = first chunk of s, cbase[ns] = total.
-__global__ void __launch_bounds__(1024) k_chunk_plan(const uint32_t *__restrict__ seg, int ns,
+// With `hist` (the item count of every super-tile, when one sort pass
+// covers all super-tile ids) the item ranges seg are derived here as well.
+__global__ void __launch_bounds__(1024) k_chunk_plan(const uint32_t *__restrict__ hist,
+                                                    uint32_t *__restrict__ seg, int ns,
                                                     uint32_t *__restrict__ cbase) {
-    __shared__ uint32_t s_sum[1024];
+    __shared__ uint64_t s_sum[1024];
     const int per = (ns + 1023) / 1024;
     const int s0 = threadIdx.x * per;
-    uint32_t tot = 0;
-    for (int s = s0; s < min(ns, s0 + per); ++s)
-        tot += (seg[2 * s + 1] - seg[2 * s] + kChunk - 1) / kChunk;
+    auto items = [&](int s) { return hist ? hist[s] : seg[2 * s + 1] - seg[2 * s]; };
+    // items in the high word, chunks in the low word: one scan for both
+    uint64_t tot = 0;
+    for (int s = s0; s < min(ns, s0 + per); ++s) {
+        const uint32_t c = items(s);
+        tot += ((uint64_t)c << 32) | ((c + kChunk - 1) / kChunk);
+    }
     s_sum[threadIdx.x] = tot;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t x = threadIdx.x >= o ? s_sum[threadIdx.x - o] : 0u;
+        const uint64_t x = threadIdx.x >= o ? s_sum[threadIdx.x - o] : 0ull;
         __syncthreads();
         s_sum[threadIdx.x] += x;
         __syncthreads();
     }
-    uint32_t run = s_sum[threadIdx.x] - tot;
+    uint64_t run = s_sum[threadIdx.x] - tot;
     for (int s = s0; s < min(ns, s0 + per); ++s) {
-        cbase[s] = run;
-        run += (seg[2 * s + 1] - seg[2 * s] + kChunk - 1) / kChunk;
+        const uint32_t c = items(s);
+        cbase[s] = (uint32_t)run;
+        if (hist) {
+            seg[2 * s] = (uint32_t)(run >> 32);
+            seg[2 * s + 1] = (uint32_t)(run >> 32) + c;
+        }
+        run += ((uint64_t)c << 32) | ((c + kChunk - 1) / kChunk);
     }
-    if (threadIdx.x == 1023) cbase[ns] = s_sum[1023];
+    if (threadIdx.x == 1023) cbase[ns] = (uint32_t)s_sum[1023];
 }
 
 // super-tile of chunk k: the last s with cbase[s] <= k
@@ -247,16 +531,27 @@ __device__ __forceinline__ int chunk_super(const uint32_t *__restrict__ cbase, i
     return lo;
 }
 
-// Stage 3a: tile mask of every item (the tiles of its rectangle inside its
-// super-tile that pass the per-tile culling test) and per-chunk counts per
-// tile. One CTA per chunk.
-__global__ void __launch_bounds__(kThreads) k_chunk_masks(const float *__restrict__ rec,
-                                                         const int32_t *__restrict__ radius,
-                                                         const uint32_t *__restrict__ svals,
-                                                         const uint32_t *__restrict__ seg,
-                                                         const uint32_t *__restrict__ cbase, Geo G,
-                                                         int cull, uint32_t *__restrict__ masks,
-                                                         uint32_t *__restrict__ ccount) {
+// 32 x 32 bit transpose across a warp: bit i of lane l's result is bit l of
+// lane i's x (lane l receives the ballot of bit l). Five butterfly stages;
+// stage j exchanges the off-diagonal j x j blocks between lanes l and l ^ j.
+__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
+    constexpr uint32_t lo[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int j = 16 >> st;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~lo[st]) | ((y >> j) & lo[st]))
+                       : ((x & lo[st]) | ((y << j) & ~lo[st]));
+    }
+    return x;
+}
+
+// Stage 3a: per chunk of 1024 items of one super-tile, the number of items
+// listed in each of its 32 tiles. One CTA per chunk.
+__global__ void __launch_bounds__(kThreads) k_chunk_counts(const uint64_t *__restrict__ svals,
+                                                          const uint32_t *__restrict__ seg,
+                                                          const uint32_t *__restrict__ cbase, Geo G,
+                                                          uint32_t *__restrict__ ccount) {
     __shared__ uint32_t s_cnt[kWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t K = cbase[G.ns];
@@ -264,39 +559,10 @@ __global__ void __launch_bounds__(kThreads) k_chunk_masks(const float *__restric
         const int s = chunk_super(cbase, G.ns, k);
         const uint32_t a = seg[2 * s] + (k - cbase[s]) * kChunk;
         const uint32_t b = min(a + (uint32_t)kChunk, seg[2 * s + 1]);
-        const int sx = s % G.sgx, sy = s / G.sgx;
         uint32_t my = 0;  // this warp's count for tile `lane`
-        for (uint32_t i0 = a; i0 < b; i0 += kThreads) {
-            const uint32_t i = i0 + threadIdx.x;
-            uint32_t mask = 0;
-            if (i < b) {
-                const SplatGeom sg = splat_geom(rec, radius, svals[i], G);
-                const int tx0 = max(sg.rc.x, sx * kSX), tx1 = min(sg.rc.z, sx * kSX + kSX);
-                const int ty0 = max(sg.rc.y, sy * kSY), ty1 = min(sg.rc.w, sy * kSY + kSY);
-                const RowCull rcl = row_cull(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau);
-                for (int ty = ty0; ty < ty1; ++ty) {
-                    const uint32_t rowbit = (uint32_t)(ty - sy * kSY) * kSX - sx * kSX;
-                    if (!cull) {
-                        for (int tx = tx0; tx < tx1; ++tx) mask |= 1u << (rowbit + tx);
-                    } else if (rcl.degenerate) {
-                        for (int tx = tx0; tx < tx1; ++tx)
-                            if (tile_reachable(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau,
-                                               tx, ty, G.tw, G.th))
-                                mask |= 1u << (rowbit + tx);
-                    } else {
-                        float L, U;
-                        if (!row_interval(rcl, ty, G.th, L, U)) continue;
-                        for (int tx = tx0; tx < tx1; ++tx)
-                            if (tile_in_row(rcl, tx, G.tw, L, U)) mask |= 1u << (rowbit + tx);
-                    }
-                }
-                masks[i] = mask;
-            }
-#pragma unroll
-            for (int l = 0; l < 32; ++l) {
-                const uint32_t m = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
-                if (lane == l) my += __popc(m);
-            }
+        for (uint32_t i = a + threadIdx.x; i - threadIdx.x < b; i += kThreads) {
+            const uint32_t mask = i < b ? (uint32_t)(svals[i] >> 32) : 0u;
+            my += __popc(warp_transpose(mask, lane));
         }
         s_cnt[wid][lane] = my;
         __syncthreads();
@@ -365,66 +631,67 @@ __global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t *__restrict
     }
 }
 
-// Stage 3d: write every item's pairs. Rank of an item in a tile = chunk
-// offset + items of earlier passes + earlier warps + earlier lanes listed in
-// that tile (from one ballot per tile per warp).
-__global__ void __launch_bounds__(kThreads) k_chunk_emit(const uint32_t *__restrict__ svals,
-                                                        const uint32_t *__restrict__ masks,
+// Stage 3d: write every item's pairs. Each warp takes 128 consecutive items
+// of the chunk (4 rounds of 32); a tile's position for an item = chunk
+// offset + items of earlier warps + items of earlier rounds + earlier lanes
+// of the round listed in that tile (one ballot per tile). Pairs are written
+// tile by tile, so the lanes listed in one tile store to consecutive
+// addresses.
+__global__ void __launch_bounds__(kThreads) k_chunk_emit(const uint64_t *__restrict__ svals,
                                                         const uint32_t *__restrict__ seg,
                                                         const uint32_t *__restrict__ cbase,
                                                         const uint32_t *__restrict__ ccount,
                                                         const uint32_t *__restrict__ tstart, Geo G,
                                                         int64_t cap, uint32_t *__restrict__ vals) {
-    __shared__ uint32_t s_bal[kWarps][32];
-    __shared__ uint32_t s_wpre[kWarps][32];
-    __shared__ uint32_t s_base[32];
+    constexpr int kRounds = kChunk / kThreads;
+    constexpr int kPerWarp = kChunk / kWarps;
+    __shared__ uint32_t s_w[kWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t cap32 = (uint32_t)cap;  // cap < 2^32
     const uint32_t K = cbase[G.ns];
     for (uint32_t k = blockIdx.x; k < K; k += gridDim.x) {
         const int s = chunk_super(cbase, G.ns, k);
         const uint32_t a = seg[2 * s] + (k - cbase[s]) * kChunk;
         const uint32_t b = min(a + (uint32_t)kChunk, seg[2 * s + 1]);
-        if (threadIdx.x < 32)
-            s_base[threadIdx.x] = tstart[s * 32 + threadIdx.x] + ccount[(size_t)k * 32 + threadIdx.x];
-        __syncthreads();
-        for (uint32_t i0 = a; i0 < b; i0 += kThreads) {
-            const uint32_t i = i0 + threadIdx.x;
-            const uint32_t mask = i < b ? masks[i] : 0u;
-            const uint32_t g = i < b ? svals[i] : 0u;
-            uint32_t mycnt = 0;
+        const uint32_t w0 = a + wid * kPerWarp;
+        uint32_t g[kRounds], mk[kRounds], tc[kRounds];
+        uint32_t cnt = 0;
 #pragma unroll
-            for (int l = 0; l < 32; ++l) {
-                const uint32_t m = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
-                if (lane == l) {
-                    s_bal[wid][l] = m;
-                    mycnt = __popc(m);
-                }
-            }
-            s_wpre[wid][lane] = mycnt;
-            __syncthreads();
-            // exclusive prefix over warps for tile `threadIdx.x`; the pass
-            // total stays in `tot` of threads 0..31
-            uint32_t tot = 0;
-            if (threadIdx.x < 32) {
-                for (int w = 0; w < kWarps; ++w) {
-                    const uint32_t c = s_wpre[w][threadIdx.x];
-                    s_wpre[w][threadIdx.x] = tot;
-                    tot += c;
-                }
-            }
-            __syncthreads();
-            uint32_t mm = mask;
-            while (mm) {
-                const int l = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const uint64_t pos = (uint64_t)s_base[l] + s_wpre[wid][l] + __popc(s_bal[wid][l] & lt);
-                if (pos < (uint64_t)cap) vals[pos] = g;
-            }
-            __syncthreads();
-            if (threadIdx.x < 32) s_base[threadIdx.x] += tot;
-            __syncthreads();
+        for (int j = 0; j < kRounds; ++j) {
+            const uint32_t i = w0 + j * 32 + lane;
+            const uint64_t v = i < b ? svals[i] : 0ull;
+            g[j] = (uint32_t)v;
+            mk[j] = (uint32_t)(v >> 32);
+            tc[j] = __popc(warp_transpose(mk[j], lane));  // round's items in tile `lane`
+            cnt += tc[j];
         }
+        s_w[wid][lane] = cnt;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t run = tstart[s * 32 + lane] + ccount[(size_t)k * 32 + lane];
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = s_w[w][lane];
+                s_w[w][lane] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        uint32_t run = s_w[wid][lane];  // next position in tile `lane`
+#pragma unroll
+        for (int j = 0; j < kRounds; ++j) {
+            if (__any_sync(0xffffffffu, mk[j] != 0u)) {
+#pragma unroll
+                for (int l = 0; l < 32; ++l) {
+                    const bool has = (mk[j] >> l) & 1u;
+                    const uint32_t bl = __ballot_sync(0xffffffffu, has);
+                    const uint32_t at = __shfl_sync(0xffffffffu, run, l) + __popc(bl & lt);
+                    if (has && at < cap32) vals[at] = g[j];
+                }
+            }
+            run += tc[j];
+        }
+        __syncthreads();
     }
 }
 
@@ -442,7 +709,8 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
                     uint32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t s) {
     const Geo G = make_geo(cam, tw, th);
     const int ntiles = G.gx * G.gy;
-    if (ntiles > 65536 || G.ns > 65536) return LGS_ERR_INVALID_ARG;
+    // row spans hold tile columns in 16 bits
+    if (ntiles > 65536 || G.ns > 65536 || G.gx > 65535) return LGS_ERR_INVALID_ARG;
     Layout L = layout(ws, maxV, cap, G.ns);
     if (L.bytes > ws_bytes) return LGS_ERR_INVALID_ARG;
     // 1. depth sort of the splats
@@ -456,43 +724,56 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
     if (st != LGS_OK) return st;
     const uint32_t *order = L.dvals[ob];
     // 2. (super-tile, splat) items in depth order, then grouped by super-tile
-    const unsigned gw = grid_for(maxV, kThreads);
+    cudaMemsetAsync(L.gstatus, 0, L.gstatus_bytes, s);
     count_launch();
-    k_super_walk<false><<<gw, kThreads, 0, s>>>(sp->rec, sp->radius, order, maxV, d_V, G, cull,
-                                               L.scnt, nullptr, 0, nullptr, nullptr);
-    st = exclusive_scan_u32_to_u64(L.scnt, L.soff, maxV, d_V, L.d_psup, L.scan, s);
-    if (st != LGS_OK) return st;
+    k_super_items<<<grid_for(maxV, kThreads, 8), kThreads, 0, s>>>(
+        sp->rec, sp->radius, order, maxV, d_V, G, cull, L.gcounter, L.gstatus, cap, L.skeys[0],
+        L.svals[0], L.d_psup);
     count_launch();
     k_check_super_capacity<<<1, 1, 0, s>>>(L.d_psup, cap);
-    count_launch();
-    k_super_walk<true><<<gw, kThreads, 0, s>>>(sp->rec, sp->radius, order, maxV, d_V, G, cull,
-                                              nullptr, L.soff, cap, L.skeys[0], L.svals[0]);
     st = check_launch();
     if (st != LGS_OK) return st;
-    st = radix_sort_u16(L.skeys, L.svals, cap, L.d_psup, nullptr, bits_for(G.ns), L.hist, &ob, s);
+    const int sbits = bits_for(G.ns);
+    st = radix_sort_u16_v64(L.skeys, L.svals, cap, L.d_psup, nullptr, sbits, L.hist, &ob, s);
     if (st != LGS_OK) return st;
-    const uint16_t *skeys = L.skeys[ob];
-    const uint32_t *svals = L.svals[ob];
-    cudaMemsetAsync(L.seg, 0, (size_t)G.ns * 8, s);
+    const uint64_t *svals = L.svals[ob];
+    const uint32_t *hist = nullptr;
+    if (radix_passes(sbits) == 1) {
+        // one pass: its digit counts are the item counts of the super-tiles
+        hist = static_cast<const uint32_t *>(L.hist);
+    } else {
+        cudaMemsetAsync(L.seg, 0, (size_t)G.ns * 8, s);
+        count_launch();
+        k_seg_ranges<<<grid_for(cap, kThreads), kThreads, 0, s>>>(L.skeys[ob], L.d_psup, cap,
+                                                                  L.seg);
+    }
     count_launch();
-    k_seg_ranges<<<grid_for(cap, kThreads), kThreads, 0, s>>>(skeys, L.d_psup, cap, L.seg);
-    count_launch();
-    k_chunk_plan<<<1, 1024, 0, s>>>(L.seg, G.ns, L.cbase);
+    k_chunk_plan<<<1, 1024, 0, s>>>(hist, L.seg, G.ns, L.cbase);
     // 3. masks, chunk counts, offsets, tile starts, pairs
     const int64_t mc = max_chunks(G.ns, cap), cap_blocks = (int64_t)num_sms() * 16;
     const unsigned gc = (unsigned)(mc < cap_blocks ? mc : cap_blocks);
     count_launch();
-    k_chunk_masks<<<gc, kThreads, 0, s>>>(sp->rec, sp->radius, svals, L.seg, L.cbase, G, cull,
-                                         L.masks, L.ccount);
+    k_chunk_counts<<<gc, kThreads, 0, s>>>(svals, L.seg, L.cbase, G, L.ccount);
     count_launch();
     k_chunk_offsets<<<(unsigned)ceil_div((int64_t)G.ns * 32, kThreads), kThreads, 0, s>>>(
         L.ccount, L.cbase, G.ns, L.ttotal);
     count_launch();
     k_tile_starts<<<1, 1024, 0, s>>>(L.ttotal, G, L.tstart, ranges, d_P, cap);
     count_launch();
-    k_chunk_emit<<<gc, kThreads, 0, s>>>(svals, L.masks, L.seg, L.cbase, L.ccount, L.tstart, G, cap,
+    k_chunk_emit<<<gc, kThreads, 0, s>>>(svals, L.seg, L.cbase, L.ccount, L.tstart, G, cap,
                                         vals);
     return check_launch();
+}
+
+lgs_status bin_wait_timeouts(uint32_t *count) {
+    unsigned int h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_bin_wait_timeouts, sizeof(h)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_bin_wait_timeouts, &zero, sizeof(zero)) != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    *count = h;
+    return h ? LGS_ERR_TIMEOUT : LGS_OK;
 }
 
 lgs_status get_overflow(int64_t *needed) {

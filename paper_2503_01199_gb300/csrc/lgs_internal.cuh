@@ -51,16 +51,23 @@ __device__ __forceinline__ float ordered_to_float(uint32_t b) {
     return __uint_as_float((b & 0x80000000u) ? (b & 0x7fffffffu) : ~b);
 }
 
+// x / t correctly rounded; for a power-of-two t, x times the exact 1 / t,
+// which rounds the same real number once and so gives the same float.
+__device__ __forceinline__ float div_by_size(float x, int t) {
+    if ((t & (t - 1)) == 0) return __fmul_rn(x, __int_as_float((127 - (__ffs(t) - 1)) << 23));
+    return __fdiv_rn(x, (float)t);
+}
+
 // Tile rectangle of a splat: tiles whose pixel square meets
 // [u - r, u + r] x [v - r, v + r], end-exclusive, clamped to the grid.
 // Single precision with explicit rounding so that every caller (and any
 // reference) obtains the same integers.
 __device__ __forceinline__ int4 tile_rect(float u, float v, float r, int tw, int th, int gx,
                                           int gy) {
-    float x0 = floorf(__fdiv_rn(__fsub_rn(u, r), (float)tw));
-    float x1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(u, r), (float)tw)), 1.0f);
-    float y0 = floorf(__fdiv_rn(__fsub_rn(v, r), (float)th));
-    float y1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(v, r), (float)th)), 1.0f);
+    float x0 = floorf(div_by_size(__fsub_rn(u, r), tw));
+    float x1 = __fadd_rn(floorf(div_by_size(__fadd_rn(u, r), tw)), 1.0f);
+    float y0 = floorf(div_by_size(__fsub_rn(v, r), th));
+    float y1 = __fadd_rn(floorf(div_by_size(__fadd_rn(v, r), th)), 1.0f);
     x0 = fminf(fmaxf(x0, 0.0f), (float)gx);
     x1 = fminf(fmaxf(x1, 0.0f), (float)gx);
     y0 = fminf(fmaxf(y0, 0.0f), (float)gy);
@@ -185,9 +192,15 @@ size_t radix_sort_workspace(int64_t n, int key_bytes);
 // counted; sort_wait_timeouts() reads and clears the count.
 size_t radix_hist_bytes(int64_t n_max);
 lgs_status sort_wait_timeouts(uint32_t *count);
+// The same count for the binning's look-back over groups of splats.
+lgs_status bin_wait_timeouts(uint32_t *count);
 lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
                           const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                           cudaStream_t s);
+// The same with 64-bit values.
+lgs_status radix_sort_u16_v64(uint16_t *keys[2], uint64_t *vals[2], int64_t n_max,
+                              const int64_t *d_n64, const int32_t *d_n32, int bits, void *scratch,
+                              int *out_buf, cudaStream_t s);
 lgs_status radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
                           const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                           cudaStream_t s);

@@ -1,4 +1,5 @@
-// Stable LSD radix sort of (key, u32 value) pairs and an exclusive scan,
+// Stable LSD radix sort of (key, value) pairs (u32 or u64 values) and an
+// exclusive scan,
 // both with the element count read on the device, so that they can sit in a
 // captured CUDA graph behind kernels that produce the count.
 //
@@ -140,10 +141,10 @@ __global__ void __launch_bounds__(256) k_onesweep_reset(uint32_t *__restrict__ s
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
 }
 
-template <typename K>
+template <typename K, typename V>
 __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
-    const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
-    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ hist, uint32_t *status,
+    const K *__restrict__ keys_in, const V *__restrict__ vals_in, K *__restrict__ keys_out,
+    V *__restrict__ vals_out, const uint32_t *__restrict__ hist, uint32_t *status,
     uint32_t *counter, int64_t n_max, const int64_t *d_n64, const int32_t *d_n32, int shift) {
     __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
     __shared__ uint32_t s_gstart[kRadix];
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     __shared__ uint64_t s_scan[33];
     __shared__ uint32_t s_tile;
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    K *s_keys = reinterpret_cast<K *>(s_dyn);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_dyn + sizeof(K) * kTile);
+    V *s_vals = reinterpret_cast<V *>(s_dyn);
+    K *s_keys = reinterpret_cast<K *>(s_dyn + sizeof(V) * kTile);
 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t n = read_count(n_max, d_n64, d_n32);
@@ -173,14 +174,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
         if (tile >= tiles) break;
         const int64_t base = tile * kTile;
         K key[kItemsPerThread];
-        uint32_t val[kItemsPerThread], rank[kItemsPerThread];
+        V val[kItemsPerThread];
+        uint32_t rank[kItemsPerThread];
         int dig[kItemsPerThread];
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
             const int64_t idx = base + wid * (kWarp * kItemsPerThread) + j * kWarp + lane;
             const bool ok = idx < n;
             key[j] = ok ? keys_in[idx] : (K)0;
-            val[j] = ok ? vals_in[idx] : 0u;
+            val[j] = ok ? vals_in[idx] : (V)0;
             dig[j] = ok ? digit_of(key[j], shift) : -1;
         }
 #pragma unroll
@@ -262,8 +264,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
 
 int64_t sort_tiles(int64_t n_max) { return (n_max + kTile - 1) / kTile; }
 
-template <typename K>
-lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
+template <typename K, typename V>
+lgs_status radix_sort_impl(K *keys[2], V *vals[2], int64_t n_max, const int64_t *d_n64,
                            const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                            cudaStream_t s) {
     if (n_max <= 0) {
@@ -276,16 +278,17 @@ lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const i
     uint32_t *hist = static_cast<uint32_t *>(scratch);             // [kMaxPasses][256]
     uint32_t *counter = hist + kMaxPasses * kRadix;                 // 64 words
     uint32_t *status = counter + 64;                                // [tiles][256]
-    const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * kTile;
+    const size_t dyn = (sizeof(K) + sizeof(V)) * kTile;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaFuncSetAttribute(k_onesweep<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn);
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, kSortThreads, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, V>, kSortThreads, dyn);
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const int64_t tmax = sort_tiles(n_max);
     const unsigned grid = (unsigned)(tmax < cap ? tmax : cap);
@@ -299,7 +302,7 @@ lgs_status radix_sort_impl(K *keys[2], uint32_t *vals[2], int64_t n_max, const i
         k_onesweep_reset<<<grid_for(tmax * kRadix, 256, 4), 256, 0, s>>>(status, counter, n_max,
                                                                       d_n64, d_n32);
         count_launch();
-        k_onesweep<K><<<grid, kSortThreads, dyn, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
+        k_onesweep<K, V><<<grid, kSortThreads, dyn, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
                                                       vals[cur ^ 1], hist + p * kRadix, status,
                                                       counter, n_max, d_n64, d_n32, p * 8);
         cur ^= 1;
@@ -386,19 +389,29 @@ lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, c
                           const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                           cudaStream_t s) {
     if (bits > 16) return LGS_ERR_INVALID_ARG;
-    return radix_sort_impl<uint16_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch, out_buf, s);
+    return radix_sort_impl<uint16_t, uint32_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch,
+                                               out_buf, s);
+}
+lgs_status radix_sort_u16_v64(uint16_t *keys[2], uint64_t *vals[2], int64_t n_max,
+                              const int64_t *d_n64, const int32_t *d_n32, int bits, void *scratch,
+                              int *out_buf, cudaStream_t s) {
+    if (bits > 16) return LGS_ERR_INVALID_ARG;
+    return radix_sort_impl<uint16_t, uint64_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch,
+                                               out_buf, s);
 }
 lgs_status radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
                           const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                           cudaStream_t s) {
     if (bits > 32) return LGS_ERR_INVALID_ARG;
-    return radix_sort_impl<uint32_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch, out_buf, s);
+    return radix_sort_impl<uint32_t, uint32_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch,
+                                               out_buf, s);
 }
 lgs_status radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
                           const int32_t *d_n32, int bits, void *scratch, int *out_buf,
                           cudaStream_t s) {
     if (bits > 64) return LGS_ERR_INVALID_ARG;
-    return radix_sort_impl<uint64_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch, out_buf, s);
+    return radix_sort_impl<uint64_t, uint32_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch,
+                                               out_buf, s);
 }
 
 size_t scan_scratch_bytes() { return kScanBlocks * sizeof(uint64_t); }
