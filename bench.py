@@ -313,7 +313,8 @@ def run_gpu(args) -> dict | None:
         mark(8)
         tr.step_count += 1
         B.lgs_preprocess_bwd_adam(tr.gaussians(), tr.m, tr.v, tr.rowmap, tr.d_V, cs, tr.gacc,
-                                  tr.lr, tr.cfg.beta1, tr.cfg.beta2, tr.cfg.eps, tr.step_count)
+                                  tr.lr, tr.cfg.beta1, tr.cfg.beta2, tr.cfg.eps, tr.step_count,
+                                  splats=tr.splats)
         mark(9)
 
     for w in range(args.warmup):
@@ -408,21 +409,22 @@ def run_gpu(args) -> dict | None:
     value = job_rate(world, args.steps, ms)
     e2e_value = job_rate(world, args.steps, e2e_ms)
     # ---- roofline of the dominant HBM-bound call: the fused preprocess
-    # backward + Adam (k_bwd_adam_fused), 1468 B per visible
-    # Gaussian at SH3: params, m, v read and written (6 x 59 x 4 B), the
-    # 9 gradients + S, M, C of its grad row (48 B) and its map entry (4 B)
+    # backward + Adam (k_bwd_adam_rec), 1480 B per visible Gaussian at SH3:
+    # params, m, v read and written (6 x 59 x 4 B), the 9 gradients + S, M, C
+    # of its grad row (48 B), its map entry (4 B) and the 3 colours of its
+    # splat record (12 B)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
     npl = B.num_planes(SH_DEG)
-    per_unit = {"a9a10_bwd_adam": 6 * npl * 4 + 48 + 4,
+    per_unit = {"a9a10_bwd_adam": 6 * npl * 4 + 48 + 4 + 12,
                 "a3_preprocess": npl * 4 + 4 + 48 + 4 + 4}  # params + map in; record, depth, radius out
     dom = "a9a10_bwd_adam"
     achieved = V * per_unit[dom] / (stage_ms[dom] * 1e-3) / 1e9
     tr_rec = traffic_record().get(dom, {})
     traffic = (round(tr_rec["bytes_per_unit"] * V) if tr_rec.get("source") == source_digest()
                and "bytes_per_unit" in tr_rec else None)
-    roofline = {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_fused<3>)",
+    roofline = {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_rec<3>)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "peak_source": "measured" if hbm else "fallback",
                 "frac": round(achieved / peak, 4), "traffic": traffic,

@@ -405,10 +405,14 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
 /* a9 + a10 without a gradient buffer: each parameter's gradient is applied
  * by Adam as soon as it is computed. m and v are planes with the stride of g;
  * g->data is updated in place. Same results as lgs_preprocess_bwd followed by
- * lgs_adam_step up to rounding. grad_acc is read only. */
+ * lgs_adam_step up to rounding. grad_acc is read only.
+ * sp (may be NULL): the splat records lgs_preprocess wrote for this camera
+ * from these parameters (rows j < V, read only). With them the colour clamp
+ * is taken from the stored colours instead of recomputing the colours, so
+ * the SH planes are read once; without them the colours are recomputed. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
-                                   const lgs_camera *cam, float *grad_acc,
+                                   const lgs_camera *cam, const lgs_splats *sp, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream);
 

@@ -29,9 +29,9 @@ lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int
                           const lgs_camera *cam, const float *gacc, float *gout, int accumulate,
                           cudaStream_t s);
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
-                               const int32_t *d_V, const lgs_camera *cam, float *gacc,
-                               const float *lr, float b1, float b2, float eps, int step,
-                               cudaStream_t s);
+                               const int32_t *d_V, const lgs_camera *cam, const float *rec,
+                               float *gacc, const float *lr, float b1, float b2, float eps,
+                               int step, cudaStream_t s);
 lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t stride, int np,
                      const float *lr, float b1, float b2, float eps, int step, const uint32_t *map,
                      const int32_t *d_V, int64_t max_rows, cudaStream_t s);
@@ -320,15 +320,16 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
 
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
-                                   const lgs_camera *cam, float *grad_acc,
+                                   const lgs_camera *cam, const lgs_splats *sp, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream) {
     if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||
-        !aligned16(grad_acc) || !aligned16(m) || !aligned16(v) || training_only(g, cam))
+        !aligned16(grad_acc) || !aligned16(m) || !aligned16(v) || training_only(g, cam) ||
+        (sp && (!sp->rec || !aligned16(sp->rec))))
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
-    return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, grad_acc, lr, beta1, beta2, eps,
-                               step, as_stream(stream));
+    return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, sp ? sp->rec : nullptr, grad_acc,
+                               lr, beta1, beta2, eps, step, as_stream(stream));
 }
 
 lgs_status lgs_moments_accumulate(const float *grad_acc, const uint32_t *map,

@@ -104,6 +104,64 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     gy += -Y33 * 6.0f * x * y * w[15];
 }
 
+// The terms of sh_basis_grad for coefficient k alone (same expressions, so
+// summing k = 1.. in order adds the same terms in the same order).
+__device__ __forceinline__ void sh_grad_single(int k, float x, float y, float z, float w,
+                                               float &gx, float &gy, float &gz) {
+    switch (k) {
+        case 0: break;
+        case 1: gy += -Y1 * w; break;
+        case 2: gz += Y1 * w; break;
+        case 3: gx += -Y1 * w; break;
+        case 4: gx += Y22 * 2.0f * y * w; gy += Y22 * 2.0f * x * w; break;
+        case 5: gy += Y21 * z * w; gz += Y21 * y * w; break;
+        case 6: gz += Y20 * 3.0f * z * w; break;
+        case 7: gx += Y21 * z * w; gz += Y21 * x * w; break;
+        case 8: gx += Y22 * 2.0f * x * w; gy += -Y22 * 2.0f * y * w; break;
+        case 9: {
+            const float xx = x * x, yy = y * y;
+            gx += Y33 * 6.0f * x * y * w;
+            gy += Y33 * (3.0f * xx - 3.0f * yy) * w;
+            break;
+        }
+        case 10:
+            gx += Y32 * 2.0f * y * z * w;
+            gy += Y32 * 2.0f * x * z * w;
+            gz += Y32 * 2.0f * x * y * w;
+            break;
+        case 11: {
+            const float zz = z * z;
+            gy += Y31 * (15.0f * zz - 3.0f) * w;
+            gz += Y31 * 30.0f * y * z * w;
+            break;
+        }
+        case 12: {
+            const float zz = z * z;
+            gz += Y30 * 0.5f * (15.0f * zz - 3.0f) * w;
+            break;
+        }
+        case 13: {
+            const float zz = z * z;
+            gx += Y31 * (15.0f * zz - 3.0f) * w;
+            gz += Y31 * 30.0f * x * z * w;
+            break;
+        }
+        case 14: {
+            const float xx = x * x, yy = y * y;
+            gx += Y32 * 2.0f * x * z * w;
+            gy += -Y32 * 2.0f * y * z * w;
+            gz += Y32 * (xx - yy) * w;
+            break;
+        }
+        default: {
+            const float xx = x * x, yy = y * y;
+            gx += Y33 * (3.0f * xx - 3.0f * yy) * w;
+            gy += -Y33 * 6.0f * x * y * w;
+            break;
+        }
+    }
+}
+
 // Everything the forward computes for one Gaussian, kept for the backward.
 struct Fwd {
     bool culled;
@@ -577,9 +635,27 @@ __device__ __forceinline__ float sh_single(int k, float x, float y, float z) {
     }
 }
 
+// Asynchronous 4-byte global -> shared copy (cp.async), its commit and wait.
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // A CTA runs part A for its chunk, then part B; CTAs in different phases
-// overlap part A's arithmetic with part B's memory traffic. Bounded to four
-// CTAs per SM (64 registers): occupancy matters more than the few spills.
+// overlap part A's arithmetic with part B's memory traffic. Part B keeps
+// kStages coefficients' loads in flight through shared memory (cp.async),
+// so its memory parallelism does not cost registers; every thread reads
+// back only what it copied itself. Bounded to four CTAs per SM (64
+// registers).
+constexpr int kStages = 4;
+
 template <int DEG>
 __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
@@ -588,6 +664,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
     constexpr int KK = (DEG + 1) * (DEG + 1);
     __shared__ float s_g[3][256], s_d[3][256];
     __shared__ int64_t s_row[256];
+    __shared__ float s_buf[kStages][9][256];  // p, m, v of the 3 channels
     const int tid = threadIdx.x;
     const int64_t V = load_count(d_V, n);
     for (int64_t c0 = (int64_t)blockIdx.x * 256; c0 < V; c0 += (int64_t)gridDim.x * 256) {
@@ -609,25 +686,162 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
             const int64_t row = s_row[tid];
             const float gr[3] = {s_g[0][tid], s_g[1][tid], s_g[2][tid]};
             const float dx = s_d[0][tid], dy = s_d[1][tid], dz = s_d[2][tid];
-#pragma unroll 2
+            auto issue = [&](int k) {
+                if (k < KK) {
+                    const int64_t at = (11 + 3 * k) * stride + row;
+                    float(*b)[256] = s_buf[k % kStages];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        cp_async4(&b[ch][tid], P + at + ch * stride);
+                        cp_async4(&b[3 + ch][tid], Mo + at + ch * stride);
+                        cp_async4(&b[6 + ch][tid], Vo + at + ch * stride);
+                    }
+                }
+                cp_async_commit();  // empty past the last coefficient
+            };
+#pragma unroll
+            for (int k = 0; k < kStages - 1; ++k) issue(k);
+#pragma unroll 1
             for (int k = 0; k < KK; ++k) {
+                issue(k + kStages - 1);
+                cp_async_wait<kStages - 1>();  // coefficient k has landed
+                const float(*b)[256] = s_buf[k % kStages];
                 const float yk = sh_single(k, dx, dy, dz);
                 const int64_t at = (11 + 3 * k) * stride + row;
-                float *pp = P + at, *pm = Mo + at, *pv = Vo + at;
-                float p[3], m[3], v[3];
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    p[ch] = pp[ch * stride];
-                    m[ch] = pm[ch * stride];
-                    v[ch] = pv[ch * stride];
+                    float p = b[ch][tid], m = b[3 + ch][tid], v = b[6 + ch][tid];
+                    adam_update(p, m, v, gr[ch] * yk, a.lr[11 + 3 * k + ch], a);
+                    P[at + ch * stride] = p;
+                    Mo[at + ch * stride] = m;
+                    Vo[at + ch * stride] = v;
                 }
+            }
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+    }
+}
+
+// The same step when the splat records of the forward are at hand (rec,
+// 12 floats per compacted row, colours at 6..8, clamped at 0). Part A takes
+// the colour clamp from the stored colours (stored > 0 exactly when the raw
+// colour is > 0, both sides computing it the same way), so it reads no SH
+// plane: it runs the geometric backward, applies Adam to planes 3..10 and
+// hands the masked colour gradient, the view direction, 1 / distance and the
+// centre's geometric gradient to part B. Part B streams the SH coefficients
+// once: Adam on each, while summing the view direction's gradient
+// sum_k (sum_ch grgb_ch c_k,ch) grad Y_k from the coefficients as read; it
+// then completes the centre's gradient and applies Adam to planes 0..2.
+constexpr int kStagesRec = 3;
+
+template <int DEG>
+__global__ void __launch_bounds__(256, 4) k_bwd_adam_rec(
+    float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
+    int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
+    const float *__restrict__ gacc, const float *__restrict__ rec, AdamArgs a) {
+    constexpr int KK = (DEG + 1) * (DEG + 1);
+    __shared__ float s_g[3][256], s_d[3][256], s_c[4][256];  // s_c: centre gradient, 1 / dist
+    __shared__ int64_t s_row[256];
+    __shared__ float s_buf[kStagesRec][9][256];
+    __shared__ float s_cen[9][256];
+    const int tid = threadIdx.x;
+    const int64_t V = load_count(d_V, n);
+    for (int64_t c0 = (int64_t)blockIdx.x * 256; c0 < V; c0 += (int64_t)gridDim.x * 256) {
+        const int64_t j = c0 + tid;
+        if (j < V) {
+            const int64_t row = map ? map[j] : j;
+            GeomSink sink{P, Mo, Vo, stride, row, &a};
+            Fwd f;
+            float gm[3] = {0.f, 0.f, 0.f}, grgb[3] = {0.f, 0.f, 0.f}, dir[3] = {0.f, 0.f, 0.f};
+            float dinv = 0.f;
+            if (geom_forward(K, P, stride, row, f)) {
+                const float *g16 = gacc + 16 * j;
+                geom_backward(K, f, g16, sink, gm);
+                const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
+                const float gcb = g16[8];
+                const float4 cr = reinterpret_cast<const float4 *>(rec + 12 * j)[1];
+                const float cb = rec[12 * j + 8];
+                grgb[0] = cr.z > 0.f ? gb.z : 0.f;
+                grgb[1] = cr.w > 0.f ? gb.w : 0.f;
+                grgb[2] = cb > 0.f ? gcb : 0.f;
+                dir[0] = f.dir[0];
+                dir[1] = f.dir[1];
+                dir[2] = f.dir[2];
+                dinv = f.dinv;
+            } else {
+#pragma unroll
+                for (int k = 3; k < 11; ++k) sink(k, 0.0f);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                s_g[c][tid] = grgb[c];
+                s_d[c][tid] = dir[c];
+                s_c[c][tid] = gm[c];
+            }
+            s_c[3][tid] = dinv;
+            s_row[tid] = row;
+        }
+        __syncthreads();
+        if (j < V) {
+            const int64_t row = s_row[tid];
+            const float gr[3] = {s_g[0][tid], s_g[1][tid], s_g[2][tid]};
+            const float dx = s_d[0][tid], dy = s_d[1][tid], dz = s_d[2][tid];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cp_async4(&s_cen[c][tid], P + c * stride + row);
+                cp_async4(&s_cen[3 + c][tid], Mo + c * stride + row);
+                cp_async4(&s_cen[6 + c][tid], Vo + c * stride + row);
+            }
+            cp_async_commit();
+            auto issue = [&](int k) {
+                if (k < KK) {
+                    const int64_t at = (11 + 3 * k) * stride + row;
+                    float(*b)[256] = s_buf[k % kStagesRec];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        cp_async4(&b[ch][tid], P + at + ch * stride);
+                        cp_async4(&b[3 + ch][tid], Mo + at + ch * stride);
+                        cp_async4(&b[6 + ch][tid], Vo + at + ch * stride);
+                    }
+                }
+                cp_async_commit();  // empty past the last coefficient
+            };
+#pragma unroll
+            for (int k = 0; k < kStagesRec - 1; ++k) issue(k);
+            float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+#pragma unroll 1
+            for (int k = 0; k < KK; ++k) {
+                issue(k + kStagesRec - 1);
+                cp_async_wait<kStagesRec - 1>();  // coefficient k has landed
+                const float(*b)[256] = s_buf[k % kStagesRec];
+                const float yk = sh_single(k, dx, dy, dz);
+                const int64_t at = (11 + 3 * k) * stride + row;
+                float w = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    adam_update(p[ch], m[ch], v[ch], gr[ch] * yk, a.lr[11 + 3 * k + ch], a);
-                    pp[ch * stride] = p[ch];
-                    pm[ch * stride] = m[ch];
-                    pv[ch * stride] = v[ch];
+                    float p = b[ch][tid], m = b[3 + ch][tid], v = b[6 + ch][tid];
+                    w += gr[ch] * p;
+                    adam_update(p, m, v, gr[ch] * yk, a.lr[11 + 3 * k + ch], a);
+                    P[at + ch * stride] = p;
+                    Mo[at + ch * stride] = m;
+                    Vo[at + ch * stride] = v;
                 }
+                sh_grad_single(k, dx, dy, dz, w, gdx, gdy, gdz);
+            }
+            cp_async_wait<0>();
+            const float dinv = s_c[3][tid];
+            const float dd = gdx * dx + gdy * dy + gdz * dz;
+            const float gc[3] = {s_c[0][tid] + (gdx - dx * dd) * dinv,
+                                 s_c[1][tid] + (gdy - dy * dd) * dinv,
+                                 s_c[2][tid] + (gdz - dz * dd) * dinv};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float p = s_cen[c][tid], m = s_cen[3 + c][tid], v = s_cen[6 + c][tid];
+                adam_update(p, m, v, gc[c], a.lr[c], a);
+                P[c * stride + row] = p;
+                Mo[c * stride + row] = m;
+                Vo[c * stride + row] = v;
             }
         }
         __syncthreads();
@@ -706,13 +920,22 @@ lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int
 }
 
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
-                               const int32_t *d_V, const lgs_camera *cam, float *gacc,
-                               const float *lr, float b1, float b2, float eps, int step,
-                               cudaStream_t s) {
+                               const int32_t *d_V, const lgs_camera *cam, const float *rec,
+                               float *gacc, const float *lr, float b1, float b2, float eps,
+                               int step, cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
     const unsigned gf = grid_for(g->n, 256, 8);
     count_launch();
+    if (rec) {
+        switch (g->sh_degree) {
+        case 0: k_bwd_adam_rec<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
+        case 1: k_bwd_adam_rec<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
+        case 2: k_bwd_adam_rec<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
+        default: k_bwd_adam_rec<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
+        }
+        return check_launch();
+    }
     switch (g->sh_degree) {
     case 0: k_bwd_adam_fused<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
     case 1: k_bwd_adam_fused<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;

@@ -223,7 +223,8 @@ class Trainer:
         g = self.gaussians()
         if fused:
             B.lgs_preprocess_bwd_adam(g, self.m, self.v, self._map(), self._dV(), cs, self.gacc,
-                                      self.lr, c.beta1, c.beta2, c.eps, self.step_count)
+                                      self.lr, c.beta1, c.beta2, c.eps, self.step_count,
+                                      splats=self.splats)
         else:
             if self.grad_planes is None:
                 self.grad_planes = torch.zeros((self.np_, self.stride), dtype=torch.float32,

@@ -188,7 +188,9 @@ def test_fused_backward_adam_map_layouts(layout):
     m0 = rng.standard_normal((59, 1000)).astype(np.float32) * 1e-3
     v0 = rng.uniform(0, 1e-4, (59, 1000)).astype(np.float32)
     out = []
-    for fused in (False, True):
+    # the separate path, the fused call recomputing the colours, and the
+    # fused call taking the colour clamp from the forward's splat records
+    for mode in ("separate", "fused", "fused_records"):
         planes, n = U.planes_tensor(sc)
         m = torch.zeros_like(planes)
         v = torch.zeros_like(planes)
@@ -199,21 +201,30 @@ def test_fused_backward_adam_map_layouts(layout):
         mp = U.t(rows.astype(np.uint32).view(np.int32))
         dV = U.t(np.array([V], np.int32))
         gacc = U.t(grads)
-        if fused:
+        if mode == "fused":
             B.lgs_preprocess_bwd_adam(g, m, v, mp, dV, cs, gacc, lr, 0.9, 0.999, 1e-15, 3)
+        elif mode == "fused_records":
+            rec = torch.empty((1000, B.SPLAT_FLOATS), dtype=torch.float32, device="cuda")
+            depth = torch.empty(1000, dtype=torch.float32, device="cuda")
+            radius = torch.empty(1000, dtype=torch.int32, device="cuda")
+            sp = B.splats_struct(rec, depth, radius)
+            B.lgs_preprocess(g, mp, dV, cs, 16, 16, sp)
+            B.lgs_preprocess_bwd_adam(g, m, v, mp, dV, cs, gacc, lr, 0.9, 0.999, 1e-15, 3,
+                                      splats=sp)
         else:
             gp = torch.zeros_like(planes)
             B.lgs_preprocess_bwd(g, mp, dV, cs, gacc, gp)
             B.lgs_adam_step(planes, gp, m, v, planes.shape[0], lr, 0.9, 0.999, 1e-15, 3, mp, dV, n)
         torch.cuda.synchronize()
         out.append((planes.cpu().numpy()[:, :n], m.cpu().numpy()[:, :n], v.cpu().numpy()[:, :n]))
-    (pa, ma, va), (pb, mb, vb) = out
+    pa, ma, va = out[0]
     hidden = np.setdiff1d(np.arange(1000), rows)
-    np.testing.assert_array_equal(pb[:, hidden], pa[:, hidden])
-    np.testing.assert_array_equal(mb[:, hidden], ma[:, hidden])
-    np.testing.assert_allclose(mb[:, rows], ma[:, rows], rtol=1e-4, atol=1e-9)
-    np.testing.assert_allclose(vb[:, rows], va[:, rows], rtol=1e-4, atol=1e-14)
-    np.testing.assert_allclose(pb[:, rows], pa[:, rows], rtol=1e-5, atol=1e-6)
+    for pb, mb, vb in out[1:]:
+        np.testing.assert_array_equal(pb[:, hidden], pa[:, hidden])
+        np.testing.assert_array_equal(mb[:, hidden], ma[:, hidden])
+        np.testing.assert_allclose(mb[:, rows], ma[:, rows], rtol=1e-4, atol=1e-9)
+        np.testing.assert_allclose(vb[:, rows], va[:, rows], rtol=1e-4, atol=1e-14)
+        np.testing.assert_allclose(pb[:, rows], pa[:, rows], rtol=1e-5, atol=1e-6)
 
 
 def test_loss_l1_kernel_matches_oracle(orc):
