@@ -46,16 +46,18 @@ SH_DEG = 3
 SEED = 2
 W_IMG, H_IMG = 1297, 840
 TILE = (16, 16)
-WORKLOAD = ("3M Gaussians SH3 uniform-box scene (seed 2, Morton-sorted), 1297x840 camera "
-            "fx=fy=1297, 16x16 tiles, training iteration a2-a10 (cluster cull/compact + "
-            "preprocess + bin sort + raster fwd + L1 + raster bwd + variance + fused "
-            "preprocess-bwd/Adam); the periodic Morton re-sort a1 is timed separately")
+WORKLOAD = ("3M Gaussians SH3 surface scene (the config-1 generator: 90% of the means on 32 "
+            "planes and 32 spheres, 10% on a radius-20 shell; seed 2, Morton-sorted), 1297x840 "
+            "orbit camera (radius 4, elevation 0.3 rad, fx=fy=0.78 W), 16x16 tiles, training "
+            "iteration a2-a10 (cluster cull/compact + preprocess + bin sort + raster fwd + L1 + "
+            "raster bwd + variance + fused preprocess-bwd/Adam); the periodic Morton re-sort a1 "
+            "is timed separately")
 
 
-def make_workload(seed_offset: int = 0, n: int | None = None):
+def make_workload(seed_offset: int = 0, n: int | None = None, width: int = W_IMG,
+                  height: int = H_IMG):
     from paper_2503_01199_gb300 import scenegen
-    return scenegen.uniform_box_scene(n or N_GAUSS, SH_DEG, SEED + seed_offset, W_IMG, H_IMG,
-                                      focal=float(W_IMG))
+    return scenegen.surface_scene(n or N_GAUSS, SH_DEG, SEED + seed_offset, width, height)
 
 
 # ---------------------------------------------------------------------------
@@ -176,8 +178,7 @@ def run_multiview(tr, steps: int, warmup: int) -> dict:
     from paper_2503_01199_gb300 import pipeline as PL
     from paper_2503_01199_gb300 import scenegen
     dev = tr.params.device
-    cams = scenegen.orbit_cameras(4, list(MV_RES), radius=4.0, elevation=0.3,
-                                  center=scenegen.BOX_CENTER)
+    cams = scenegen.orbit_cameras(4, list(MV_RES), radius=4.0, elevation=0.3)
     rng = np.random.default_rng(4)
     tgts = [torch.from_numpy(rng.uniform(0, 1, (3, h, w)).astype(np.float32)).to(dev)
             for w, h in MV_RES]
@@ -200,7 +201,7 @@ def run_multiview(tr, steps: int, warmup: int) -> dict:
     del mv
     torch.cuda.empty_cache()
     return {"workload": ("3M Gaussians SH3 (same scene), 8 orbit cameras (radius 4 around the "
-                         "box centre) at 640x360, 960x540, 1297x840, 1600x1063, two each: "
+                         "origin) at 640x360, 960x540, 1297x840, 1600x1063, two each: "
                          "per-view cull/preprocess/binning, batched raster fwd, L1, batched "
                          "raster bwd, preprocess bwd summed over views"),
             **out, "views_per_s": round(8 * 1e3 / out["graph_ms_per_batch"], 1),
@@ -254,6 +255,51 @@ def run_ccc_ablation(steps: int = 8, warmup: int = 2) -> dict:
                 del tr
                 torch.cuda.empty_cache()
         out[name] = res
+    return out
+
+
+def run_extra_configs(steps: int, warmup: int) -> dict:
+    """The other single-GPU configurations, each a whole a2-a10 iteration
+    through the pipeline on Morton-sorted state: the 3M scene with its
+    1600x1063 camera (plain and mixed blend), and the 500K surface scene
+    (seed 1) with its 1297x840 camera."""
+    import torch
+    from paper_2503_01199_gb300 import binding as B
+    from paper_2503_01199_gb300 import pipeline as PL
+    from paper_2503_01199_gb300 import scenegen
+    out = {}
+    cases = (("3m_1600x1063", lambda: make_workload(width=1600, height=1063),
+              (("fp32", B.LGS_FP32), ("fp16", B.LGS_MIXED_FP16), ("bf16", B.LGS_MIXED_BF16))),
+             ("500k_1297x840", lambda: scenegen.surface_scene(500_000, SH_DEG, 1, W_IMG, H_IMG),
+              (("fp32", B.LGS_FP32),)))
+    for name, make, precs in cases:
+        d = make()
+        cam = d["camera"]
+        tr = PL.Trainer(d["scene"], cam["width"], cam["height"],
+                        PL.StepConfig(tile=TILE, pair_capacity=128_000_000))
+        tr.morton_reorder()
+        cs = B.camera_struct(cam)
+        target = torch.from_numpy(d["target"]).to(tr.dev)
+        res = {"n_gaussians": int(d["scene"]["mean"].shape[0]),
+               "resolution": f"{cam['width']}x{cam['height']}"}
+        for pname, prec in precs:
+            tr.cfg.precision = prec
+            for _ in range(warmup):
+                tr.step(cs, target, reorder=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                tr.step(cs, target, reorder=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[pname] = {"iters_per_s": round(1e3 / ms, 2), "ms_per_iter": round(ms, 4)}
+        res["visible_gaussians"] = int(tr.d_V.item())
+        res["pairs"] = int(tr.d_P.item())
+        out[name] = res
+        del tr, target
+        torch.cuda.empty_cache()
     return out
 
 
@@ -481,33 +527,38 @@ def run_serving(seconds: float) -> dict:
     gc.collect()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    scenes = [SV.ResidentScene(scenegen.uniform_box_scene(n, SH_DEG, seed, 64, 64,
-                                                          with_target=False)["scene"])
+    scenes = [SV.ResidentScene(scenegen.surface_scene(n, SH_DEG, seed, 64, 64)["scene"])
               for n, seed in SERVE_SCENES]
+    origin = (0.0, 0.0, 0.0)
     need = SV.slot_bytes(max(n for n, _ in SERVE_SCENES), 1920, 1080, SERVE_PAIR_CAPACITY)
     budget = int(SERVE_SLOTS * need + need // 5)
     # a short discarded stream first (process warm-up after the training runs)
-    SV.serve(scenes, scenegen.render_requests(21, 1.0, SERVE_RATE, len(scenes), list(SERVE_RES)),
+    SV.serve(scenes, scenegen.render_requests(21, 1.0, SERVE_RATE, len(scenes), list(SERVE_RES),
+                                              center=origin),
              budget, list(SERVE_RES), SERVE_PAIR_CAPACITY)
     gc.collect()
     torch.cuda.empty_cache()
-    reqs = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES))
+    reqs = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES),
+                                     center=origin)
     served = SV.serve(scenes, reqs, budget, list(SERVE_RES), SERVE_PAIR_CAPACITY)
     st = served["stats"]
     del served
     torch.cuda.empty_cache()
-    reqs_g = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES))
+    reqs_g = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES),
+                                     center=origin)
     grouped = SV.serve(scenes, reqs_g, budget, list(SERVE_RES), SERVE_PAIR_CAPACITY,
                        grouped=True)
     gst = grouped["stats"]
     del grouped
     torch.cuda.empty_cache()
-    reqs2 = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES))
+    reqs2 = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES),
+                                     center=origin)
     plain = SV.plain_loop(scenes, reqs2, list(SERVE_RES), SERVE_PAIR_CAPACITY)["stats"]
-    return {"workload": ("4 resident scenes (uniform box, SH3, BF16 colour + FP32 geometry): "
-                         "0.5M/1M/2M/3M Gaussians, seeds 10-13; Poisson arrivals at 200 req/s "
-                         f"for {seconds:g} s, resolution uniform over 640x360/1280x720/"
-                         "1920x1080, orbit cameras; forward render + image to pinned host"),
+    return {"workload": ("4 resident scenes (config-1 surface generator, SH3, BF16 colour + "
+                         "FP32 geometry): 0.5M/1M/2M/3M Gaussians, seeds 10-13; Poisson arrivals "
+                         f"at 200 req/s for {seconds:g} s, resolution uniform over 640x360/"
+                         "1280x720/1920x1080, orbit cameras around the origin; forward render + "
+                         "image to pinned host"),
             "hbm_budget_bytes": budget, **{k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms",
                                                                "frames_per_s", "requests",
                                                                "slots", "max_inflight",
@@ -668,6 +719,8 @@ def main():
                       if args.serve_seconds > 0 and not args.n_gaussians else None)
     out["ccc_ablation"] = (run_ccc_ablation()
                            if not args.no_ablation and not args.n_gaussians else None)
+    out["other_configs"] = (run_extra_configs(args.steps, args.warmup)
+                            if not args.n_gaussians else None)
     if out["n_gpus"] == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(make_workload())
     else:

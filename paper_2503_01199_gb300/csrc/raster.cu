@@ -241,37 +241,52 @@ __global__ void __launch_bounds__(kBatch) k_raster_fwd(const float *__restrict__
     fwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, image, finalT, last, s_sp, s_fl);
 }
 
-// Reduce-scatter of 16 values across the warp: on return v[0] of lanes 2i
-// and 2i + 1 holds the warp sum of input value i.
-__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+// Reduce-scatter of 10 values across the warp in 12 shuffles (halving the
+// vector at every butterfly stage, odd lengths padded with a zero): on
+// return, the two lanes 2i, 2i + 1 hold the warp sum of value
+// scatter10_index(2i), or a padding zero when that index is negative.
+__device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int lane) {
+    float w[6], x[4], y[2];
+    {
+        const bool up = lane & 16;  // 10 -> 5
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool up = lane & 16;
-        const float send = up ? v[i] : v[i + 8];
-        const float keep = up ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = lane & 8;
-        const float send = up ? v[i] : v[i + 4];
-        const float keep = up ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = lane & 4;
-        const float send = up ? v[i] : v[i + 2];
-        const float keep = up ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        for (int i = 0; i < 5; ++i) {
+            const float send = up ? v[i] : v[i + 5];
+            const float keep = up ? v[i + 5] : v[i];
+            w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        w[5] = 0.0f;
     }
     {
-        const bool up = lane & 2;
-        const float send = up ? v[0] : v[1];
-        const float keep = up ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        const bool up = lane & 8;  // 5 (+1) -> 3
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float send = up ? w[i] : w[i + 3];
+            const float keep = up ? w[i + 3] : w[i];
+            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        x[3] = 0.0f;
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    {
+        const bool up = lane & 4;  // 3 (+1) -> 2
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float send = up ? x[i] : x[i + 2];
+            const float keep = up ? x[i + 2] : x[i];
+            y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+    }
+    const bool up = lane & 2;  // 2 -> 1
+    const float z = (up ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, up ? y[0] : y[1], 2);
+    return z + __shfl_xor_sync(0xffffffffu, z, 1);
+}
+
+// The value index warp_reduce_scatter10 leaves in `lane`: 5 b4 + 3 b3 +
+// 2 b2 + b1 (b_k = bit k of the lane) when that slot holds a value, else -1.
+__device__ __forceinline__ int scatter10_index(int lane) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
+    const int loc = 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+    return loc < (b3 ? 2 : 3) ? 5 * b4 + 3 * b3 + loc : -1;
 }
 
 // Warp sum by the integer warp reduction of Sec. 3.1: the largest exponent
@@ -360,7 +375,8 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                 power2(s, fx, fy, p0, p1);
                 blend2<PREC>(s, p0, p1, G0, G1, a0, a1, c0, c1);
                 float gr = 0.f, gg = 0.f, gb = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f,
-                      syy = 0.f, dO = 0.f, S = 0.f, n = 0.f;
+                      syy = 0.f, dO = 0.f, S = 0.f;
+                uint32_t n = 0;
                 const float dy = __fsub_rn(s.v, fy);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -388,14 +404,17 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                             sxy = fmaf(dy, qx, sxy);
                             syy = fmaf(dy, qy, syy);
                         }
-                        n += 1.0f;
+                        ++n;
                         accg[h] = fmaf(a, dd, accg[h]);
                         T[h] = Tk;
                     }
                 }
-                if (__any_sync(0xffffffffu, n != 0.0f)) {
+                if (__any_sync(0xffffffffu, n != 0u)) {
                     // -(A sx + B sy), -(B sx + C sy), -sxx/2, -sxy, -syy/2 with
-                    // A = -2a, B = -b, C = -2c
+                    // A = -2a, B = -b, C = -2c; then dL/do, dL/dcolour, S. The
+                    // row's M (slot 10) is the same sum as dL/do, C (11) the
+                    // integer count of contributing pixels.
+                    float v[10];
                     v[0] = 2.0f * s.a * sx + s.b * sy;
                     v[1] = s.b * sx + 2.0f * s.c * sy;
                     v[2] = -0.5f * sxx;
@@ -406,32 +425,32 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                     v[7] = gg;
                     v[8] = gb;
                     v[9] = S;
-                    v[10] = dO;
-                    v[11] = n;
+                    const uint32_t cnt = __reduce_add_sync(0xffffffffu, n);
                     float *row = gacc + 16 * (int64_t)s_id[k];
-                    const int vi = lane >> 1;
                     if constexpr (int_reduce(PREC)) {
+                        const int vi = lane >> 1;
                         float mine = 0.f;
 #pragma unroll
                         for (int i = 0; i < 10; ++i) {
                             const float t = warp_sum_int(v[i]);
                             if (vi == i || (i == 5 && vi == 10)) mine = t;  // M = the opacity sum
                         }
-                        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)v[11]);
                         if ((lane & 1) == 0) {
                             if (vi < 11)
                                 atomicAdd(row + vi, mine);
                             else if (vi == 11)
-                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11), c);
+                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11), cnt);
                         }
                     } else {
-                        const float red = warp_reduce_scatter16(v, lane);
+                        const float red = warp_reduce_scatter10(v, lane);
                         if ((lane & 1) == 0) {
-                            if (vi < 11)
+                            const int vi = scatter10_index(lane);
+                            if (vi >= 0) {
                                 atomicAdd(row + vi, red);
-                            else if (vi == 11)
-                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11),
-                                          (unsigned int)(red + 0.5f));
+                                if (vi == 5) atomicAdd(row + 10, red);
+                            } else if (lane == 12) {
+                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11), cnt);
+                            }
                         }
                     }
                 }

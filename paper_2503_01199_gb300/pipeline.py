@@ -74,6 +74,8 @@ class StepConfig:
     # Cluster-Cull-Compact (Sec. 3.2.2); off: every row is processed each
     # step (culled Gaussians get zero gradients, Adam touches every row)
     ccc: bool = True
+    # raster blend precision: B.LGS_FP32, LGS_MIXED_FP16 or LGS_MIXED_BF16
+    precision: int = 0
 
 
 class Trainer:
@@ -177,7 +179,7 @@ class Trainer:
         B.lgs_bin_sort(self.splats, self._dV(), self.n, cs, tw, th, self.vals, self.d_P,
                        self.ranges, self.ws_bin)
         B.lgs_raster_fwd(self.splats, self.vals, self.ranges, cs, tw, th, self.image, self.finalT,
-                         self.last)
+                         self.last, precision=self.cfg.precision)
         return cs
 
     def backward(self, cs: B.LgsCamera, target: torch.Tensor, accumulate=False):
@@ -185,7 +187,8 @@ class Trainer:
         tw, th = self.cfg.tile
         B.lgs_loss_l1(self.image, target, self.dLdI, self.loss)
         B.lgs_raster_bwd(self.splats, self.vals, self.ranges, cs, tw, th, self.finalT, self.last,
-                         self.dLdI, self.gacc, accumulate=accumulate)
+                         self.dLdI, self.gacc, accumulate=accumulate,
+                         precision=self.cfg.precision)
         B.lgs_opacity_variance(self.gacc, self._map(), self._dV(), self.n, self.metric)
         if self.track_moments:
             B.lgs_moments_accumulate(self.gacc, self._map(), self._dV(), self.n, self.S_acc,
