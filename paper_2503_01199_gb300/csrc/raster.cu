@@ -65,8 +65,22 @@ __device__ __forceinline__ uint32_t pack_pair(float x) {
     }
 }
 
+// Approximate square root for the quadrant test: x * rsqrt(x), 0 for
+// x <= 0, and finite (about 1.8e19) for an infinite x.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    x = fminf(x, 3.0e38f);
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 // Loads splat j into s and returns the 4-bit mask of the tile quadrants
-// (bit w: quadrant x0 + 8 (w & 1), y0 + 8 (w >> 1)) it may reach.
+// (bit w: quadrant x0 + 8 (w & 1), y0 + 8 (w >> 1)) it may reach. The mask
+// only saves work: a quadrant left out must have alpha < 1/255 at every
+// pixel, so the test may be loose but never tight. It is the row form of
+// the tile test (per quadrant row, the x interval [L, U] of the ellipse
+// q <= tau) in approximate arithmetic (reciprocals and square roots by the
+// special-function unit), with slack far above that arithmetic's error: the
+// y extent and the interval are widened by 2e-3 of the ellipse's extent plus
+// 1e-2 pixel. A conic that is not positive definite reaches every quadrant.
 template <int PREC>
 __device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_t j, float x0,
                                           float y0, SplatS &s) {
@@ -83,27 +97,29 @@ __device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_
     s.g = y.w;
     s.bl = z.x;
     s.oh = pack_pair<PREC>(y.y);
-    const float rA = __frcp_rn(x.z), rC = __frcp_rn(y.x);
-    const RowCull rc = row_cull(x.x, x.y, x.z, x.w, y.x, rA, rC, z.y);
+    const float A = x.z, B = x.w, C = y.x, tau = z.y;
+    if (!(tau >= 0.0f)) return 0u;
+    const float det = A * C - B * B;
+    if (!(det > 0.0f) || !(A > 0.0f) || !(C > 0.0f)) return 0xfu;
+    const float rdet = __fdividef(1.0f, det), rA = __fdividef(1.0f, A);
+    const float ex = sqrt_approx(tau * C * rdet), ey = sqrt_approx(tau * A * rdet);
+    const float dyU = -B * ex * __fdividef(1.0f, C);
+    const float sy = 2e-3f * ey + 1e-2f, sx = 2e-3f * ex + 1e-2f;
+    const float At = A * tau;
     uint32_t m = 0;
-    if (rc.degenerate) {
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const float xl = x0 + 8.0f * (w & 1), yl = y0 + 8.0f * (w >> 1);
-            if (box_reachable(x.x, x.y, x.z, x.w, y.x, rA, rC, z.y, xl, xl + 7.0f, yl, yl + 7.0f))
-                m |= 1u << w;
-        }
-    } else {
+    for (int qr = 0; qr < 2; ++qr) {
+        const float yl = y0 + 8.0f * qr;
+        const float ay = x.y - (yl + 7.0f), by = x.y - yl;
+        if (ay > ey + sy || by < -(ey + sy)) continue;
+        float d = fminf(fmaxf(dyU, ay), by);
+        const float U = (sqrt_approx(At - det * d * d) - B * d) * rA + sx;
+        d = fminf(fmaxf(-dyU, ay), by);
+        const float L = -(sqrt_approx(At - det * d * d) + B * d) * rA - sx;
 #pragma unroll
-        for (int qr = 0; qr < 2; ++qr) {
-            float L, U;
-            const float yl = y0 + 8.0f * qr;
-            if (!slab_interval(rc, yl, yl + 7.0f, L, U)) continue;
-#pragma unroll
-            for (int qc = 0; qc < 2; ++qc) {
-                const float xl = x0 + 8.0f * qc;
-                if (__fsub_rn(x.x, xl + 7.0f) <= U && __fsub_rn(x.x, xl) >= L) m |= 1u << (2 * qr + qc);
-            }
+        for (int qc = 0; qc < 2; ++qc) {
+            const float xl = x0 + 8.0f * qc;
+            if (x.x - (xl + 7.0f) <= U && x.x - xl >= L) m |= 1u << (2 * qr + qc);
         }
     }
     return m;
