@@ -145,11 +145,16 @@ FUSED_SOURCES = ("paper_2503_01199_gb300/csrc/preprocess.cu",
 
 
 def source_digest(files=FUSED_SOURCES) -> str:
+    """Digest of the code of `files` (comments and whitespace removed)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in files:
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(ROOT, name), encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(name.encode() + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -188,8 +188,10 @@ size_t radix_sort_workspace(int64_t n, int key_bytes);
 // (keys[0], vals[0]); keys[1] / vals[1] are the alternate buffers. Returns
 // the index (0 or 1) of the buffers holding the result in *out_buf.
 // `scratch` holds the digit histograms and the tiles' look-back status
-// (radix_hist_bytes(n_max)). Bounded look-back waits that give up are
-// counted; sort_wait_timeouts() reads and clears the count.
+// (radix_hist_bytes(n_max)); after the sort, u32 word 256 p + d of it is
+// the number of keys whose digit in pass p (bits 8p..8p+7) is d. Bounded
+// look-back waits that give up are counted; sort_wait_timeouts() reads and
+// clears the count.
 size_t radix_hist_bytes(int64_t n_max);
 lgs_status sort_wait_timeouts(uint32_t *count);
 // The same count for the binning's look-back over groups of splats.
