@@ -170,6 +170,33 @@ def test_bin_sort_bit_exact(orc, n, W, H, tile, cull):
     U.assert_same_tile_lists(vals, ranges, rv, rr)
 
 
+@pytest.mark.parametrize("cull", [0, 1])
+def test_bin_sort_large_and_degenerate_splats(orc, cull):
+    """Splats up to 600 px: groups of 32 splats with more tile rows than the
+    shared-memory spans hold and more super-tile items than the staged
+    output holds (the per-lane and direct-write paths of the item kernel);
+    conics whose det is 0 or negative after rounding (the per-tile box test);
+    thin ellipses (an axis ratio up to 1000)."""
+    W, H = 1297, 840
+    s = U.random_splat_dict(4000, 77, W, H, max_radius=600)
+    conic = s["conic"].astype(np.float64)
+    A, C = conic[:, 0], conic[:, 2]
+    conic[::7, 1] = np.sqrt(A[::7] * C[::7])            # det = 0 (rounds to 0 or below)
+    conic[3::11, 1] = 1.5 * np.sqrt(A[3::11] * C[3::11])  # det < 0
+    thin = np.arange(5, 4000, 13)
+    conic[thin, 0] *= 1e3                                # axis ratio up to ~1000
+    s["conic"] = conic.astype(np.float32)
+    s["radius"][::29] = 0
+    vals, ranges, P = U.gpu_bin(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H,
+                                (16, 16), conic=s["conic"], tau=s["tau"], cull=cull,
+                                cap=64_000_000)
+    rv, rr, rP = orc.bin_splats(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H,
+                                (16, 16), conic=s["conic"], tau=s["tau"], cull=bool(cull))
+    assert P == rP and P > 100_000
+    U.assert_same_tile_lists(vals, ranges, rv, rr)
+    assert B.lgs_get_wait_timeouts() == 0
+
+
 def test_bin_sort_empty_and_device_count(orc):
     s = U.random_splat_dict(5000, 3, 300, 200)
     s["radius"][:] = 0
