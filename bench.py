@@ -333,6 +333,10 @@ def run_gpu(args) -> dict | None:
     B.load()
     d = make_workload(rank, args.n_gaussians)
     sc, cam, tgt_np = d["scene"], d["camera"], d["target"]
+    morton = args.storage == "morton"
+    if not morton:  # rows in a random order, never re-sorted (profiling evidence only)
+        perm = np.random.default_rng(9).permutation(sc["mean"].shape[0])
+        sc = {k: (np.asarray(v)[perm] if k != "sh_degree" else v) for k, v in sc.items()}
     tr = PL.Trainer(sc, W_IMG, H_IMG, PL.StepConfig(tile=TILE, pair_capacity=128_000_000),
                     device=str(dev))
     del sc
@@ -374,7 +378,7 @@ def run_gpu(args) -> dict | None:
         mark(9)
 
     for w in range(args.warmup):
-        step(reorder=(w == 0))  # the timed steps run on Morton-sorted state
+        step(reorder=(w == 0 and morton))  # the timed steps run on Morton-sorted state
     torch.cuda.synchronize()
     overflow = B.lgs_get_overflow()
     if overflow:
@@ -718,6 +722,9 @@ def main():
                     help="length of the served-render request stream (0: skip)")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the Cluster-Cull-Compact / storage-order ablation")
+    ap.add_argument("--storage", default="morton", choices=["morton", "shuffled"],
+                    help="row order of the scene: Morton-sorted (the bench line) or shuffled "
+                         "and never re-sorted (profiling evidence for the re-sort)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -726,6 +733,9 @@ def main():
     out = run_gpu(args)
     if out is None:
         return
+    if args.storage != "morton":
+        out["config"]["workload"] = ("storage-order case (rows shuffled, never re-sorted): " +
+                                     out["config"]["workload"].replace(", Morton-sorted", ""))
     if args.n_gaussians:
         out["config"]["n_gaussians"] = args.n_gaussians
         out["config"]["workload"] = "profiling case: " + out["config"]["workload"].replace(

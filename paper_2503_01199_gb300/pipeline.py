@@ -237,6 +237,34 @@ class Trainer:
                             c.beta1, c.beta2, c.eps, self.step_count, self._map(), self._dV(),
                             self.n)
 
+    # -- checkpoint / resume -------------------------------------------------
+    def save(self, path) -> None:
+        """Write the scene state as raw arrays (numpy .npz): the parameter
+        planes and both Adam moments of the live rows (current storage order),
+        the SH degree and the step count, so that a resumed run continues the
+        same Adam schedule."""
+        n = self.n
+        np.savez(path, params=self.params[:, :n].cpu().numpy(), m=self.m[:, :n].cpu().numpy(),
+                 v=self.v[:, :n].cpu().numpy(), sh_degree=np.int64(self.sh_degree),
+                 step_count=np.int64(self.step_count))
+
+    def load(self, path) -> None:
+        """Read a checkpoint written by save() into this trainer (its
+        capacity must hold the saved rows; the camera size and buffers are
+        this trainer's own)."""
+        with np.load(path) as z:
+            if int(z["sh_degree"]) != self.sh_degree:
+                raise ValueError("checkpoint has another SH degree")
+            n = int(z["params"].shape[1])
+            if n > self.capacity:
+                raise ValueError("checkpoint has more rows than this trainer's capacity")
+            st = self.state[self.cur]
+            st.zero_()
+            for k, name in enumerate(("params", "m", "v")):
+                st[k, :, :n].copy_(torch.from_numpy(np.ascontiguousarray(z[name])).to(self.dev))
+            self.n = n
+            self.step_count = int(z["step_count"])
+
     def step(self, cam: dict | B.LgsCamera, target: torch.Tensor, reorder: bool = True,
              fused: bool = True):
         """One full training step a1..a10."""

@@ -302,3 +302,25 @@ def test_cull_does_not_change_the_image(orc):
     B.lgs_raster_fwd(tr.splats, tr.vals, tr.ranges, cs, 16, 16, tr.image, tr.finalT, tr.last)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(tr.image.cpu().numpy(), img_cull)
+
+
+def test_checkpoint_resume_continues_identically(tmp_path):
+    """save() after two steps, load() into a fresh trainer: the next step
+    gives the same parameters and moments as continuing (up to the order of
+    the backward's float atomic additions)."""
+    d = scenegen.surface_scene(20000, 3, 41, 160, 120)
+    sc, cam, tgt = d["scene"], d["camera"], U.t(d["target"])
+    a = PL.Trainer(sc, 160, 120)
+    a.step(cam, tgt, reorder=True)
+    a.step(cam, tgt, reorder=False)
+    path = tmp_path / "ckpt.npz"
+    a.save(path)
+    b = PL.Trainer(sc, 160, 120)
+    b.load(path)
+    assert b.n == a.n and b.step_count == a.step_count
+    a.step(cam, tgt, reorder=False)
+    b.step(cam, tgt, reorder=False)
+    torch.cuda.synchronize()
+    for x, y in ((a.params, b.params), (a.m, b.m), (a.v, b.v)):
+        np.testing.assert_allclose(y[:, :b.n].cpu().numpy(), x[:, :a.n].cpu().numpy(),
+                                   rtol=1e-4, atol=1e-9)
