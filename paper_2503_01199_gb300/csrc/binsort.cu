@@ -150,7 +150,7 @@ __device__ __forceinline__ SplatGeom splat_geom(const float *__restrict__ rec,
 // u - xh(tx) <= U only gets truer as tx grows and u - xl(tx) >= L only
 // falser (correctly rounded differences are monotone), so the kept tiles
 // form one interval, found from an estimate (rtw = 1 / tw) and a few exact
-// tests -- the same tests, operation for operation, as tile_in_row.
+// tests -- the same operations as the row form's per-tile condition.
 __device__ __forceinline__ bool right_ok(float u, int tx, int tw, float U) {
     const float xh = __fadd_rn((float)(tx * tw + tw), -0.5f);
     return __fsub_rn(u, xh) <= U;

@@ -126,7 +126,8 @@ __device__ __forceinline__ bool tile_reachable(float u, float v, float A, float 
 // lies outside the slab, at the slab edge nearest to it, where the ellipse's
 // quadratic in d_x gives U = (sqrt(A tau - det d_y^2) - B d_y) / A; L
 // likewise with the signs flipped. A tile of the row is reachable when its
-// offsets [u - xh, u - xl] meet [L, U]. Exact in real arithmetic, the same
+// offsets [u - xh, u - xl] meet [L, U] (u - xh <= U and u - xl >= L, the
+// differences correctly rounded). Exact in real arithmetic, the same
 // decision as the box minimum; evaluated with explicitly rounded single
 // precision operations, in this order, by every implementation.
 struct RowCull {
@@ -169,12 +170,6 @@ __device__ __forceinline__ bool row_interval(const RowCull &r, int ty, int th, f
     return slab_interval(r, yl, yh, L, U);
 }
 
-// Whether tile tx of a row with interval [L, U] is reachable.
-__device__ __forceinline__ bool tile_in_row(const RowCull &r, int tx, int tw, float L, float U) {
-    const float xl = __fadd_rn((float)(tx * tw), 0.5f), xh = __fadd_rn((float)(tx * tw + tw), -0.5f);
-    return __fsub_rn(r.u, xh) <= U && __fsub_rn(r.u, xl) >= L;
-}
-
 // ---------------------------------------------------------------------------
 // host-side building blocks implemented in sort.cu
 // ---------------------------------------------------------------------------
@@ -196,10 +191,7 @@ size_t radix_hist_bytes(int64_t n_max);
 lgs_status sort_wait_timeouts(uint32_t *count);
 // The same count for the binning's look-back over groups of splats.
 lgs_status bin_wait_timeouts(uint32_t *count);
-lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
-                          const int32_t *d_n32, int bits, void *scratch, int *out_buf,
-                          cudaStream_t s);
-// The same with 64-bit values.
+// 16-bit keys carry 64-bit values.
 lgs_status radix_sort_u16_v64(uint16_t *keys[2], uint64_t *vals[2], int64_t n_max,
                               const int64_t *d_n64, const int32_t *d_n32, int bits, void *scratch,
                               int *out_buf, cudaStream_t s);

@@ -385,13 +385,6 @@ size_t radix_sort_workspace(int64_t n, int key_bytes) {
     return 2 * al((size_t)n * key_bytes) + 2 * al((size_t)n * 4) + al(radix_hist_bytes(n));
 }
 
-lgs_status radix_sort_u16(uint16_t *keys[2], uint32_t *vals[2], int64_t n_max, const int64_t *d_n64,
-                          const int32_t *d_n32, int bits, void *scratch, int *out_buf,
-                          cudaStream_t s) {
-    if (bits > 16) return LGS_ERR_INVALID_ARG;
-    return radix_sort_impl<uint16_t, uint32_t>(keys, vals, n_max, d_n64, d_n32, bits, scratch,
-                                               out_buf, s);
-}
 lgs_status radix_sort_u16_v64(uint16_t *keys[2], uint64_t *vals[2], int64_t n_max,
                               const int64_t *d_n64, const int32_t *d_n32, int bits, void *scratch,
                               int *out_buf, cudaStream_t s) {
