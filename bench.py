@@ -138,10 +138,13 @@ def traffic_record() -> dict:
         return {}
 
 
-# sources the fused backward + Adam kernel is compiled from: its recorded
-# DRAM traffic stays valid while these are unchanged
+# sources each recorded kernel is compiled from: its recorded DRAM traffic
+# stays valid while these are unchanged (profiles/traffic.json carries the
+# digest and the list)
 FUSED_SOURCES = ("paper_2503_01199_gb300/csrc/preprocess.cu",
                  "paper_2503_01199_gb300/csrc/lgs_internal.cuh", "include/lgs.h")
+RASTER_SOURCES = ("paper_2503_01199_gb300/csrc/raster.cu",
+                  "paper_2503_01199_gb300/csrc/lgs_internal.cuh", "include/lgs.h")
 
 
 def source_digest(files=FUSED_SOURCES) -> str:
@@ -156,6 +159,22 @@ def source_digest(files=FUSED_SOURCES) -> str:
         text = re.sub(r"//[^\n]*", " ", text)
         h.update(name.encode() + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+def recorded_traffic(key: str, units: float | None = None) -> int | None:
+    """DRAM bytes of one launch of the recorded kernel `key`: bytes_per_unit
+    x units for a kernel whose traffic scales with its units, or the
+    bytes of a launch captured at the bench workload itself; None when the
+    kernel's sources changed since the capture or nothing was recorded."""
+    rec = traffic_record().get(key, {})
+    files = tuple(rec.get("source_files", FUSED_SOURCES))
+    if not rec or rec.get("source") != source_digest(files):
+        return None
+    if "bytes_per_unit" in rec and units is not None:
+        return round(rec["bytes_per_unit"] * units)
+    if "bytes_per_launch" in rec and units is None:
+        return int(rec["bytes_per_launch"])
+    return None
 
 
 def max_over_ranks(values, device) -> list:
@@ -385,6 +404,9 @@ def run_gpu(args) -> dict | None:
         raise RuntimeError(f"pair capacity too small: {overflow} pairs needed")
     V = int(tr.d_V.item())
     P = int(tr.d_P.item())
+    # fragments up to each pixel's last composited splat (the raster's unit of
+    # work): the sum of last_contrib over the image, the same every iteration
+    F = int(tr.last.sum(dtype=torch.int64).item())
     # ---- timed region: device throughput with per-stage events
     bus = None
     try:
@@ -468,30 +490,51 @@ def run_gpu(args) -> dict | None:
     ms_step = ms / args.steps
     value = job_rate(world, args.steps, ms)
     e2e_value = job_rate(world, args.steps, e2e_ms)
-    # ---- roofline of the dominant HBM-bound call: the fused preprocess
-    # backward + Adam (k_bwd_adam_rec), 1480 B per visible Gaussian at SH3:
-    # params, m, v read and written (6 x 59 x 4 B), the 9 gradients + S, M, C
-    # of its grad row (48 B), its map entry (4 B) and the 3 colours of its
-    # splat record (12 B)
+    # ---- rooflines. The dominant kernel of the iteration is the backward
+    # raster (k_raster_bwd, a7; a third of the launch list), bound by FP32
+    # arithmetic: about 30 FP32 operations per fragment up to `last` (the
+    # per-pixel gradient terms; an FMA counts as one operation) against the
+    # FP32 lanes' rate, 152 SMs x 128 lanes x 2.07 GHz = 40.3 T operations/s.
+    # The forward (a5): about 9 per fragment. The largest HBM-bound call is
+    # the fused preprocess backward + Adam (k_bwd_adam_rec), 1480 B per
+    # visible Gaussian at SH3: params, m, v read and written (6 x 59 x 4 B),
+    # the 9 gradients + S, M, C of its grad row (48 B), its map entry (4 B)
+    # and the 3 colours of its splat record (12 B).
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
+    fp32_peak = 152 * 128 * 2.07e9 / 1e12  # T operations/s
+    ops_bwd, ops_fwd = 30, 9
+    bwd_t = F * ops_bwd / (stage_ms["a7_raster_bwd"] * 1e-3) / 1e12
+    fwd_t = F * ops_fwd / (stage_ms["a5_raster_fwd"] * 1e-3) / 1e12
+    roofline = {"kernel": "lgs_raster_bwd (k_raster_bwd<0>)", "bound": "alu",
+                "achieved": round(bwd_t, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2,070 MHz, an FMA as one "
+                                "operation"),
+                "frac": round(bwd_t / fp32_peak, 4),
+                "traffic": (recorded_traffic("a7_raster_bwd")
+                            if not args.n_gaussians and morton else None),
+                "algorithmic_ops": int(F * ops_bwd), "fragments": F,
+                "ops_per_fragment": ops_bwd}
     npl = B.num_planes(SH_DEG)
     per_unit = {"a9a10_bwd_adam": 6 * npl * 4 + 48 + 4 + 12,
                 "a3_preprocess": npl * 4 + 4 + 48 + 4 + 4}  # params + map in; record, depth, radius out
     dom = "a9a10_bwd_adam"
     achieved = V * per_unit[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    tr_rec = traffic_record().get(dom, {})
-    traffic = (round(tr_rec["bytes_per_unit"] * V) if tr_rec.get("source") == source_digest()
-               and "bytes_per_unit" in tr_rec else None)
-    roofline = {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_rec<3>)",
-                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "peak_source": "measured" if hbm else "fallback",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "algorithmic_bytes": int(V * per_unit[dom]),
-                "bytes_per_visible_gaussian": per_unit[dom]}
+    traffic = recorded_traffic(dom, V)
     pre_gbs = V * per_unit["a3_preprocess"] / (stage_ms["a3_preprocess"] * 1e-3) / 1e9
-    other = {"a3_preprocess": {"bound": "hbm", "achieved": round(pre_gbs, 1),
+    other = {"a9a10_bwd_adam": {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_rec<3>)",
+                                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                                "unit": "GB/s",
+                                "peak_source": "measured" if hbm else "fallback",
+                                "frac": round(achieved / peak, 4), "traffic": traffic,
+                                "algorithmic_bytes": int(V * per_unit[dom]),
+                                "bytes_per_visible_gaussian": per_unit[dom]},
+             "a5_raster_fwd": {"kernel": "lgs_raster_fwd (k_raster_fwd<0>)", "bound": "alu",
+                               "achieved": round(fwd_t, 3), "peak": round(fp32_peak, 2),
+                               "unit": "TFLOP/s", "frac": round(fwd_t / fp32_peak, 4),
+                               "ops_per_fragment": ops_fwd},
+             "a3_preprocess": {"bound": "hbm", "achieved": round(pre_gbs, 1),
                                "frac": round(pre_gbs / peak, 4)}}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -501,6 +544,7 @@ def run_gpu(args) -> dict | None:
         "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "sh_degree": SH_DEG,
                    "resolution": f"{W_IMG}x{H_IMG}", "tile": f"{TILE[0]}x{TILE[1]}",
                    "parallelism": f"replicas x{world}", "visible_gaussians": V, "pairs": P,
+                   "fragments": F,
                    "l2": "inputs larger than L2 (2.1 GB resident state), no flush"},
         "roofline": roofline,
         "roofline_other": other,
