@@ -407,7 +407,7 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
  * g->data is updated in place. Same results as lgs_preprocess_bwd followed by
  * lgs_adam_step up to rounding. grad_acc is read only.
  * sp (may be NULL): the splat records lgs_preprocess wrote for this camera
- * from these parameters (rows j < V, read only). With them the colour clamp
+ * from these parameters (rows j < V read, capacity >= g->n). With them the colour clamp
  * is taken from the stored colours instead of recomputing the colours, so
  * the SH planes are read once; without them the colours are recomputed. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,

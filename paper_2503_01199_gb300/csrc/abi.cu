@@ -325,7 +325,7 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    int32_t step, lgs_stream stream) {
     if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||
         !aligned16(grad_acc) || !aligned16(m) || !aligned16(v) || training_only(g, cam) ||
-        (sp && (!sp->rec || !aligned16(sp->rec))))
+        (sp && bad_splats(sp, g->n)))
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
     return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, sp ? sp->rec : nullptr, grad_acc,
