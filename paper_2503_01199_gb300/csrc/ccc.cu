@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_cluster_cull(const float *__restri
          c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         const int64_t r0 = c * cs, r1 = min(r0 + cs, n);
+#pragma unroll 4
         for (int64_t r = r0 + lane; r < r1; r += 32) {
             const float e = 3.0f * fmaxf(expf(p[3 * stride + r]),
                                          fmaxf(expf(p[4 * stride + r]), expf(p[5 * stride + r])));
