@@ -1,7 +1,6 @@
 """Pins of the oracle's densification, opacity decay and moment sums
 (Sec. 3.3), independent of how the oracle computes them."""
 import numpy as np
-import pytest
 
 from paper_2503_01199_gb300 import scenegen
 

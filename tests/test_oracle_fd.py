@@ -8,7 +8,6 @@ changes any discrete decision (which fragments are included, where a pixel
 stops, a clamp, a tile rectangle, the sign of I - gt) is skipped and counted.
 """
 import numpy as np
-import pytest
 
 from paper_2503_01199_gb300 import scenegen
 
