@@ -4,7 +4,9 @@
 // captured CUDA graph behind kernels that produce the count.
 //
 // Radix sort, one 8-bit digit per pass, "onesweep" with decoupled look-back:
-//   histogram - one read of the keys counts the digits of every pass;
+//   histogram - one read of the keys counts the digits of every pass (and
+//               clears the first pass's tile status; each pass clears the
+//               next one's);
 //   per pass  - CTAs take 4096-item tiles in launch order from an atomic
 //               counter, rank each tile's items stably with a warp
 //               multisplit (peer masks from per-bit ballots), publish the
@@ -107,15 +109,23 @@ constexpr int kMaxPasses = 8;
 __device__ unsigned int g_sort_wait_timeouts;
 
 // Digit counts of every pass in one read of the keys (hist zeroed).
+// Also clears the tile status words and the tile counter of the first pass.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const K *__restrict__ keys,
                                                             int64_t n_max, const int64_t *d_n64,
                                                             const int32_t *d_n32, int passes,
-                                                            uint32_t *__restrict__ hist) {
+                                                            uint32_t *__restrict__ hist,
+                                                            uint32_t *__restrict__ status0,
+                                                            uint32_t *__restrict__ counter0) {
     __shared__ uint32_t s_h[kMaxPasses][kRadix];
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = read_count(n_max, d_n64, d_n32);
+    const int64_t words = (n + kTile - 1) / kTile * kRadix;
+    for (int64_t i = blockIdx.x * (int64_t)kSortThreads + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * kSortThreads)
+        status0[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter0 = 0u;
     for (int64_t i = blockIdx.x * (int64_t)kSortThreads + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * kSortThreads) {
         const K k = keys[i];
@@ -128,24 +138,12 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const K *__restrict
     }
 }
 
-// Clears the tile status words of the current count and the tile counter.
-__global__ void __launch_bounds__(256) k_onesweep_reset(uint32_t *__restrict__ status,
-                                                       uint32_t *__restrict__ counter,
-                                                       int64_t n_max, const int64_t *d_n64,
-                                                       const int32_t *d_n32) {
-    const int64_t n = read_count(n_max, d_n64, d_n32);
-    const int64_t words = (n + kTile - 1) / kTile * kRadix;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
-         i += (int64_t)gridDim.x * blockDim.x)
-        status[i] = 0u;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
-}
-
 template <typename K, typename V>
 __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const K *__restrict__ keys_in, const V *__restrict__ vals_in, K *__restrict__ keys_out,
     V *__restrict__ vals_out, const uint32_t *__restrict__ hist, uint32_t *status,
-    uint32_t *counter, int64_t n_max, const int64_t *d_n64, const int32_t *d_n32, int shift) {
+    uint32_t *counter, uint32_t *next_status, uint32_t *next_counter, int64_t n_max,
+    const int64_t *d_n64, const int32_t *d_n32, int shift) {
     __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
     __shared__ uint32_t s_gstart[kRadix];
     __shared__ uint32_t s_start[kRadix];
@@ -159,6 +157,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t n = read_count(n_max, d_n64, d_n32);
     const int64_t tiles = (n + kTile - 1) / kTile;
+    if (next_status) {
+        // the next pass's status words (its region was last used by the
+        // previous pass, which has finished)
+        for (int64_t i = blockIdx.x * (int64_t)kSortThreads + threadIdx.x; i < tiles * kRadix;
+             i += (int64_t)gridDim.x * kSortThreads)
+            next_status[i] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *next_counter = 0u;
+    }
     {
         // global start of each digit
         const uint64_t h = threadIdx.x < kRadix ? hist[threadIdx.x] : 0u;
@@ -275,9 +281,14 @@ lgs_status radix_sort_impl(K *keys[2], V *vals[2], int64_t n_max, const int64_t 
     if (n_max > (int64_t)kCountMask) return LGS_ERR_INVALID_ARG;
     const int passes = radix_passes(bits);
     if (passes > kMaxPasses) return LGS_ERR_INVALID_ARG;
-    uint32_t *hist = static_cast<uint32_t *>(scratch);             // [kMaxPasses][256]
-    uint32_t *counter = hist + kMaxPasses * kRadix;                 // 64 words
-    uint32_t *status = counter + 64;                                // [tiles][256]
+    // scratch: digit counts [kMaxPasses][256], two tile counters, and two
+    // status regions [tiles][256] used by alternate passes, so that each pass
+    // clears the region of the next one
+    const int64_t tmax = sort_tiles(n_max);
+    uint32_t *hist = static_cast<uint32_t *>(scratch);
+    uint32_t *counter[2] = {hist + kMaxPasses * kRadix, hist + kMaxPasses * kRadix + 32};
+    uint32_t *status[2] = {hist + kMaxPasses * kRadix + 64,
+                           hist + kMaxPasses * kRadix + 64 + tmax * kRadix};
     const size_t dyn = (sizeof(K) + sizeof(V)) * kTile;
     static bool attr_set[64] = {};
     int dev = 0;
@@ -290,21 +301,20 @@ lgs_status radix_sort_impl(K *keys[2], V *vals[2], int64_t n_max, const int64_t 
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, V>, kSortThreads, dyn);
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t tmax = sort_tiles(n_max);
     const unsigned grid = (unsigned)(tmax < cap ? tmax : cap);
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kRadix * passes, s);
     count_launch();
     k_digit_hist<K><<<grid_for(n_max, kSortThreads, 4), kSortThreads, 0, s>>>(
-        keys[0], n_max, d_n64, d_n32, passes, hist);
+        keys[0], n_max, d_n64, d_n32, passes, hist, status[0], counter[0]);
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
+        const int q = p & 1;
+        const bool more = p + 1 < passes;
         count_launch();
-        k_onesweep_reset<<<grid_for(tmax * kRadix, 256, 4), 256, 0, s>>>(status, counter, n_max,
-                                                                      d_n64, d_n32);
-        count_launch();
-        k_onesweep<K, V><<<grid, kSortThreads, dyn, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
-                                                      vals[cur ^ 1], hist + p * kRadix, status,
-                                                      counter, n_max, d_n64, d_n32, p * 8);
+        k_onesweep<K, V><<<grid, kSortThreads, dyn, s>>>(
+            keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], hist + p * kRadix, status[q],
+            counter[q], more ? status[q ^ 1] : nullptr, more ? counter[q ^ 1] : nullptr, n_max,
+            d_n64, d_n32, p * 8);
         cur ^= 1;
     }
     *out_buf = cur;
@@ -366,7 +376,7 @@ int radix_passes(int bits) { return bits <= 0 ? 1 : (bits + 7) / 8; }
 
 size_t radix_hist_bytes(int64_t n_max) {
     return sizeof(uint32_t) * ((size_t)kMaxPasses * kRadix + 64 +
-                               (size_t)sort_tiles(n_max > 0 ? n_max : 1) * kRadix);
+                               2 * (size_t)sort_tiles(n_max > 0 ? n_max : 1) * kRadix);
 }
 
 lgs_status sort_wait_timeouts(uint32_t *count) {
