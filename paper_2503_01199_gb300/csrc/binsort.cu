@@ -576,20 +576,31 @@ __global__ void __launch_bounds__(kThreads) k_chunk_counts(const uint64_t *__res
 }
 
 // Stage 3b: per super-tile and tile, exclusive offsets of the chunks (in
-// place) and the tile's total. One warp per super-tile, lane = tile.
+// place) and the tile's total. One CTA per super-tile, lane = tile: each
+// warp scans a contiguous range of the super-tile's chunks, then the warps'
+// totals are scanned and added.
 __global__ void __launch_bounds__(kThreads) k_chunk_offsets(uint32_t *__restrict__ ccount,
                                                            const uint32_t *__restrict__ cbase,
                                                            int ns, uint32_t *__restrict__ ttotal) {
-    const int lane = threadIdx.x & 31;
-    for (int s = (blockIdx.x * kThreads + threadIdx.x) >> 5; s < ns;
-         s += (gridDim.x * kThreads) >> 5) {
+    __shared__ uint32_t s_w[kWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int s = blockIdx.x; s < ns; s += gridDim.x) {
+        const uint32_t k0 = cbase[s], k1 = cbase[s + 1];
+        const uint32_t per = (k1 - k0 + kWarps - 1) / kWarps;
+        const uint32_t a = min(k0 + wid * per, k1), b = min(a + per, k1);
         uint32_t run = 0;
-        for (uint32_t k = cbase[s]; k < cbase[s + 1]; ++k) {
+        for (uint32_t k = a; k < b; ++k) run += ccount[(size_t)k * 32 + lane];
+        s_w[wid][lane] = run;
+        __syncthreads();
+        uint32_t base = 0;
+        for (int w = 0; w < wid; ++w) base += s_w[w][lane];
+        if (wid == kWarps - 1) ttotal[s * 32 + lane] = base + run;
+        for (uint32_t k = a; k < b; ++k) {
             const uint32_t c = ccount[(size_t)k * 32 + lane];
-            ccount[(size_t)k * 32 + lane] = run;
-            run += c;
+            ccount[(size_t)k * 32 + lane] = base;
+            base += c;
         }
-        ttotal[s * 32 + lane] = run;
+        __syncthreads();
     }
 }
 
@@ -755,8 +766,7 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
     count_launch();
     k_chunk_counts<<<gc, kThreads, 0, s>>>(svals, L.seg, L.cbase, G, L.ccount);
     count_launch();
-    k_chunk_offsets<<<(unsigned)ceil_div((int64_t)G.ns * 32, kThreads), kThreads, 0, s>>>(
-        L.ccount, L.cbase, G.ns, L.ttotal);
+    k_chunk_offsets<<<(unsigned)G.ns, kThreads, 0, s>>>(L.ccount, L.cbase, G.ns, L.ttotal);
     count_launch();
     k_tile_starts<<<1, 1024, 0, s>>>(L.ttotal, G, L.tstart, ranges, d_P, cap);
     count_launch();
