@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_super_items(
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t V = load_count(d_V, maxV);
     const int64_t groups = (V + 31) / 32;
-    const float rtw = div_by_size(1.0f, G.tw);
+    const float rtw = div_by_size(1.0f, G.tw), rth = div_by_size(1.0f, G.th);
     if (groups == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_psup = 0;
     for (;;) {
         uint32_t gid = 0;
@@ -347,7 +347,21 @@ __global__ void __launch_bounds__(kThreads) k_super_items(
         const RowCull rcl = row_cull(sg.u, sg.v, sg.A, sg.B, sg.C, sg.rA, sg.rC, sg.tau);
         const bool per_tile = cull && rcl.degenerate;
         const bool row_test = cull && !rcl.degenerate;
-        const uint32_t n = (uint32_t)(rc.w - rc.y);
+        // with the row test, only the rows [ry0, ry1) that pass its first
+        // condition (v - yh <= e_y and v - yl >= -e_y, monotone in the row)
+        // can keep a tile; the others are empty without computing them
+        int ry0 = rc.y, ry1 = rc.w;
+        if (row_test && rc.w > rc.y) {
+            if (!(rcl.tau >= 0.0f)) {
+                ry1 = ry0;
+            } else {
+                int a, b;
+                row_span(rcl.v, rc.y, rc.w, G.th, rth, -rcl.ey, rcl.ey, a, b);
+                ry0 = a;
+                ry1 = max(a, b + 1);
+            }
+        }
+        const uint32_t n = (uint32_t)(ry1 - ry0);
         uint32_t incl = n;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -361,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_super_items(
             s_par[wid][lane][0] = make_float4(rcl.u, rcl.v, rcl.A, rcl.B);
             s_par[wid][lane][1] = make_float4(rcl.tau, rcl.det, rcl.ey, rcl.dyU);
             s_par[wid][lane][2] = make_float4(__int_as_float(rc.x), __int_as_float(rc.z),
-                                              __int_as_float(rc.y),
+                                              __int_as_float(ry0),
                                               __int_as_float((int)(first << 1) | (row_test ? 1 : 0)));
             __syncwarp();
             for (uint32_t c = 0; c < T; c += 32) {
@@ -383,8 +397,10 @@ __global__ void __launch_bounds__(kThreads) k_super_items(
             __syncwarp();
         }
         auto span_of = [&](int k) -> uint32_t {
-            return staged ? s_span[wid][first + k]
-                          : row_span_of(rcl, rc.x, rc.z, rc.y + k, row_test, G, rtw);
+            const int ty = rc.y + k;
+            if (ty < ry0 || ty >= ry1) return kEmptySpan;
+            return staged ? s_span[wid][first + (ty - ry0)]
+                          : row_span_of(rcl, rc.x, rc.z, ty, row_test, G, rtw);
         };
         uint32_t items;
         if (per_tile) {
