@@ -41,3 +41,73 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert L.lgs_adam_step(None, None, None, None, 0, 0, None, 0.9, 0.999, 1e-15, 1, None, None, 0,
                            None) == B.LGS_ERR_INVALID_ARG
     assert L.lgs_bin_sort_workspace_size(1000, 100000, 64) > 100000 * 6
+
+
+def _aligned(nbytes: int):
+    import numpy as np
+    raw = np.zeros(nbytes + 64, np.uint8)
+    off = (-raw.ctypes.data) % 64
+    return raw, raw.ctypes.data + off
+
+
+def test_capacity_and_grid_rules_are_checked_on_the_host():
+    """The argument rules the header states for the binning and the fused
+    optimizer are checked before anything is enqueued: every case below is
+    refused without touching a device."""
+    from paper_2503_01199_gb300 import binding as B
+    L = B.load()
+    keep = []
+
+    def buf(nbytes):
+        raw, p = _aligned(nbytes)
+        keep.append(raw)
+        return ctypes.c_void_p(p)
+
+    cam = B.LgsCamera()
+    cam.R[:] = [1, 0, 0, 0, 1, 0, 0, 0, 1]
+    cam.fx = cam.fy = 500.0
+    cam.cx, cam.cy, cam.width, cam.height, cam.znear = 64.0, 64.0, 128, 128, 0.01
+    n = 256
+    sp = B.LgsSplats(buf(48 * n).value, buf(4 * n).value, buf(4 * n).value, n)
+    ws = buf(1 << 20)
+    vals, npairs, ranges, nvis = buf(4 * 4096), buf(8), buf(8 * 65536), buf(4)
+
+    def bin_sort(sp_, max_splats, cam_, tw, th, cull, cap, wsb=1 << 20):
+        return L.lgs_bin_sort(ctypes.byref(sp_), nvis, max_splats, ctypes.byref(cam_), tw, th, cull,
+                              vals, cap, npairs, ranges, ws, wsb, None)
+
+    bad = B.LGS_ERR_INVALID_ARG
+    assert bin_sort(sp, n + 1, cam, 16, 16, 1, 4096) == bad          # capacity < max_splats
+    assert bin_sort(sp, n, cam, 16, 16, 2, 4096) == bad              # tile_cull not 0 / 1
+    assert bin_sort(sp, n, cam, 0, 16, 1, 4096) == bad               # empty tile
+    assert bin_sort(sp, n, cam, 16, 16, 1, 1 << 32) == bad           # pairs beyond u32 indices
+    assert bin_sort(sp, n, cam, 16, 16, 1, 4096, wsb=16) == bad      # workspace too small
+    big = B.LgsCamera.from_buffer_copy(cam)
+    big.width, big.height = 257 * 16, 256 * 16                       # 65,792 tiles > 65,536
+    assert bin_sort(sp, n, big, 16, 16, 1, 4096) == bad
+    unaligned = B.LgsSplats(sp.rec + 4, sp.depth, sp.radius, n)
+    assert bin_sort(unaligned, n, cam, 16, 16, 1, 4096) == bad
+
+    deg = 3
+    stride = 256
+    planes = buf(4 * B.num_planes(deg) * stride)
+    g = B.LgsGaussians(planes.value, n, stride, deg, B.LGS_SH_F32, None)
+    m, v = buf(4 * B.num_planes(deg) * stride), buf(4 * B.num_planes(deg) * stride)
+    gacc, lr, rowmap = buf(64 * n), buf(4 * B.num_planes(deg)), buf(4 * n)
+
+    def fused(g_, sp_, gacc_=gacc, step=1, cam_=cam):
+        return L.lgs_preprocess_bwd_adam(ctypes.byref(g_), m, v, rowmap, nvis, ctypes.byref(cam_),
+                                         None if sp_ is None else ctypes.byref(sp_), gacc_, lr,
+                                         0.9, 0.999, 1e-15, step, None)
+
+    small = B.LgsSplats(sp.rec, sp.depth, sp.radius, n - 1)
+    assert fused(g, small) == bad                                    # records fewer than rows
+    assert fused(g, sp, step=0) == bad                               # Adam step counts from 1
+    assert fused(g, sp, gacc_=ctypes.c_void_p(gacc.value + 4)) == bad
+    posed = B.LgsCamera.from_buffer_copy(cam)
+    posed.d_pose = buf(48).value                                     # training takes a host pose
+    assert fused(g, sp, cam_=posed) == bad
+    g16 = B.LgsGaussians(planes.value, n, stride, deg, B.LGS_SH_BF16, buf(2 * 48 * stride).value)
+    assert fused(g16, sp) == bad                                     # FP32 colour planes only
+    skew = B.LgsGaussians(planes.value, n, stride + 2, deg, B.LGS_SH_F32, None)
+    assert fused(skew, sp) == bad                                    # stride a multiple of 4
