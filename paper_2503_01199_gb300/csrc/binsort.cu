@@ -69,6 +69,7 @@ struct Layout {
     uint64_t *svals[2];   // tile mask << 32 | splat
     uint32_t *seg;        // [ns][2]
     uint32_t *cbase;      // [ns + 1]
+    uint4 *ctab;          // [max_chunks]: super-tile, first item, end item
     uint32_t *ccount;     // [max_chunks][32]
     uint32_t *tstart;     // [ns * 32]
     uint32_t *ttotal;     // [ns * 32]
@@ -95,6 +96,7 @@ Layout layout(void *base, int64_t maxV, int64_t cap, int ns) {
     for (int k = 0; k < 2; ++k) L.svals[k] = reinterpret_cast<uint64_t *>(take((size_t)cap * 8));
     L.seg = reinterpret_cast<uint32_t *>(take((size_t)ns * 8));
     L.cbase = reinterpret_cast<uint32_t *>(take((size_t)(ns + 1) * 4));
+    L.ctab = reinterpret_cast<uint4 *>(take((size_t)max_chunks(ns, cap) * 16));
     L.ccount = reinterpret_cast<uint32_t *>(take((size_t)max_chunks(ns, cap) * 32 * 4));
     L.tstart = reinterpret_cast<uint32_t *>(take((size_t)ns * 32 * 4));
     L.ttotal = reinterpret_cast<uint32_t *>(take((size_t)ns * 32 * 4));
@@ -130,13 +132,16 @@ __device__ __forceinline__ SplatGeom splat_geom(const float *__restrict__ rec,
     SplatGeom s;
     s.rc = make_int4(0, 0, 0, 0);
     s.u = s.v = s.A = s.B = s.C = s.rA = s.rC = s.tau = 0.f;
+    // the record is read whatever the radius (row g < V is in bounds), so
+    // both loads are in flight together; a culled splat's is unused
     const int rad = radius[g];
+    const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)g);
+    const float4 a = p[0];
+    const float c = p[1].x, tau = p[2].y;
     if (rad > 0) {
-        const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)g);
-        const float4 a = p[0];
         s.u = a.x; s.v = a.y; s.A = a.z; s.B = a.w;
-        s.C = p[1].x;
-        s.tau = p[2].y;
+        s.C = c;
+        s.tau = tau;
         s.rA = __frcp_rn(s.A);
         s.rC = __frcp_rn(s.C);
         s.rc = tile_rect(a.x, a.y, (float)rad, G.tw, G.th, G.gx, G.gy);
@@ -499,12 +504,14 @@ __global__ void __launch_bounds__(kThreads) k_seg_ranges(const uint16_t *__restr
     }
 }
 
-// Chunks of every super-tile: cbase[s] = first chunk of s, cbase[ns] = total.
+// Chunks of every super-tile: cbase[s] = first chunk of s, cbase[ns] = total,
+// and ctab[k] = (super-tile, first item, end item) of every chunk k.
 // With `hist` (the item count of every super-tile, when one sort pass
 // covers all super-tile ids) the item ranges seg are derived here as well.
 __global__ void __launch_bounds__(1024) k_chunk_plan(const uint32_t *__restrict__ hist,
                                                     uint32_t *__restrict__ seg, int ns,
-                                                    uint32_t *__restrict__ cbase) {
+                                                    uint32_t *__restrict__ cbase,
+                                                    uint4 *__restrict__ ctab) {
     __shared__ uint64_t s_sum[1024];
     const int per = (ns + 1023) / 1024;
     const int s0 = threadIdx.x * per;
@@ -527,24 +534,19 @@ __global__ void __launch_bounds__(1024) k_chunk_plan(const uint32_t *__restrict_
     for (int s = s0; s < min(ns, s0 + per); ++s) {
         const uint32_t c = items(s);
         cbase[s] = (uint32_t)run;
+        const uint32_t a = hist ? (uint32_t)(run >> 32) : seg[2 * s];
         if (hist) {
-            seg[2 * s] = (uint32_t)(run >> 32);
-            seg[2 * s + 1] = (uint32_t)(run >> 32) + c;
+            seg[2 * s] = a;
+            seg[2 * s + 1] = a + c;
+        }
+        for (uint32_t q = 0; q * kChunk < c; ++q) {
+            const uint32_t i0 = q * kChunk;
+            ctab[(uint32_t)run + q] =
+                make_uint4((uint32_t)s, a + i0, a + i0 + min(c - i0, (uint32_t)kChunk), 0u);
         }
         run += ((uint64_t)c << 32) | ((c + kChunk - 1) / kChunk);
     }
     if (threadIdx.x == 1023) cbase[ns] = (uint32_t)s_sum[1023];
-}
-
-// super-tile of chunk k: the last s with cbase[s] <= k
-__device__ __forceinline__ int chunk_super(const uint32_t *__restrict__ cbase, int ns, uint32_t k) {
-    int lo = 0, hi = ns - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cbase[mid] <= k) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
 }
 
 // 32 x 32 bit transpose across a warp: bit i of lane l's result is bit l of
@@ -565,16 +567,15 @@ __device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
 // Stage 3a: per chunk of 1024 items of one super-tile, the number of items
 // listed in each of its 32 tiles. One CTA per chunk.
 __global__ void __launch_bounds__(kThreads) k_chunk_counts(const uint64_t *__restrict__ svals,
-                                                          const uint32_t *__restrict__ seg,
+                                                          const uint4 *__restrict__ ctab,
                                                           const uint32_t *__restrict__ cbase, Geo G,
                                                           uint32_t *__restrict__ ccount) {
     __shared__ uint32_t s_cnt[kWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t K = cbase[G.ns];
     for (uint32_t k = blockIdx.x; k < K; k += gridDim.x) {
-        const int s = chunk_super(cbase, G.ns, k);
-        const uint32_t a = seg[2 * s] + (k - cbase[s]) * kChunk;
-        const uint32_t b = min(a + (uint32_t)kChunk, seg[2 * s + 1]);
+        const uint4 ck = ctab[k];
+        const uint32_t a = ck.y, b = ck.z;
         uint32_t my = 0;  // this warp's count for tile `lane`
         for (uint32_t i = a + threadIdx.x; i - threadIdx.x < b; i += kThreads) {
             const uint32_t mask = i < b ? (uint32_t)(svals[i] >> 32) : 0u;
@@ -659,13 +660,18 @@ __global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t *__restrict
 }
 
 // Stage 3d: write every item's pairs. Each warp takes 128 consecutive items
-// of the chunk (4 rounds of 32); a tile's position for an item = chunk
-// offset + items of earlier warps + items of earlier rounds + earlier lanes
-// of the round listed in that tile (one ballot per tile). Pairs are written
-// tile by tile, so the lanes listed in one tile store to consecutive
-// addresses.
+// of the chunk (4 rounds of 32); the bit transpose of a round's masks gives
+// lane t the round's items listed in tile t, so lane t writes tile t's
+// entries itself, in item order, at: the chunk's start in the tile + items
+// of earlier warps + items of earlier rounds. The entries go to a
+// tile-major buffer in shared memory, copied out tile by tile with
+// consecutive lanes storing consecutive addresses; a chunk with more pairs
+// than the buffer holds is written directly.
+constexpr int kStage = 6144;  // pairs of one chunk staged in shared memory (twice the
+                              // typical chunk, small enough for 8 CTAs per SM)
+
 __global__ void __launch_bounds__(kThreads) k_chunk_emit(const uint64_t *__restrict__ svals,
-                                                        const uint32_t *__restrict__ seg,
+                                                        const uint4 *__restrict__ ctab,
                                                         const uint32_t *__restrict__ cbase,
                                                         const uint32_t *__restrict__ ccount,
                                                         const uint32_t *__restrict__ tstart, Geo G,
@@ -673,50 +679,78 @@ __global__ void __launch_bounds__(kThreads) k_chunk_emit(const uint64_t *__restr
     constexpr int kRounds = kChunk / kThreads;
     constexpr int kPerWarp = kChunk / kWarps;
     __shared__ uint32_t s_w[kWarps][32];
+    __shared__ uint32_t s_start[32], s_off[33];
+    __shared__ uint32_t s_pairs[kStage];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t cap32 = (uint32_t)cap;  // cap < 2^32
     const uint32_t K = cbase[G.ns];
     for (uint32_t k = blockIdx.x; k < K; k += gridDim.x) {
-        const int s = chunk_super(cbase, G.ns, k);
-        const uint32_t a = seg[2 * s] + (k - cbase[s]) * kChunk;
-        const uint32_t b = min(a + (uint32_t)kChunk, seg[2 * s + 1]);
+        const uint4 ck = ctab[k];
+        const int s = (int)ck.x;
+        const uint32_t a = ck.y, b = ck.z;
         const uint32_t w0 = a + wid * kPerWarp;
-        uint32_t g[kRounds], mk[kRounds], tc[kRounds];
+        // the chunk's start in every tile, loaded while the items arrive
+        uint32_t start = 0;
+        if (threadIdx.x < 32) start = tstart[s * 32 + lane] + ccount[(size_t)k * 32 + lane];
+        uint32_t g[kRounds], tw[kRounds];  // tw: the round's items listed in tile `lane`
         uint32_t cnt = 0;
 #pragma unroll
         for (int j = 0; j < kRounds; ++j) {
             const uint32_t i = w0 + j * 32 + lane;
             const uint64_t v = i < b ? svals[i] : 0ull;
             g[j] = (uint32_t)v;
-            mk[j] = (uint32_t)(v >> 32);
-            tc[j] = __popc(warp_transpose(mk[j], lane));  // round's items in tile `lane`
-            cnt += tc[j];
+            tw[j] = warp_transpose((uint32_t)(v >> 32), lane);
+            cnt += __popc(tw[j]);
         }
         s_w[wid][lane] = cnt;
         __syncthreads();
         if (threadIdx.x < 32) {
-            uint32_t run = tstart[s * 32 + lane] + ccount[(size_t)k * 32 + lane];
+            // per tile: earlier warps' items, the chunk's total, and the
+            // tile's place in the staging buffer
+            uint32_t run = 0;
             for (int w = 0; w < kWarps; ++w) {
                 const uint32_t c = s_w[w][lane];
                 s_w[w][lane] = run;
                 run += c;
             }
+            uint32_t incl = run;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            s_start[lane] = start;
+            s_off[lane] = incl - run;
+            if (lane == 31) s_off[32] = incl;
         }
         __syncthreads();
-        uint32_t run = s_w[wid][lane];  // next position in tile `lane`
+        const bool staged = s_off[32] <= (uint32_t)kStage;
+        // next entry of tile `lane`: in the buffer, or its position in vals
+        uint64_t pos = (uint64_t)s_w[wid][lane] + (staged ? s_off[lane] : s_start[lane]);
 #pragma unroll
         for (int j = 0; j < kRounds; ++j) {
-            if (__any_sync(0xffffffffu, mk[j] != 0u)) {
-#pragma unroll
-                for (int l = 0; l < 32; ++l) {
-                    const bool has = (mk[j] >> l) & 1u;
-                    const uint32_t bl = __ballot_sync(0xffffffffu, has);
-                    const uint32_t at = __shfl_sync(0xffffffffu, run, l) + __popc(bl & lt);
-                    if (has && at < cap32) vals[at] = g[j];
+            const int n = __reduce_max_sync(0xffffffffu, (unsigned)__popc(tw[j]));
+            uint32_t t = tw[j];
+            for (int r = 0; r < n; ++r) {
+                const int i = t ? __ffs(t) - 1 : 0;
+                const uint32_t gi = __shfl_sync(0xffffffffu, g[j], i);
+                if (t) {
+                    if (staged)
+                        s_pairs[pos] = gi;
+                    else if (pos < (uint64_t)cap)
+                        vals[pos] = gi;
+                    ++pos;
+                    t &= t - 1u;
                 }
             }
-            run += tc[j];
+        }
+        __syncthreads();
+        if (staged) {
+            for (int l = wid; l < 32; l += kWarps) {
+                const uint32_t o = s_off[l], n = s_off[l + 1] - o;
+                const uint64_t base = s_start[l];
+                for (uint32_t e = lane; e < n; e += 32)
+                    if (base + e < (uint64_t)cap) vals[base + e] = s_pairs[o + e];
+            }
         }
         __syncthreads();
     }
@@ -775,18 +809,18 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
                                                                   L.seg);
     }
     count_launch();
-    k_chunk_plan<<<1, 1024, 0, s>>>(hist, L.seg, G.ns, L.cbase);
+    k_chunk_plan<<<1, 1024, 0, s>>>(hist, L.seg, G.ns, L.cbase, L.ctab);
     // 3. masks, chunk counts, offsets, tile starts, pairs
     const int64_t mc = max_chunks(G.ns, cap), cap_blocks = (int64_t)num_sms() * 16;
     const unsigned gc = (unsigned)(mc < cap_blocks ? mc : cap_blocks);
     count_launch();
-    k_chunk_counts<<<gc, kThreads, 0, s>>>(svals, L.seg, L.cbase, G, L.ccount);
+    k_chunk_counts<<<gc, kThreads, 0, s>>>(svals, L.ctab, L.cbase, G, L.ccount);
     count_launch();
     k_chunk_offsets<<<(unsigned)G.ns, kThreads, 0, s>>>(L.ccount, L.cbase, G.ns, L.ttotal);
     count_launch();
     k_tile_starts<<<1, 1024, 0, s>>>(L.ttotal, G, L.tstart, ranges, d_P, cap);
     count_launch();
-    k_chunk_emit<<<gc, kThreads, 0, s>>>(svals, L.seg, L.cbase, L.ccount, L.tstart, G, cap,
+    k_chunk_emit<<<gc, kThreads, 0, s>>>(svals, L.ctab, L.cbase, L.ccount, L.tstart, G, cap,
                                         vals);
     return check_launch();
 }
