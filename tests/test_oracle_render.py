@@ -1,7 +1,7 @@
 """Pins of the oracle's preprocess, binning and forward rendering.
 
 Closed forms (Eq. 1-2 for one and two splats, the EWA covariance of an
-isotropic / axis-aligned / off-axis Gaussian), invariants of Eq. 1 (zero
+isotropic / axis-aligned / off-axis / rotated Gaussian), invariants of Eq. 1 (zero
 opacity gives the background, weights plus final transmittance sum to one,
 alpha never exceeds 0.99, T never drops below 1e-4) and a brute-force
 per-tile enumeration of the binning.
@@ -278,3 +278,46 @@ def test_tile_culling_decision_is_the_box_minimum(orc):
         dx, dy = u[i] - X, v[i] - Y
         dense = (A[i] * dx * dx + 2 * B[i] * dx * dy + C[i] * dy * dy).min()
         assert qmin[i] <= dense + 1e-9 * (1 + dense)
+
+
+def test_rotated_splat_off_diagonal_conic_and_image(orc):
+    """The off-diagonal term, which the axis-aligned pins leave at zero: a
+    splat on the axis turned by 30 degrees about the view direction. On the
+    axis the EWA Jacobian is (f/z) I, so the screen covariance is
+    R2 diag(sx^2, sy^2) R2^T (f/z)^2 + 0.3 I; the conic (a, b, c) is its
+    inverse, the radius that of the unrotated splat (same eigenvalues), and
+    the image follows G = exp(-0.5 (a dx^2 + 2 b dx dy + c dy^2)) as the
+    scanline formulation of App. A writes it."""
+    W = H = 64
+    f, z, sx, sy, th = 64.0, 3.0, 0.12, 0.04, np.pi / 6
+    cam = scenegen.pinhole_camera(W, H, f, bg=(0.1, 0.2, 0.3))
+    q = [np.cos(th / 2), 0.0, 0.0, np.sin(th / 2)]
+    sc = _one([0.0, 0.0, z], np.log([sx, sy, 0.2]), quat=q, logit=1.3)
+    r = orc.render_scene(sc, cam, (16, 16))
+    sp = r["splats"]
+    R2 = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    S2 = (f / z) ** 2 * R2 @ np.diag([sx ** 2, sy ** 2]) @ R2.T + 0.3 * np.eye(2)
+    det = S2[0, 0] * S2[1, 1] - S2[0, 1] ** 2
+    a, b, c = S2[1, 1] / det, -S2[0, 1] / det, S2[0, 0] / det
+    assert abs(b) > 0.1 * max(a, c)
+    np.testing.assert_allclose(sp["conic"][0], [a, b, c], rtol=1e-12, atol=1e-15)
+    lam = max((f * sx / z) ** 2, (f * sy / z) ** 2) + 0.3
+    assert sp["radius"][0] == int(np.ceil(3 * np.sqrt(lam)))
+    o = _sigmoid(1.3)
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    dx, dy = px - W / 2, py - H / 2
+    rad = sp["radius"][0]
+    t0, t1 = int(np.floor((W / 2 - rad) / 16)), int(np.floor((W / 2 + rad) / 16)) + 1
+    inrect = (px // 16 >= t0) & (px // 16 < t1) & (py // 16 >= t0) & (py // 16 < t1)
+    rgb = np.array([0.8, 0.5, 0.2])
+    bg = np.array([0.1, 0.2, 0.3])
+
+    def image(bb):
+        G = np.exp(-0.5 * (a * dx ** 2 + 2 * bb * dx * dy + c * dy ** 2))
+        al = np.minimum(0.99, o * G)
+        al = np.where((al >= 1 / 255) & inrect, al, 0.0)
+        return rgb[:, None, None] * al + (1 - al) * bg[:, None, None]
+
+    np.testing.assert_allclose(r["image"], image(b), atol=1e-13)
+    # the pin tells the orientation apart: the mirrored ellipse is far off
+    assert np.abs(r["image"] - image(-b)).max() > 0.1
