@@ -3,7 +3,8 @@
 The oracle has two derivations (associated-Legendre recurrence in spherical
 angles, and Cartesian polynomials); they are checked against each other,
 against orthonormality on the sphere, against textbook closed forms, and the
-Cartesian gradient against finite differences.
+Cartesian gradient against finite differences; the preprocess colour against
+the closed form at a known view direction.
 """
 import numpy as np
 import pytest
@@ -72,3 +73,40 @@ def test_cartesian_gradient_matches_fd(orc):
 def test_lower_degrees_are_prefixes(orc, deg):
     d = _dirs(1, 3)[0]
     np.testing.assert_array_equal(orc.sh_spherical(deg, d), orc.sh_spherical(3, d)[: (deg + 1) ** 2])
+
+
+def test_colour_follows_the_view_direction(orc):
+    """The colour of Sec. 3's primitives is the SH expansion at the unit
+    direction from the camera centre c = -R^T t to the mean, plus 0.5,
+    clamped at 0. A camera turned about y and moved off the origin sees a
+    degree-1 splat on its optical axis, where that direction is R's third
+    row; the expected colour is written with the textbook degree-0/1
+    functions. The opposite direction, or a centre taken as t, fails."""
+    from paper_2503_01199_gb300 import scenegen
+    ph = 0.7
+    R = np.array([[np.cos(ph), 0.0, -np.sin(ph)], [0.0, 1.0, 0.0], [np.sin(ph), 0.0, np.cos(ph)]])
+    centre = np.array([0.4, -0.3, -2.0])
+    t = -R @ centre
+    cam = scenegen.pinhole_camera(64, 64, 64.0, R=R, t=t)
+    R32 = np.asarray(cam["R"], np.float64)
+    c32 = -R32.T @ np.asarray(cam["t"], np.float64)   # the camera as stored (float32)
+    mean = c32 + R32.T @ np.array([0.0, 0.0, 3.0])
+    sh = np.array([[[0.3, 0.1, -0.2], [0.5, -0.4, 0.2], [0.6, 0.3, -0.9], [-0.8, 0.2, 0.4]]])
+    scene = {"mean": mean[None], "log_scale": np.full((1, 3), np.log(0.05)),
+             "quat": np.array([[1.0, 0, 0, 0]]), "logit": np.zeros(1), "sh": sh, "sh_degree": 1}
+    sp = orc.preprocess(scene, cam)
+    assert sp["radius"][0] > 0
+    np.testing.assert_allclose(sp["uv"][0], [32.0, 32.0], atol=1e-9)
+
+    def colour(d):
+        x, y, z = d / np.linalg.norm(d)
+        s = np.sqrt(3 / (4 * np.pi))
+        Y = np.array([0.5 / np.sqrt(np.pi), -s * y, s * z, -s * x])
+        return np.maximum(0.0, 0.5 + Y @ sh[0])
+
+    d = R32[2]
+    want = colour(d)
+    assert want.min() == 0.0 < want.max()            # one channel clamped
+    np.testing.assert_allclose(sp["rgb"][0], want, rtol=1e-12, atol=1e-14)
+    assert np.abs(colour(-d) - want).max() > 0.05
+    assert np.abs(colour(mean - np.asarray(cam["t"], np.float64)) - want).max() > 0.05
