@@ -321,3 +321,30 @@ def test_rotated_splat_off_diagonal_conic_and_image(orc):
     np.testing.assert_allclose(r["image"], image(b), atol=1e-13)
     # the pin tells the orientation apart: the mirrored ellipse is far off
     assert np.abs(r["image"] - image(-b)).max() > 0.1
+
+
+def test_covariance_in_a_turned_camera(orc):
+    """Sec. 3's world covariance R(q) S S^T R(q)^T, q normalised first, seen by
+    a camera whose rotation is the inverse of R(q): in camera coordinates the
+    Gaussian is axis-aligned again, so on the optical axis its conic is the
+    axis-aligned closed form. Taking the camera rotation transposed, or the
+    quaternion conjugated, turns it by twice the angle instead; scaling q by
+    3.7 changes nothing."""
+    W, H, f, z = 96, 96, 80.0, 3.0
+    sx, sy, sz = 0.09, 0.03, 0.2
+    ph = 0.6
+    Rc = np.array([[np.cos(ph), 0.0, -np.sin(ph)], [0.0, 1.0, 0.0], [np.sin(ph), 0.0, np.cos(ph)]])
+    centre = np.array([0.2, 0.1, -1.5])
+    cam = scenegen.pinhole_camera(W, H, f, R=Rc, t=-Rc @ centre)
+    R32 = np.asarray(cam["R"], np.float64)
+    mean = -R32.T @ np.asarray(cam["t"], np.float64) + R32.T @ np.array([0.0, 0.0, z])
+    a = (f * sx / z) ** 2 + 0.3
+    c = (f * sy / z) ** 2 + 0.3
+    q = np.array([np.cos(ph / 2), 0.0, np.sin(ph / 2), 0.0])  # R(q) = Rc^T: a turn about y
+    for scale in (1.0, 3.7):
+        sp = orc.preprocess(_one(mean, np.log([sx, sy, sz]), quat=scale * q), cam)
+        np.testing.assert_allclose(sp["uv"][0], [W / 2, H / 2], atol=1e-5)
+        np.testing.assert_allclose(sp["conic"][0], [1 / a, 0.0, 1 / c], rtol=2e-6, atol=2e-7)
+    # the Gaussian turned the other way is not axis-aligned in this camera
+    sp = orc.preprocess(_one(mean, np.log([sx, sy, sz]), quat=q * [1, -1, -1, -1]), cam)
+    assert abs(sp["conic"][0][0] - 1 / a) > 0.05 / a
