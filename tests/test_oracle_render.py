@@ -348,3 +348,25 @@ def test_covariance_in_a_turned_camera(orc):
     # the Gaussian turned the other way is not axis-aligned in this camera
     sp = orc.preprocess(_one(mean, np.log([sx, sy, sz]), quat=q * [1, -1, -1, -1]), cam)
     assert abs(sp["conic"][0][0] - 1 / a) > 0.05 / a
+
+
+def test_jacobian_clamp_beyond_the_field_of_view(orc):
+    """The EWA Jacobian is taken at the centre with x/z clamped to
+    +-1.3 W / (2 fx) (the 3DGS rule the paper's projection inherits), while
+    the splat's screen position uses the unclamped centre. A splat at
+    x/z = 1 with the limit at 0.832 (principal point moved to x = 0 so that
+    it stays on screen): the conic's a takes the clamped x, u the true one."""
+    W, H, f = 128, 96, 100.0
+    cam = scenegen.pinhole_camera(W, H, f)
+    cam["cx"] = 0.0
+    z, x = 4.0, 4.0
+    sx, sy, sz = 0.02, 0.03, 0.3
+    sp = orc.preprocess(_one([x, 0.0, z], np.log([sx, sy, sz])), cam)
+    lim = 1.3 * W / (2 * f)
+    assert x / z > lim and sp["radius"][0] > 0
+    a = (f * sx / z) ** 2 + (f * lim / z) ** 2 * sz ** 2 + 0.3
+    c = (f * sy / z) ** 2 + 0.3
+    np.testing.assert_allclose(sp["conic"][0], [1 / a, 0.0, 1 / c], rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(sp["uv"][0], [f * x / z, H / 2], rtol=1e-14)
+    unclamped = (f * sx / z) ** 2 + (f * x / z ** 2) ** 2 * sz ** 2 + 0.3
+    assert abs(1 / unclamped - sp["conic"][0][0]) > 0.1 / a
