@@ -370,3 +370,23 @@ def test_jacobian_clamp_beyond_the_field_of_view(orc):
     np.testing.assert_allclose(sp["uv"][0], [f * x / z, H / 2], rtol=1e-14)
     unclamped = (f * sx / z) ** 2 + (f * x / z ** 2) ** 2 * sz ** 2 + 0.3
     assert abs(1 / unclamped - sp["conic"][0][0]) > 0.1 / a
+
+
+def test_radius_is_three_sigma_of_the_larger_eigenvalue(orc):
+    """r = ceil(3 sqrt(lambda_max)), lambda_max = m + sqrt(max(0.1, m^2 - det))
+    with m the mean of the 2D covariance's diagonal (the 3DGS rule the
+    projection inherits). Axis-aligned, the eigenvalues are the diagonal
+    itself; isotropic, the 0.1 floor lifts lambda_max by sqrt(0.1), which
+    at a variance of 3.9 px^2 makes the radius 7 instead of 6."""
+    W, H, f, z = 64, 64, 64.0, 3.0
+    cam = scenegen.pinhole_camera(W, H, f)
+    s_iso = np.sqrt(3.6) * z / f                           # (f s / z)^2 = 3.6, +0.3 = 3.9
+    sp = orc.preprocess(_one([0.0, 0.0, z], [np.log(s_iso)] * 3), cam)
+    np.testing.assert_allclose(1 / sp["conic"][0][0], 3.9, rtol=1e-12)
+    assert int(np.ceil(3 * np.sqrt(3.9))) == 6
+    assert sp["radius"][0] == int(np.ceil(3 * np.sqrt(3.9 + np.sqrt(0.1)))) == 7
+    # axis-aligned, variances 9.3 and 1.3: the larger one, exactly
+    sx, sy = 3.0 * z / f, 1.0 * z / f
+    sp = orc.preprocess(_one([0.0, 0.0, z], np.log([sx, sy, 0.1])), cam)
+    np.testing.assert_allclose(sp["conic"][0], [1 / 9.3, 0.0, 1 / 1.3], rtol=1e-12, atol=1e-16)
+    assert sp["radius"][0] == int(np.ceil(3 * np.sqrt(9.3))) == 10
