@@ -20,7 +20,12 @@ double-precision code are reported rather than hidden:
     default); bit1: two included splats whose depths differ by less than a
     relative 2e-6 (their order may flip);
   * render-backward ``sflags`` bit0: a fragment in a flagged pixel; bit1: a
-    fragment with o*G within the alpha margin of the 0.99 clamp.
+    fragment with o*G within the alpha margin of the 0.99 clamp;
+  * tile culling (``tile_reachable``, ``tile_near_pairs``): (splat, tile)
+    pairs whose box minimum of the exponent's quadratic form lies within
+    rounding of tau. tau is widened beyond alpha = 1/255, so such a pair
+    holds no fragment that passes the alpha test, and listing it or not
+    changes no pixel, only list positions.
 Parity tests compare exactly where no flag is set and count the flagged.
 
 Every function here is pinned by the CPU tests in ``tests/test_oracle_*.py``
@@ -105,6 +110,8 @@ def lib():
             "or_adam": (None, [i64, i32, P, P, P, P, P, f64, f64, f64, i32, P, i64]),
             "or_densify": (i64, [i64, i32, i64, P, P, P, P, i64, f64, P, P]),
             "or_tile_reachable": (None, [i64, P, P, P, P, P, P, i32, i32, P]),
+            "or_tile_near_pairs": (i64, [i64, P, P, P, P, P, i32, i32, i32, i32, i64, P]),
+            "or_set_tau_margin": (None, [f64]),
             "or_opacity_decay": (None, [i64, P]),
             "or_moments_accumulate": (None, [i64, P, P, P, P, P, P, P]),
         }
@@ -117,6 +124,7 @@ def lib():
 
 
 MARGINS_END_TO_END = (2e-4, 2e-4, 2e-3, 1e-5, 5e-7)
+TAU_MARGIN = 4e-6   # the tile decisions' near-tau flag (or_set_tau_margin)
 MARGINS_SHARED_SPLATS = (2e-5, 2e-4, 2e-3, 1e-5, 0.0)
 
 
@@ -377,15 +385,34 @@ def densify(planes, m, v, metric, K: int, split_scale: float, normals) -> dict:
     return {"planes": planes, "m": m, "v": v, "n": int(n_new), "selected": sel[:n_new - n]}
 
 
-def tile_reachable(u, v, conic, tau, tx, ty, tile=(16, 16)) -> np.ndarray:
-    """The single-precision tile-culling decision for each (splat, tile) query."""
+def tile_reachable(u, v, conic, tau, tx, ty, tile=(16, 16)):
+    """The tile-culling decision for each (splat, tile) query: (listed,
+    near), near marking a box minimum within rounding of tau."""
     u, v, tau = _c(u, np.float32), _c(v, np.float32), _c(tau, np.float32)
     conic = _c(conic, np.float32)
     tx, ty = _c(tx, np.int32), _c(ty, np.int32)
     out = np.zeros(u.size, np.uint8)
     lib().or_tile_reachable(u.size, _p(u), _p(v), _p(conic), _p(tau), _p(tx), _p(ty), tile[0],
                             tile[1], _p(out))
-    return out.astype(bool)
+    return (out & 1).astype(bool), (out & 2).astype(bool)
+
+
+def tile_near_pairs(u, v, radius, conic, tau, width: int, height: int, tile=(16, 16)) -> np.ndarray:
+    """(tile << 32) | splat of every rectangle pair whose tile-culling
+    decision is within rounding of tau (listed or not), uint64."""
+    u, v, tau = _c(u, np.float32), _c(v, np.float32), _c(tau, np.float32)
+    radius, conic = _c(radius, np.int32), _c(conic, np.float32)
+    args = (u.size, _p(u), _p(v), _p(radius), _p(conic), _p(tau), width, height, tile[0], tile[1])
+    k = lib().or_tile_near_pairs(*args, 0, None)
+    keys = np.zeros(max(k, 1), np.uint64)
+    k2 = lib().or_tile_near_pairs(*args, k, _p(keys))
+    assert k2 == k
+    return keys[:k]
+
+
+def set_tau_margin(rel: float) -> None:
+    """Relative input perturbation behind the tile decisions' near-tau flag."""
+    lib().or_set_tau_margin(float(rel))
 
 
 def opacity_decay(logit) -> np.ndarray:

@@ -344,67 +344,73 @@ static void tile_rect_f32(float u, float v, float r, int tw, int th, int gx, int
 /* Tile-level culling (App. A.1: tiles where a splat has decayed to nothing
  * are not listed). Tile (tx, ty) can receive a contribution when the minimum
  * of q(d) = A dx^2 + 2 B dx dy + C dy^2 over the box of its pixel centres
- * (d = splat centre - pixel centre) is <= tau. The minimum is 0 when the box
- * holds the centre, else it lies on an edge at the clamped 1D minimiser.
- * Single precision, in the kernel's operation order: the decision selects
- * list entries, which must match bit for bit. */
-static float quad_form_f32(float A, float B, float C, float dx, float dy) {
-    float t1 = (A * dx) * dx;
-    float t2 = ((B * dx) * dy) * 2.0f;
-    float t3 = (C * dy) * dy;
-    return (t1 + t2) + t3;
+ * (d = splat centre - pixel centre) is at most tau [reading: App. A.1, tile
+ * culling]. This is that definition in double precision on the splat's
+ * single-precision values, with no reformulation:
+ *   - a positive-definite form whose box holds d = 0 has minimum 0;
+ *   - otherwise the minimum lies on the box's boundary, and on each edge q is
+ *     a quadratic in one variable, minimised at an end point or, when its
+ *     leading coefficient is positive, at the stationary point clamped to
+ *     the edge.
+ * The minimiser is returned in (mx, my) for the rounding flag below. */
+static double qform(double A, double B, double C, double dx, double dy) {
+    return A * dx * dx + 2.0 * B * dx * dy + C * dy * dy;
 }
 
-static int tile_box_f32(float u, float v, float A, float B, float C, float tau, int tx,
-                              int ty, int tw, int th) {
-    float xl = (float)(tx * tw) + 0.5f, xh = (float)(tx * tw + tw) + -0.5f;
-    float yl = (float)(ty * th) + 0.5f, yh = (float)(ty * th + th) + -0.5f;
-    float ax = u - xh, bx = u - xl, ay = v - yh, by = v - yl;
-    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return 1;
-    /* edge minimiser -B dx / C as (B dx) * (1/C), reciprocals rounded once */
-    float rA = 1.0f / A, rC = 1.0f / C;
-    float d, q;
-    d = fminf(fmaxf(-((B * ax) * rC), ay), by);
-    q = quad_form_f32(A, B, C, ax, d);
-    d = fminf(fmaxf(-((B * bx) * rC), ay), by);
-    q = fminf(q, quad_form_f32(A, B, C, bx, d));
-    d = fminf(fmaxf(-((B * ay) * rA), ax), bx);
-    q = fminf(q, quad_form_f32(A, B, C, d, ay));
-    d = fminf(fmaxf(-((B * by) * rA), ax), bx);
-    q = fminf(q, quad_form_f32(A, B, C, d, by));
-    return q <= tau;
+static void edge_try(double A, double B, double C, double dx, double dy, double *best,
+                     double *mx, double *my) {
+    double q = qform(A, B, C, dx, dy);
+    if (q < *best) { *best = q; *mx = dx; *my = dy; }
 }
 
-/* Whether the minimum of q(d) = d^T [[A, B], [B, C]] d over the tile's box of
- * pixel centres is at most tau (App. A.1's tile culling), decided row-wise:
- * within the tile row's slab of offsets d_y = v - y in [ay, by], the ellipse
- * q <= tau covers one interval [L, U] of d_x = u - x, whose ends are the
- * ellipse's extreme d_x (at d_y = -/+ B e_x / C, e_x = sqrt(tau C / det)) or,
- * when those lie outside the slab, the roots of the ellipse's quadratic in
- * d_x at the nearest slab edge; the tile is reachable when [u - xh, u - xl]
- * meets [L, U]. Exact in real arithmetic (the same predicate as the box
- * minimum); taken in single precision in this operation order because the
- * listing is an integer decision [reading: App. A.1, tile culling]. A conic
- * whose det rounds to <= 0 falls back to the box's edge minima. */
-static int tile_reachable_f32(float u, float v, float A, float B, float C, float tau, int tx,
-                              int ty, int tw, int th) {
-    float det = A * C - B * B;
-    if (!(det > 0.0f)) return tile_box_f32(u, v, A, B, C, tau, tx, ty, tw, th);
-    if (!(tau >= 0.0f)) return 0;
-    float ex = sqrtf((tau * C) / det), ey = sqrtf((tau * A) / det);
-    float dyU = -((B * ex) / C);
-    float yl = (float)(ty * th) + 0.5f, yh = (float)(ty * th + th) + -0.5f;
-    float ay = v - yh, by = v - yl;
-    if (ay > ey || by < -ey) return 0;
-    float At = A * tau;
-    float d = fminf(fmaxf(dyU, ay), by);
-    float D = fmaxf(At - det * (d * d), 0.0f);
-    float U = (sqrtf(D) - B * d) / A;
-    d = fminf(fmaxf(-dyU, ay), by);
-    D = fmaxf(At - det * (d * d), 0.0f);
-    float L = -(sqrtf(D) + B * d) / A;
-    float xl = (float)(tx * tw) + 0.5f, xh = (float)(tx * tw + tw) + -0.5f;
-    return (u - xh) <= U && (u - xl) >= L;
+static double box_min_q(double A, double B, double C, double ax, double bx, double ay,
+                        double by, double *mx, double *my) {
+    *mx = 0.0; *my = 0.0;
+    if (A > 0.0 && A * C - B * B > 0.0 && ax <= 0.0 && bx >= 0.0 && ay <= 0.0 && by >= 0.0)
+        return 0.0;
+    double best = INFINITY;
+    double ex[2] = {ax, bx}, ey[2] = {ay, by};
+    for (int k = 0; k < 2; ++k) {
+        /* vertical edge d_x = ex[k], d_y in [ay, by] */
+        edge_try(A, B, C, ex[k], ay, &best, mx, my);
+        edge_try(A, B, C, ex[k], by, &best, mx, my);
+        if (C > 0.0) edge_try(A, B, C, ex[k], fmin(fmax(-B * ex[k] / C, ay), by), &best, mx, my);
+        /* horizontal edge d_y = ey[k], d_x in [ax, bx] */
+        if (A > 0.0) edge_try(A, B, C, fmin(fmax(-B * ey[k] / A, ax), bx), ey[k], &best, mx, my);
+    }
+    return best;
+}
+
+/* Relative size of the perturbation of a splat's single-precision values
+ * (centre, conic, tau, pixel coordinates) under which a tile decision taken
+ * in single precision is still expected to agree with this one; pairs whose
+ * decision could flip under it are flagged (bit0 of the pair flags). */
+static double OR_MARGIN_TAU = 4e-6;
+
+void or_set_tau_margin(double rel) { OR_MARGIN_TAU = rel; }
+
+/* Decision and flag for splat (u, v, conic, tau) and tile (tx, ty):
+ * returns 1 when listed; *near = 1 when the first-order change of the box
+ * minimum and of tau under relative perturbations OR_MARGIN_TAU of every
+ * input reaches |qmin - tau|. */
+static int tile_listed(float uf, float vf, float Af, float Bf, float Cf, float tauf, int tx,
+                       int ty, int tw, int th, int *near) {
+    double u = uf, v = vf, A = Af, B = Bf, C = Cf, tau = tauf;
+    double xl = tx * tw + 0.5, xh = tx * tw + tw - 0.5;
+    double yl = ty * th + 0.5, yh = ty * th + th - 0.5;
+    double mx, my;
+    double q = box_min_q(A, B, C, u - xh, u - xl, v - yh, v - yl, &mx, &my);
+    int in = q <= tau;
+    if (near) {
+        /* the offsets u - x, v - y are what a single-precision evaluation
+         * rounds, so their perturbation is relative to the box's offsets */
+        double gx = 2.0 * (A * mx + B * my), gy = 2.0 * (B * mx + C * my);
+        double sens = fabs(gx) * (fabs(u - xl) + fabs(u - xh)) +
+                      fabs(gy) * (fabs(v - yl) + fabs(v - yh)) + fabs(A) * mx * mx +
+                      2.0 * fabs(B * mx * my) + fabs(C) * my * my + fabs(tau) + 1.0;
+        *near = isfinite(tau) && fabs(q - tau) <= OR_MARGIN_TAU * sens;
+    }
+    return in;
 }
 
 static int frac_near_int(double x, double margin) {
@@ -601,8 +607,8 @@ int64_t or_cluster_cull(int64_t n, int cluster, const double *mean, const double
 static int listed(const float *u, const float *v, const float *conic, const float *tau, int cull,
                   int64_t i, int x, int y, int tw, int th) {
     if (!cull) return 1;
-    return tile_reachable_f32(u[i], v[i], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], tau[i],
-                              x, y, tw, th);
+    return tile_listed(u[i], v[i], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], tau[i], x, y,
+                       tw, th, NULL);
 }
 
 int64_t or_bin(int64_t n, const float *u, const float *v, const int32_t *radius,
@@ -1123,11 +1129,42 @@ void or_moments_accumulate(int64_t nvis, const uint32_t *rows, const double *S, 
     }
 }
 
-/* The tile-culling decision for a list of (splat, tile) queries (testing). */
+/* The tile-culling decision for a list of (splat, tile) queries (testing):
+ * bit0 listed, bit1 within rounding of tau (see tile_listed). */
 void or_tile_reachable(int64_t n, const float *u, const float *v, const float *conic,
                        const float *tau, const int32_t *tx, const int32_t *ty, int tw, int th,
                        uint8_t *out) {
-    for (int64_t i = 0; i < n; ++i)
-        out[i] = (uint8_t)tile_reachable_f32(u[i], v[i], conic[3 * i], conic[3 * i + 1],
-                                             conic[3 * i + 2], tau[i], tx[i], ty[i], tw, th);
+    for (int64_t i = 0; i < n; ++i) {
+        int near = 0;
+        int in = tile_listed(u[i], v[i], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], tau[i],
+                             tx[i], ty[i], tw, th, &near);
+        out[i] = (uint8_t)(in | (near << 1));
+    }
+}
+
+/* Every (tile, splat) pair of the splats' tile rectangles whose tile-culling
+ * decision is within rounding of tau, listed or not, as (tile << 32) | splat
+ * in increasing splat order; writes at most cap keys and returns the count.
+ * A single-precision binning may take either decision on these pairs; every
+ * other pair it must decide as or_bin does. */
+int64_t or_tile_near_pairs(int64_t n, const float *u, const float *v, const int32_t *radius,
+                           const float *conic, const float *tau, int W, int H, int tw, int th,
+                           int64_t cap, uint64_t *keys) {
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (radius[i] <= 0) continue;
+        int rc[4];
+        tile_rect_f32(u[i], v[i], (float)radius[i], tw, th, gx, gy, rc);
+        for (int y = rc[1]; y < rc[3]; ++y)
+            for (int x = rc[0]; x < rc[2]; ++x) {
+                int near = 0;
+                tile_listed(u[i], v[i], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], tau[i], x,
+                            y, tw, th, &near);
+                if (!near) continue;
+                if (k < cap) keys[k] = ((uint64_t)(uint32_t)(y * gx + x) << 32) | (uint64_t)i;
+                ++k;
+            }
+    }
+    return k;
 }

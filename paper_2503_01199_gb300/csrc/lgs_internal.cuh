@@ -87,8 +87,9 @@ __device__ __forceinline__ float quad_form(float A, float B, float C, float dx, 
 // contribution from a splat: the minimum of the conic's quadratic form
 // q(d) = d^T [[A, B], [B, C]] d over the box (d = splat centre - pixel
 // centre) is at most tau, where tau bounds q at alpha = 1/255
-// (alpha = o exp(-q / 2)). The minimum is 0 if the box holds the centre,
-// else it lies on an edge at the clamped one-dimensional minimiser
+// (alpha = o exp(-q / 2)). The minimum is at most 0 if the box holds the
+// centre (0 for a definite form, so a negative tau lists nothing), else it
+// lies on an edge at the clamped one-dimensional minimiser
 // (-B dx / C on an edge of constant dx; rA = 1/A and rC = 1/C, correctly
 // rounded). Single precision, explicit rounding.
 __device__ __forceinline__ bool box_reachable(float u, float v, float A, float B, float C,
@@ -96,7 +97,7 @@ __device__ __forceinline__ bool box_reachable(float u, float v, float A, float B
                                               float yl, float yh) {
     const float ax = __fsub_rn(u, xh), bx = __fsub_rn(u, xl);
     const float ay = __fsub_rn(v, yh), by = __fsub_rn(v, yl);
-    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return true;
+    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f && tau >= 0.0f) return true;
     float d, q;
     d = fminf(fmaxf(-__fmul_rn(__fmul_rn(B, ax), rC), ay), by);
     q = quad_form(A, B, C, ax, d);
@@ -129,7 +130,9 @@ __device__ __forceinline__ bool tile_reachable(float u, float v, float A, float 
 // offsets [u - xh, u - xl] meet [L, U] (u - xh <= U and u - xl >= L, the
 // differences correctly rounded). Exact in real arithmetic, the same
 // decision as the box minimum; evaluated with explicitly rounded single
-// precision operations, in this order, by every implementation.
+// precision operations (no contraction), so every binning kernel takes the
+// same decision. It agrees with the exact minimum wherever that is not
+// within a few roundings of tau.
 struct RowCull {
     float u, v, A, B, C, rA, rC, tau, det, ey, dyU;
     bool degenerate;  // det <= 0 after rounding: the box test decides

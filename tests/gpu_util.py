@@ -156,13 +156,97 @@ def random_splat_dict(n, seed, W, H, max_radius=40):
             "rgb": s["rgb"], "depth": s["depth"], "radius": s["radius"], "tau": tau_of(s["opacity"])}
 
 
-def assert_same_tile_lists(vals_a, ranges_a, vals_b, ranges_b):
+def assert_same_tile_lists(vals_a, ranges_a, vals_b, ranges_b, near=None, max_near_diff=None):
     """Every tile's list is the same sequence (the tiles' groups may be laid
-    out in different orders in the two vals arrays)."""
+    out in different orders in the two vals arrays). `near` (uint64 keys
+    (tile << 32) | splat from the oracle's tile_near_pairs) names the pairs
+    whose tile-culling decision lies within rounding of tau: either side may
+    list those, so they are removed from both lists before the comparison,
+    and only they may make the lists' lengths differ. Returns the keys of
+    the near pairs listed by one side only."""
     ra, rb = np.asarray(ranges_a, np.int64), np.asarray(ranges_b, np.int64)
     assert ra.shape == rb.shape
-    np.testing.assert_array_equal(ra[:, 1] - ra[:, 0], rb[:, 1] - rb[:, 0])
     va, vb = np.asarray(vals_a), np.asarray(vals_b)
-    for t in np.flatnonzero(ra[:, 1] > ra[:, 0]):
-        if not np.array_equal(va[ra[t, 0]:ra[t, 1]], vb[rb[t, 0]:rb[t, 1]]):
-            raise AssertionError(f"tile {t}: lists differ")
+    near_by_tile = {}
+    if near is not None and len(near):
+        keys = np.asarray(near, np.uint64)
+        tiles, splats = (keys >> np.uint64(32)).astype(np.int64), (keys & np.uint64(0xffffffff)).astype(np.int64)
+        for t_, j in zip(tiles.tolist(), splats.tolist()):
+            near_by_tile.setdefault(t_, set()).add(j)
+    diff = []
+    la, lb = ra[:, 1] - ra[:, 0], rb[:, 1] - rb[:, 0]
+    for t_ in np.flatnonzero((la > 0) | (lb > 0)):
+        a, b = va[ra[t_, 0]:ra[t_, 1]], vb[rb[t_, 0]:rb[t_, 1]]
+        if np.array_equal(a, b):
+            continue
+        nb = near_by_tile.get(int(t_))
+        if nb is None:
+            raise AssertionError(f"tile {t_}: lists differ")
+        fa = np.array([j for j in a.tolist() if j not in nb], np.int64)
+        fb = np.array([j for j in b.tolist() if j not in nb], np.int64)
+        if not np.array_equal(fa, fb):
+            raise AssertionError(f"tile {t_}: lists differ outside the near-tau pairs")
+        diff += [(int(t_) << 32) | j for j in sorted(set(a.tolist()) ^ set(b.tolist()))]
+    if max_near_diff is not None:
+        assert len(diff) <= max_near_diff, len(diff)
+    return np.array(diff, np.uint64)
+
+
+def assert_near_pairs_hold_no_fragment(near, sp, W, H, tile=(16, 16)):
+    """The given (tile << 32) | splat pairs hold no fragment that passes the
+    alpha >= 1/255 test, so listing them or not changes no pixel (tau is
+    widened by 1e-3 (1 + |tau|) beyond that threshold, far more than the
+    rounding of a single-precision decision). Brute force over every pixel
+    centre of each pair's tile, in double precision."""
+    gx = -(-W // tile[0])
+    keys = np.asarray(near, np.uint64)
+    for key in keys.tolist():
+        t_, j = key >> 32, key & 0xffffffff
+        tx, ty = t_ % gx, t_ // gx
+        px, py = np.meshgrid(tx * tile[0] + np.arange(tile[0]) + 0.5, ty * tile[1] + np.arange(tile[1]) + 0.5)
+        A, B_, C = (float(c) for c in sp["conic"][j])
+        dx, dy = float(sp["uv"][j, 0]) - px, float(sp["uv"][j, 1]) - py
+        a = float(sp["opacity"][j]) * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B_ * dx * dy)
+        assert (a < 1.0 / 255.0).all(), (t_, j, a.max())
+
+
+def last_ids(last, vals, ranges, W, tile=(16, 16)):
+    """Each pixel's last composited splat as a splat index (-1 for none):
+    `last` is a position in the pixel's tile list, so two binnings that
+    differ only in near-tau pairs (which hold no fragment) give different
+    positions for the same splat."""
+    last = np.asarray(last, np.int64)
+    H = last.shape[0]
+    gx = -(-W // tile[0])
+    ys, xs = np.mgrid[0:H, 0:last.shape[1]]
+    t_ = (ys // tile[1]) * gx + xs // tile[0]
+    start = np.asarray(ranges, np.int64)[t_, 0]
+    v = np.asarray(vals, np.int64)
+    out = np.full(last.shape, -1, np.int64)
+    m = last > 0
+    out[m] = v[start[m] + last[m] - 1]
+    return out
+
+
+def check_bins(orc, vals, ranges, P, sp, W, H, tile=(16, 16), cull=True, max_near_frac=1e-3):
+    """Compares a GPU binning of float32 splats `sp` (uv, conic, depth,
+    radius, tau, opacity) with the oracle's: bit-exact tile lists apart from
+    near-tau pairs (at most max_near_frac of P differ), which must hold no
+    contributing fragment when the conic is positive definite. Returns the
+    oracle's (vals, ranges, P)."""
+    u, v = sp["uv"][:, 0], sp["uv"][:, 1]
+    rv, rr, rP = orc.bin_splats(u, v, sp["radius"], sp["depth"], W, H, tile,
+                                conic=sp["conic"] if cull else None, tau=sp["tau"] if cull else None,
+                                cull=bool(cull))
+    near = orc.tile_near_pairs(u, v, sp["radius"], sp["conic"], sp["tau"], W, H, tile) if cull else None
+    diff = assert_same_tile_lists(vals, ranges, rv, rr, near=near,
+                                  max_near_diff=int(max_near_frac * max(rP, 1)))
+    assert abs(P - rP) <= len(diff), (P, rP, len(diff))
+    if len(diff) and "opacity" in sp:
+        # the pairs the two binnings decide differently hold no contributing
+        # fragment (definite conics only: the others have no such meaning)
+        c = np.asarray(sp["conic"], np.float64)
+        pd = (c[:, 0] > 0) & (c[:, 0] * c[:, 2] - c[:, 1] ** 2 > 0)
+        j = (diff & np.uint64(0xffffffff)).astype(np.int64)
+        assert_near_pairs_hold_no_fragment(diff[pd[j]], sp, W, H, tile)
+    return rv, rr, rP

@@ -151,6 +151,37 @@ def test_cluster_cull_compact_matches_oracle(orc, gen):
         np.testing.assert_array_equal(rowmap.cpu().numpy()[:V].view(np.uint32), ref["map"])
 
 
+@pytest.mark.parametrize("case", ["side_planes", "widening"])
+def test_cluster_cull_closed_form_cases(orc, case):
+    """The closed-form cull cases of the oracle's pins (each of the five
+    planes, a relative 1e-3 inside and outside; the 3 x largest-scale
+    widening 2e-3 above and below the reach needed) through the kernel:
+    the same flags as the closed form and the oracle."""
+    import cull_cases as CC
+    geo, want = CC.side_plane_scene() if case == "side_planes" else CC.widening_scene()
+    n = geo["mean"].shape[0]
+    quat = np.zeros((n, 4), np.float32)
+    quat[:, 0] = 1.0
+    sc = {"mean": geo["mean"].astype(np.float32), "log_scale": geo["log_scale"].astype(np.float32),
+          "quat": quat, "logit": np.zeros(n, np.float32), "sh": np.zeros((n, 1, 3), np.float32),
+          "sh_degree": 0}
+    cam = CC.camera()
+    ref = orc.cluster_cull(sc, cam, CC.CLUSTER)
+    np.testing.assert_array_equal(ref["visible"], want)
+    planes, n = U.planes_tensor(sc)
+    g = B.gaussians_struct(planes, n, 0)
+    ncl = -(-n // CC.CLUSTER)
+    aabb = torch.zeros((ncl, 6), dtype=torch.float32, device="cuda")
+    vis = torch.zeros(ncl, dtype=torch.int32, device="cuda")
+    rowmap = torch.zeros(n, dtype=torch.int32, device="cuda")
+    dV = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(B.lgs_ccc_workspace_size(n, CC.CLUSTER), dtype=torch.uint8, device="cuda")
+    B.lgs_cluster_cull_compact(g, B.camera_struct(cam), CC.CLUSTER, aabb, vis, rowmap, dV, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(vis.cpu().numpy(), want)
+    assert int(dV.item()) == CC.CLUSTER * int(want.sum())
+
+
 # ---------------------------------------------------------------------------
 # a4 bin sort
 # ---------------------------------------------------------------------------
@@ -164,10 +195,7 @@ def test_bin_sort_bit_exact(orc, n, W, H, tile, cull):
     s["tau"][::17] = -np.inf                        # splats that reach no pixel
     vals, ranges, P = U.gpu_bin(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H, tile,
                                 conic=s["conic"], tau=s["tau"], cull=cull)
-    rv, rr, rP = orc.bin_splats(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H, tile,
-                                conic=s["conic"], tau=s["tau"], cull=bool(cull))
-    assert P == rP
-    U.assert_same_tile_lists(vals, ranges, rv, rr)
+    U.check_bins(orc, vals, ranges, P, s, W, H, tile, cull=cull)
 
 
 @pytest.mark.parametrize("cull", [0, 1])
@@ -190,10 +218,8 @@ def test_bin_sort_large_and_degenerate_splats(orc, cull):
     vals, ranges, P = U.gpu_bin(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H,
                                 (16, 16), conic=s["conic"], tau=s["tau"], cull=cull,
                                 cap=64_000_000)
-    rv, rr, rP = orc.bin_splats(s["uv"][:, 0], s["uv"][:, 1], s["radius"], s["depth"], W, H,
-                                (16, 16), conic=s["conic"], tau=s["tau"], cull=bool(cull))
-    assert P == rP and P > 100_000
-    U.assert_same_tile_lists(vals, ranges, rv, rr)
+    _, _, rP = U.check_bins(orc, vals, ranges, P, s, W, H, (16, 16), cull=cull)
+    assert rP > 100_000
     assert B.lgs_get_wait_timeouts() == 0
 
 
@@ -237,16 +263,14 @@ def _raster_case(orc, sp, cam, tile=(16, 16), seed=0, min_ok=0.995):
     W, H = cam["width"], cam["height"]
     w = np.random.default_rng(seed).standard_normal((3, H, W)).astype(np.float32) * 1e-3
     g = U.gpu_raster(sp, cam, tile, dLdI=w)
-    vals, ranges, P = orc.bin_splats(sp["uv"][:, 0], sp["uv"][:, 1], sp["radius"], sp["depth"], W, H,
-                                     tile, conic=sp["conic"], tau=sp["tau"])
-    assert g["P"] == P
-    U.assert_same_tile_lists(g["vals"], g["ranges"], vals, ranges)
+    vals, ranges, P = U.check_bins(orc, g["vals"], g["ranges"], g["P"], sp, W, H, tile)
     o = orc.render_fwd(sp, vals, ranges, cam, tile)
     ok = o["pixflags"] == 0
     assert ok.mean() > min_ok, ok.mean()
     err = np.abs(g["image"] - o["image"])[:, ok].max()
     assert err <= 1e-5, err
-    np.testing.assert_array_equal(g["last"][ok], o["last"][ok])
+    np.testing.assert_array_equal(U.last_ids(g["last"], g["vals"], g["ranges"], W, tile)[ok],
+                                  U.last_ids(o["last"], vals, ranges, W, tile)[ok])
     np.testing.assert_allclose(g["T"][ok], o["T"][ok], rtol=2e-5, atol=1e-7)
     ob = orc.render_bwd(sp, vals, ranges, cam, w, tile)
     names = ["du", "dv", "dA", "dB", "dC", "do", "dr", "dg", "db"]
@@ -271,18 +295,8 @@ def test_tile_culling_keeps_the_image_bit_identical(orc):
     np.testing.assert_array_equal(a["image"], b["image"])
     np.testing.assert_array_equal(a["T"], b["T"])
     # the last contributor is the same splat (list positions differ)
-    def last_id(g):
-        out = np.full(g["last"].shape, -1, np.int64)
-        gx = -(-320 // 16)
-        for t in range(g["ranges"].shape[0]):
-            ty, tx = divmod(t, gx)
-            blk = g["last"][ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
-            m = blk > 0
-            ids = np.full(blk.shape, -1, np.int64)
-            ids[m] = g["vals"][g["ranges"][t, 0] + blk[m] - 1]
-            out[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = ids
-        return out
-    np.testing.assert_array_equal(last_id(a), last_id(b))
+    np.testing.assert_array_equal(U.last_ids(a["last"], a["vals"], a["ranges"], 320),
+                                  U.last_ids(b["last"], b["vals"], b["ranges"], 320))
     for q in range(9):
         assert U.rel_l2(b["grad9"][:, q], a["grad9"][:, q]) < 1e-5
     np.testing.assert_array_equal(a["C"], b["C"])

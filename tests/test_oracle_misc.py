@@ -159,3 +159,29 @@ def test_l1_loss_and_gradient(orc):
     n = img.size
     assert g[0, 0, 0] == -1.0 / n and g[1, 2, 3] == 1.0 / n
     assert np.count_nonzero(g) == 2   # sign(0) = 0
+
+
+def test_cluster_cull_side_planes_closed_form(orc):
+    """Sec. 3.2.2's cull against each of the five planes in turn: a cluster
+    box whose nearest corner is a relative 1e-3 inside a plane is kept, one
+    1e-3 outside is culled (camera turned and moved; closed forms in
+    cull_cases). Deleting any plane keeps an outside cluster; transposing
+    the camera rotation moves the boxes elsewhere."""
+    import cull_cases as CC
+    sc, want = CC.side_plane_scene()
+    cc = orc.cluster_cull(sc, CC.camera(), CC.CLUSTER)
+    np.testing.assert_array_equal(cc["visible"], want)
+    assert (cc["flags"] == 0).all()
+    assert cc["V"] == CC.CLUSTER * int(want.sum())
+
+
+def test_cluster_cull_widening_by_three_largest_scales(orc):
+    """The box is widened by 3 x the largest scale of each member: clusters
+    whose centres all lie outside a side plane are kept exactly when one
+    member's 3 s reaches it (s on the x, y or z axis; 3 s a relative 2e-3
+    above or below the reach needed)."""
+    import cull_cases as CC
+    sc, want = CC.widening_scene()
+    cc = orc.cluster_cull(sc, CC.camera(), CC.CLUSTER)
+    np.testing.assert_array_equal(cc["visible"], want)
+    assert (cc["flags"] == 0).all()

@@ -233,51 +233,208 @@ def test_tile_culling_leaves_the_image_unchanged(orc):
     assert b["P"] < a["P"]
 
 
-def _box_min_q(u, v, A, B, C, xl, xh, yl, yh):
-    """Exact minimum over the box of q(d) = A dx^2 + 2B dx dy + C dy^2,
-    d = (u - x, v - y), in double precision: 0 if the box holds the centre,
-    else the least of the four edge minima (a convex quadratic restricted to
-    a segment is minimised at its clamped stationary point)."""
+def _tile_queries(n, seed, W=400, H=300, max_radius=60, reach=3):
+    rng = np.random.default_rng(seed)
+    sp = scenegen.random_splats(n, seed + 1, W, H, max_radius=max_radius)
+    tau = _tau(sp["opacity"]).astype(np.float32)
+    tx = (np.floor(sp["u"] / 16) + rng.integers(-reach, reach + 1, n)).astype(np.int32)
+    ty = (np.floor(sp["v"] / 16) + rng.integers(-reach, reach + 1, n)).astype(np.int32)
+    return sp, tau, tx, ty
+
+
+def test_tile_culling_axis_aligned_closed_form(orc):
+    """App. A.1's tile test for an axis-aligned conic (B = 0): the minimum of
+    A dx^2 + C dy^2 over the box of pixel centres is A ex^2 + C ey^2, ex and
+    ey the distances from the splat centre to the box's x and y ranges (0
+    inside). Swapping A and C, or measuring to the far edge, fails it."""
+    n = 100000
+    sp, tau, tx, ty = _tile_queries(n, 60)
+    conic = sp["conic"].copy()
+    conic[:, 1] = 0.0
+    u, v = sp["u"].astype(np.float64), sp["v"].astype(np.float64)
+    A, C = conic[:, 0].astype(np.float64), conic[:, 2].astype(np.float64)
+    xl, xh = tx * 16 + 0.5, tx * 16 + 15.5
+    yl, yh = ty * 16 + 0.5, ty * 16 + 15.5
+    ex = np.maximum(np.maximum(xl - u, u - xh), 0.0)
+    ey = np.maximum(np.maximum(yl - v, v - yh), 0.0)
+    qmin = A * ex * ex + C * ey * ey
+    got, near = orc.tile_reachable(sp["u"], sp["v"], conic, tau, tx, ty)
+    t = tau.astype(np.float64)
+    np.testing.assert_array_equal(got[~near], (qmin <= t)[~near])
+    assert near.mean() < 1e-3 and 0.05 < got.mean() < 0.95
+    swapped = C * ex * ex + A * ey * ey
+    assert ((swapped <= t) != got).sum() > 100
+
+
+def test_tile_culling_rotated_conic_against_a_numerical_minimum(orc):
+    """For rotated conics the box minimum is found independently: zero when a
+    positive-definite form's box holds the centre, else the least of a
+    bounded scalar minimisation (scipy) along each of the four edges."""
+    from scipy.optimize import minimize_scalar
+    n = 1500
+    sp, tau, tx, ty = _tile_queries(n, 61, reach=2)
+    got, near = orc.tile_reachable(sp["u"], sp["v"], sp["conic"], tau, tx, ty)
+    agree = 0
+    for i in range(n):
+        A, B, C = (float(c) for c in sp["conic"][i])
+        u, v = float(sp["u"][i]), float(sp["v"][i])
+        xl, xh = tx[i] * 16 + 0.5, tx[i] * 16 + 15.5
+        yl, yh = ty[i] * 16 + 0.5, ty[i] * 16 + 15.5
+        q = lambda x, y: A * (u - x) ** 2 + 2 * B * (u - x) * (v - y) + C * (v - y) ** 2
+        if xl <= u <= xh and yl <= v <= yh:
+            best = 0.0
+        else:
+            best = np.inf
+            for f, lo, hi in ((lambda y: q(xl, y), yl, yh), (lambda y: q(xh, y), yl, yh),
+                              (lambda x: q(x, yl), xl, xh), (lambda x: q(x, yh), xl, xh)):
+                r = minimize_scalar(f, bounds=(lo, hi), method="bounded",
+                                    options={"xatol": 1e-10})
+                best = min(best, r.fun, f(lo), f(hi))
+        t = float(tau[i])
+        if abs(best - t) > 1e-6 * (1 + abs(t)):
+            assert got[i] == (best <= t), (i, best, t)
+            agree += 1
+    assert agree > 0.99 * n and 0.1 < got.mean() < 0.9
+
+
+def _row_form_f32(u, v, A, B, C, tau, tx, ty, tw=16, th=16):
+    """A single-precision evaluation of the same test in its row form (per
+    tile row the x interval [L, U] of the ellipse q <= tau, then the tile's
+    offsets against it; a conic whose determinant rounds to <= 0 takes the
+    edge minima), each operation rounded once, as a kernel evaluates it."""
+    f32 = np.float32
+    u, v, A, B, C, tau = (np.asarray(a, f32) for a in (u, v, A, B, C, tau))
+    with np.errstate(all="ignore"):
+        det = A * C - B * B
+        ex, ey = np.sqrt((tau * C) / det), np.sqrt((tau * A) / det)
+        dyU = -((B * ex) / C)
+        yl, yh = (ty * th).astype(f32) + f32(0.5), (ty * th + th).astype(f32) + f32(-0.5)
+        xl, xh = (tx * tw).astype(f32) + f32(0.5), (tx * tw + tw).astype(f32) + f32(-0.5)
+        ay, by = v - yh, v - yl
+        At = A * tau
+        d = np.minimum(np.maximum(dyU, ay), by)
+        Uu = (np.sqrt(np.maximum(At - det * (d * d), f32(0))) - B * d) / A
+        d = np.minimum(np.maximum(-dyU, ay), by)
+        L = (-(np.sqrt(np.maximum(At - det * (d * d), f32(0))) + B * d)) / A
+        row = (tau >= 0) & (ay <= ey) & (by >= -ey) & ((u - xh) <= Uu) & ((u - xl) >= L)
+        ax, bx = u - xh, u - xl
+        inside = (ax <= 0) & (bx >= 0) & (ay <= 0) & (by >= 0)
+        rA, rC = f32(1) / A, f32(1) / C
+        qf = lambda dx, dy: ((A * dx) * dx + ((B * dx) * dy) * f32(2)) + (C * dy) * dy
+        q = qf(ax, np.minimum(np.maximum(-((B * ax) * rC), ay), by))
+        q = np.minimum(q, qf(bx, np.minimum(np.maximum(-((B * bx) * rC), ay), by)))
+        q = np.minimum(q, qf(np.minimum(np.maximum(-((B * ay) * rA), ax), bx), ay))
+        q = np.minimum(q, qf(np.minimum(np.maximum(-((B * by) * rA), ax), bx), by))
+        box = (inside & (tau >= 0)) | (q <= tau)
+    return np.where(det > 0, row, box)
+
+
+@pytest.mark.parametrize("case", ["plain", "large", "degenerate"])
+def test_tile_culling_single_precision_agrees_off_the_flags(orc, case):
+    """The oracle's near-tau flag covers single-precision evaluation: a row
+    form evaluated with one rounding per operation takes the oracle's
+    decision on every unflagged pair, including thin ellipses (axis ratio up
+    to ~1000) and conics whose determinant is 0 or negative."""
+    n = 300000
+    sp, tau, tx, ty = _tile_queries(n, 70 + len(case), W=1297, H=840,
+                                    max_radius=600 if case != "plain" else 40, reach=4)
+    conic = sp["conic"].astype(np.float64)
+    if case == "degenerate":
+        A, C = conic[:, 0], conic[:, 2]
+        conic[::7, 1] = np.sqrt(A[::7] * C[::7])
+        conic[3::11, 1] = 1.5 * np.sqrt(A[3::11] * C[3::11])
+        conic[5::13, 0] *= 1e3
+    conic = conic.astype(np.float32)
+    got, near = orc.tile_reachable(sp["u"], sp["v"], conic, tau, tx, ty)
+    emu = _row_form_f32(sp["u"], sp["v"], conic[:, 0], conic[:, 1], conic[:, 2], tau, tx, ty)
+    np.testing.assert_array_equal(emu[~near], got[~near])
+    assert near.mean() < 1e-3 and 0.02 < got.mean() < 0.98
+
+
+def _edge_min(u, v, A, B, C, tx, ty):
+    """Box minimum by the clamped stationary point of each edge (convex
+    edges: A, C > 0), 0 when the box holds the centre; numpy, double."""
+    xl, xh, yl, yh = tx * 16 + 0.5, tx * 16 + 15.5, ty * 16 + 0.5, ty * 16 + 15.5
     ax, bx, ay, by = u - xh, u - xl, v - yh, v - yl
-    inside = (ax <= 0) & (bx >= 0) & (ay <= 0) & (by >= 0)
     q = lambda dx, dy: A * dx * dx + 2 * B * dx * dy + C * dy * dy
     best = np.full(u.shape, np.inf)
     for dx in (ax, bx):
         best = np.minimum(best, q(dx, np.clip(-B * dx / C, ay, by)))
     for dy in (ay, by):
         best = np.minimum(best, q(np.clip(-B * dy / A, ax, bx), dy))
-    return np.where(inside, 0.0, best)
+    return np.where((ax <= 0) & (bx >= 0) & (ay <= 0) & (by >= 0), 0.0, best)
 
 
-def test_tile_culling_decision_is_the_box_minimum(orc):
-    # the oracle's single-precision row-interval decision agrees with the
-    # exact box minimum of the quadratic form wherever that minimum is not
-    # within rounding of tau; checked on random anisotropic splats and tiles
-    rng = np.random.default_rng(44)
-    n = 200000
-    sp = scenegen.random_splats(n, 45, 400, 300, max_radius=60)
-    tau = (2.0 * np.log(255.0 * sp["opacity"].astype(np.float64)))
-    tau = (tau + 1e-3 * (1 + np.abs(tau))).astype(np.float32)
-    # tiles around each splat's centre, up to 3 tiles away
-    tx = (np.floor(sp["u"] / 16) + rng.integers(-3, 4, n)).astype(np.int32)
-    ty = (np.floor(sp["v"] / 16) + rng.integers(-3, 4, n)).astype(np.int32)
-    got = orc.tile_reachable(sp["u"], sp["v"], sp["conic"], tau, tx, ty)
-    u, v = sp["u"].astype(np.float64), sp["v"].astype(np.float64)
+@pytest.mark.parametrize("seed,max_radius", [(1, 40), (2, 200), (3, 600)])
+def test_tile_culling_flag_covers_the_boundary(orc, seed, max_radius):
+    """Stress of the near-tau flag where it matters: tau placed within a
+    relative 3e-6 of each pair's exact box minimum, so that a few percent of
+    single-precision decisions differ from the exact ones. Every such
+    difference is flagged, and it still is with the margin cut 64-fold."""
+    n = 300000
+    rng = np.random.default_rng(seed)
+    sp = scenegen.random_splats(n, seed, 1297, 840, max_radius=max_radius)
+    tx = (np.floor(sp["u"] / 16) + rng.integers(-4, 5, n)).astype(np.int32)
+    ty = (np.floor(sp["v"] / 16) + rng.integers(-4, 5, n)).astype(np.int32)
     A, B, C = (sp["conic"][:, k].astype(np.float64) for k in range(3))
-    qmin = _box_min_q(u, v, A, B, C, tx * 16 + 0.5, tx * 16 + 15.5, ty * 16 + 0.5, ty * 16 + 15.5)
-    t = tau.astype(np.float64)
-    clear = np.abs(qmin - t) > 1e-4 * (1 + np.abs(t))
-    assert clear.mean() > 0.99
-    np.testing.assert_array_equal(got[clear], (qmin <= t)[clear])
-    assert 0.05 < got.mean() < 0.95          # both outcomes are exercised
-    # the exact minimum is a lower bound of a dense sampling of the box
-    for i in rng.choice(n, 50, replace=False):
-        xs = np.linspace(tx[i] * 16 + 0.5, tx[i] * 16 + 15.5, 61)
-        ys = np.linspace(ty[i] * 16 + 0.5, ty[i] * 16 + 15.5, 61)
-        X, Y = np.meshgrid(xs, ys)
-        dx, dy = u[i] - X, v[i] - Y
-        dense = (A[i] * dx * dx + 2 * B[i] * dx * dy + C[i] * dy * dy).min()
-        assert qmin[i] <= dense + 1e-9 * (1 + dense)
+    qm = _edge_min(sp["u"].astype(np.float64), sp["v"].astype(np.float64), A, B, C, tx, ty)
+    border = (qm > 0.5) & (qm < 30)
+    tau = (qm * (1 + rng.uniform(-3e-6, 3e-6, n))).astype(np.float32)
+    emu = _row_form_f32(sp["u"], sp["v"], sp["conic"][:, 0], sp["conic"][:, 1], sp["conic"][:, 2],
+                        tau, tx, ty)
+    for m in (orc.TAU_MARGIN, orc.TAU_MARGIN / 64):
+        orc.set_tau_margin(m)
+        try:
+            got, near = orc.tile_reachable(sp["u"], sp["v"], sp["conic"], tau, tx, ty)
+        finally:
+            orc.set_tau_margin(orc.TAU_MARGIN)
+        differ = (emu != got) & border
+        assert differ.sum() > 0.01 * border.sum()
+        assert near[differ].all()
+
+
+def test_tile_culling_near_pairs_enumerated(orc):
+    """tile_near_pairs lists exactly the rectangle pairs that tile_reachable
+    flags (with the flag widened so that many exist)."""
+    W, H = 300, 200
+    s = scenegen.random_splats(3000, 90, W, H, max_radius=40)
+    tau = _tau(s["opacity"]).astype(np.float32)
+    orc.set_tau_margin(1e-3)
+    try:
+        keys = orc.tile_near_pairs(s["u"], s["v"], s["radius"], s["conic"], tau, W, H)
+        full, ranges, P = orc.bin_splats(s["u"], s["v"], s["radius"], s["depth"], W, H)
+        gx = -(-W // 16)
+        tiles = np.repeat(np.arange(ranges.shape[0]), (ranges[:, 1] - ranges[:, 0]).astype(np.int64))
+        j = full[np.concatenate([np.arange(a, b) for a, b in ranges.astype(np.int64)])]
+        _, near = orc.tile_reachable(s["u"][j], s["v"][j], s["conic"][j], tau[j], tiles % gx, tiles // gx)
+    finally:
+        orc.set_tau_margin(orc.TAU_MARGIN)
+    want = np.sort((tiles[near].astype(np.uint64) << np.uint64(32)) | j[near].astype(np.uint64))
+    np.testing.assert_array_equal(np.sort(keys), want)
+    assert 10 < keys.size < 0.1 * P
+
+
+def test_tile_culling_near_pairs_hold_no_fragment(orc):
+    """At the default margin and for splats up to 60 px, no near-tau pair
+    holds a pixel centre with alpha >= 1/255 (tau is widened by
+    1e-3 (1 + |tau|) beyond that threshold, more than the flag's margin on
+    such offsets), so whichever way a kernel decides them, no pixel changes.
+    Brute force over each pair's tile. (For much larger splats the margin,
+    64 roundings of the offsets, can exceed the widening; the GPU tests then
+    check the pairs that the two binnings actually decide differently.)"""
+    W, H = 1297, 840
+    s = scenegen.random_splats(200000, 91, W, H, max_radius=60)
+    tau = _tau(s["opacity"]).astype(np.float32)
+    keys = orc.tile_near_pairs(s["u"], s["v"], s["radius"], s["conic"], tau, W, H)
+    assert keys.size > 5
+    gx = -(-W // 16)
+    for key in keys.tolist():
+        t, i = key >> 32, key & 0xffffffff
+        px, py = np.meshgrid((t % gx) * 16 + np.arange(16) + 0.5, (t // gx) * 16 + np.arange(16) + 0.5)
+        A, B, C = (float(c) for c in s["conic"][i])
+        dx, dy = float(s["u"][i]) - px, float(s["v"][i]) - py
+        a = float(s["opacity"][i]) * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+        assert (a < 1 / 255).all()
 
 
 def test_rotated_splat_off_diagonal_conic_and_image(orc):
