@@ -1,25 +1,32 @@
 // Tile rasteriser, forward (Eq. 1-2, Alg. 1) and backward (Eq. 3, App. A.1
 // Eq. 4-6) with the opacity-gradient moments of Sec. 3.3.
 //
-// One CTA of 4 warps per 16 x 16 tile; warp w owns the 8 x 8 quadrant w of
-// the tile and every thread a horizontal pair of pixels. The tile's sorted
-// splats are staged through shared memory 128 at a time (one per thread).
-// While staging, each thread tests its splat against the four quadrants
-// with the test the binning uses per tile (the minimum of the exponent's
-// quadratic form over the quadrant's pixel centres against tau, in its row
-// form: one x interval per 8-row slab), so each warp walks only the splats
-// that can reach its quadrant.
-// In the backward each thread first sums a splat's per-pixel terms over its
-// two pixels, the warp reduces the 12 sums with a reduce-scatter butterfly
-// (16 shuffles; value i ends on lanes 2i, 2i + 1) and lanes 0, 2, .., 22
-// issue one atomic each (App. A.1 Eq. 5-6: one atomic per value per warp).
+// A tile is 16 x 16 pixels in four 8 x 8 quadrants. The tile's sorted
+// splats are staged through shared memory 128 at a time. While staging, each
+// thread tests its splats against the four quadrants with the test the
+// binning uses per tile (the minimum of the exponent's quadratic form over
+// the quadrant's pixel centres against tau, in its row form: one x interval
+// per 8-row slab), so that each quadrant walks only the splats that can
+// reach it.
+// One CTA of 4 warps per tile; warp w owns quadrant w and each lane a
+// horizontal pair of pixels of it, in both passes.
+// In the backward each lane first sums a splat's per-pixel terms over its
+// two pixels (App. A.1's thread-local sum), the warp reduces the 12 sums
+// (9 gradients, S, M and the fragment count) with a reduce-scatter
+// butterfly (13 shuffles; value i ends on lanes 2i', 2i' + 1) and one lane
+// per value issues one atomic: one atomic per value per splat and quadrant
+// (App. A.1 Eq. 5-6, the tile's reduction split over its four quadrant
+// warps). The per-pixel exponent moments are summed as sum qq, sum dx qq and
+// sum dx^2 qq over the lane's row (dy is the same for both pixels), which
+// gives the five conic and centre sums with dy applied once per splat.
 //
-// The exponent is power = dx (a dx + b dy) + c dy^2 with a = -A/2, b = -B,
-// c = -C/2, evaluated with explicitly rounded FP32 operations in one helper
-// shared by both passes, so the backward re-derives exactly the alphas the
-// forward composited. In the mixed-precision variants the Gaussian value G,
-// o G and alpha are computed for the pixel pair as one FP16x2 or BF16x2
-// value; the exponent (conic), transmittance, colour accumulators and
+// The exponent is evaluated in base 2: power log2(e) = dx (a dx + b dy) +
+// c dy^2 with a = -A log2(e) / 2, b = -B log2(e), c = -C log2(e) / 2, so that
+// G is one ex2 per pixel, with explicitly rounded FP32 operations in one
+// helper shared by both passes, pixel by pixel: the backward re-derives
+// exactly the alphas the forward composited. In the mixed-precision variants
+// the Gaussian value G, o G and alpha of a pair of pixels are one FP16x2 or
+// BF16x2 value; the exponent (conic), transmittance, colour accumulators and
 // gradient sums stay FP32.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -32,14 +39,22 @@ namespace lgs {
 namespace {
 
 constexpr int kTile = 16;
-constexpr int kBatch = 128;  // threads per CTA = splats staged per round
+constexpr int kFwdThreads = 128;  // four warps per tile, one per quadrant
+constexpr int kBwdThreads = 128;
+constexpr int kBatch = 128;       // splats staged per round, one per thread
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
 
-struct SplatS {
-    float u, v, a, b, c, o, r, g, bl;
-    uint32_t oh;  // o as a 16-bit pair (mixed precision only)
+// A staged splat: 3 x 16 bytes, read with three vector loads.
+struct __align__(16) SplatS {
+    float u, v, a, b, c, o;  // centre, exponent coefficients (base 2), opacity
+    float r, g, bl;          // colour
+    uint32_t oh;             // o as a 16-bit pair (mixed precision only)
+    uint32_t id;             // splat index (gradient row)
+    float pad;
 };
 
 struct RCam {
@@ -65,6 +80,12 @@ __device__ __forceinline__ uint32_t pack_pair(float x) {
     }
 }
 
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Approximate square root for the quadrant test: x * rsqrt(x), 0 for
 // x <= 0, and finite (about 1.8e19) for an infinite x.
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -73,7 +94,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // Loads splat j into s and returns the 4-bit mask of the tile quadrants
-// (bit w: quadrant x0 + 8 (w & 1), y0 + 8 (w >> 1)) it may reach. The mask
+// (bit 2 qr + qc: quadrant x0 + 8 qc, y0 + 8 qr) it may reach. The mask
 // only saves work: a quadrant left out must have alpha < 1/255 at every
 // pixel, so the test may be loose but never tight. It is the row form of
 // the tile test (per quadrant row, the x interval [L, U] of the ellipse
@@ -87,16 +108,20 @@ __device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_
     const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)j);
     const float4 x = __ldg(p), y = __ldg(p + 1);
     const float2 z = __ldg(reinterpret_cast<const float2 *>(rec + 12 * (int64_t)j + 8));
-    s.u = x.x;
-    s.v = x.y;
-    s.a = -0.5f * x.z;
-    s.b = -x.w;
-    s.c = -0.5f * y.x;
-    s.o = y.y;
-    s.r = y.z;
-    s.g = y.w;
-    s.bl = z.x;
-    s.oh = pack_pair<PREC>(y.y);
+    SplatS t;
+    t.u = x.x;
+    t.v = x.y;
+    t.a = __fmul_rn(x.z, -0.5f * kLog2e);
+    t.b = __fmul_rn(x.w, -kLog2e);
+    t.c = __fmul_rn(y.x, -0.5f * kLog2e);
+    t.o = y.y;
+    t.r = y.z;
+    t.g = y.w;
+    t.bl = z.x;
+    t.oh = pack_pair<PREC>(y.y);
+    t.id = j;
+    t.pad = 0.0f;
+    s = t;
     const float A = x.z, B = x.w, C = y.x, tau = z.y;
     if (!(tau >= 0.0f)) return 0u;
     const float det = A * C - B * B;
@@ -125,34 +150,42 @@ __device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_
     return m;
 }
 
-// Exponent at two horizontally adjacent pixels of one row.
-__device__ __forceinline__ void power2(const SplatS &s, float fx, float fy, float &p0,
-                                       float &p1) {
-    const float dx0 = __fsub_rn(s.u, fx), dx1 = __fsub_rn(s.u, __fadd_rn(fx, 1.0f));
-    const float dy = __fsub_rn(s.v, fy);
-    const float bdy = __fmul_rn(s.b, dy), cdy2 = __fmul_rn(__fmul_rn(s.c, dy), dy);
+// Exponent (base 2) at two horizontally adjacent pixel centres fx, fx + 1
+// of a row whose terms b dy and c dy^2 are given.
+__device__ __forceinline__ void power2(const SplatS &s, float fx, float bdy, float cdy2,
+                                       float &dx0, float &dx1, float &p0, float &p1) {
+    dx0 = __fsub_rn(s.u, fx);
+    dx1 = __fsub_rn(s.u, __fadd_rn(fx, 1.0f));
     p0 = __fmaf_rn(dx0, __fmaf_rn(s.a, dx0, bdy), cdy2);
     p1 = __fmaf_rn(dx1, __fmaf_rn(s.a, dx1, bdy), cdy2);
 }
 
-// G = exp(power), alpha = min(0.99, o G) and whether the clamp is active,
-// for a pixel pair.
+// b dy and c dy^2 of the row at fy; dy = v - fy.
+__device__ __forceinline__ void row_terms(const SplatS &s, float fy, float &dy, float &bdy,
+                                          float &cdy2) {
+    dy = __fsub_rn(s.v, fy);
+    bdy = __fmul_rn(s.b, dy);
+    cdy2 = __fmul_rn(__fmul_rn(s.c, dy), dy);
+}
+
+// G = 2^p, alpha = min(0.99, o G) and whether the clamp is active, for a
+// pixel pair (elementwise: a pixel's values do not depend on its partner).
 template <int PREC>
 __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, float &G0, float &G1,
                                        float &a0, float &a1, bool &cl0, bool &cl1) {
     if constexpr (blend_of(PREC) == LGS_FP32) {
-        G0 = __expf(p0);
-        G1 = __expf(p1);
+        G0 = ex2(p0);
+        G1 = ex2(p1);
         const float q0 = s.o * G0, q1 = s.o * G1;
         a0 = fminf(kAlphaMax, q0);
         a1 = fminf(kAlphaMax, q1);
         cl0 = q0 >= kAlphaMax;
         cl1 = q1 >= kAlphaMax;
     } else if constexpr (blend_of(PREC) == LGS_MIXED_FP16) {
-        const __half2 G = h2exp(__floats2half2_rn(p0, p1));
-        const __half2 q = __hmul2(*reinterpret_cast<const __half2 *>(&s.oh), G);
+        const __half2 g = h2exp2(__floats2half2_rn(p0, p1));
+        const __half2 q = __hmul2(*reinterpret_cast<const __half2 *>(&s.oh), g);
         const __half2 cap = __float2half2_rn(kAlphaMax);
-        const float2 Gf = __half22float2(G), af = __half22float2(__hmin2(q, cap));
+        const float2 Gf = __half22float2(g), af = __half22float2(__hmin2(q, cap));
         const __half2 ge = __hge2(q, cap);
         G0 = Gf.x;
         G1 = Gf.y;
@@ -161,10 +194,10 @@ __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, floa
         cl0 = __low2float(ge) != 0.0f;
         cl1 = __high2float(ge) != 0.0f;
     } else {
-        const __nv_bfloat162 G = h2exp(__floats2bfloat162_rn(p0, p1));
-        const __nv_bfloat162 q = __hmul2(*reinterpret_cast<const __nv_bfloat162 *>(&s.oh), G);
+        const __nv_bfloat162 g = h2exp2(__floats2bfloat162_rn(p0, p1));
+        const __nv_bfloat162 q = __hmul2(*reinterpret_cast<const __nv_bfloat162 *>(&s.oh), g);
         const __nv_bfloat162 cap = __float2bfloat162_rn(kAlphaMax);
-        const float2 Gf = __bfloat1622float2(G), af = __bfloat1622float2(__hmin2(q, cap));
+        const float2 Gf = __bfloat1622float2(g), af = __bfloat1622float2(__hmin2(q, cap));
         const __nv_bfloat162 ge = __hge2(q, cap);
         G0 = Gf.x;
         G1 = Gf.y;
@@ -175,14 +208,22 @@ __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, floa
     }
 }
 
-// One tile of the forward pass, by the whole CTA.
+struct RasterSmem {
+    SplatS sp[kBatch];
+    uint8_t fl[kBatch];
+    int maxlast;
+};
+
+// One tile of the forward pass, by the whole CTA (kFwdThreads): warp w
+// owns quadrant w (x0 + 8 (w & 1), y0 + 8 (w >> 1)), lane l the pixels
+// (2 (l & 3), l >> 2) and its right neighbour in it.
 template <int PREC>
 __device__ __forceinline__ void fwd_tile(const float *__restrict__ rec,
                                          const uint32_t *__restrict__ vals,
                                          const uint32_t *__restrict__ ranges, const RCam &K,
                                          int tile, float *__restrict__ image,
                                          float *__restrict__ finalT, int32_t *__restrict__ last,
-                                         SplatS *s_sp, uint8_t *s_fl) {
+                                         RasterSmem &sm) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
     const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
@@ -195,20 +236,22 @@ __device__ __forceinline__ void fwd_tile(const float *__restrict__ rec,
     for (uint32_t b0 = r0; b0 < r1; b0 += kBatch) {
         if (__syncthreads_count(live != 0) == 0) break;
         const uint32_t idx = b0 + threadIdx.x;
-        if (idx < r1) s_fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, vals[idx], tx0, ty0, s_sp[threadIdx.x]);
+        if (idx < r1)
+            sm.fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, vals[idx], tx0, ty0, sm.sp[threadIdx.x]);
         __syncthreads();
         const int cnt = (int)min((uint32_t)kBatch, r1 - b0);
 #pragma unroll 1
         for (int q = 0; q < kBatch / 32; ++q) {
             const int t = 32 * q + lane;
-            uint32_t m = __ballot_sync(0xffffffffu, t < cnt && ((s_fl[t] >> w) & 1u));
+            uint32_t m = __ballot_sync(0xffffffffu, t < cnt && ((sm.fl[t] >> w) & 1u));
             while (m && live) {
                 const int k = 32 * q + __ffs(m) - 1;
                 m &= m - 1;
-                const SplatS s = s_sp[k];
-                float p0, p1, G0, G1, a0, a1;
+                const SplatS s = sm.sp[k];
+                float dy, bdy, cdy2, dx0, dx1, p0, p1, G0, G1, a0, a1;
                 bool c0, c1;
-                power2(s, fx, fy, p0, p1);
+                row_terms(s, fy, dy, bdy, cdy2);
+                power2(s, fx, bdy, cdy2, dx0, dx1, p0, p1);
                 blend2<PREC>(s, p0, p1, G0, G1, a0, a1, c0, c1);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -229,7 +272,6 @@ __device__ __forceinline__ void fwd_tile(const float *__restrict__ rec,
                 }
             }
         }
-        __syncthreads();
     }
     const int64_t hw = (int64_t)K.W * K.H;
 #pragma unroll
@@ -246,63 +288,51 @@ __device__ __forceinline__ void fwd_tile(const float *__restrict__ rec,
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kBatch) k_raster_fwd(const float *__restrict__ rec,
-                                                     const uint32_t *__restrict__ vals,
-                                                     const uint32_t *__restrict__ ranges, RCam K,
-                                                     float *__restrict__ image,
-                                                     float *__restrict__ finalT,
-                                                     int32_t *__restrict__ last) {
-    __shared__ SplatS s_sp[kBatch];
-    __shared__ uint8_t s_fl[kBatch];
-    fwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, image, finalT, last, s_sp, s_fl);
+__global__ void __launch_bounds__(kFwdThreads) k_raster_fwd(const float *__restrict__ rec,
+                                                            const uint32_t *__restrict__ vals,
+                                                            const uint32_t *__restrict__ ranges,
+                                                            RCam K, float *__restrict__ image,
+                                                            float *__restrict__ finalT,
+                                                            int32_t *__restrict__ last) {
+    __shared__ RasterSmem sm;
+    fwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, image, finalT, last, sm);
 }
 
-// Reduce-scatter of 10 values across the warp in 12 shuffles (halving the
-// vector at every butterfly stage, odd lengths padded with a zero): on
-// return, the two lanes 2i, 2i + 1 hold the warp sum of value
-// scatter10_index(2i), or a padding zero when that index is negative.
-__device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int lane) {
-    float w[6], x[4], y[2];
-    {
-        const bool up = lane & 16;  // 10 -> 5
+// Reduce-scatter of 12 values across the warp in 13 shuffles (halving the
+// vector at the butterfly stages on lane bits 4..1, 3 values padded to 4,
+// then one all-reduce step on bit 0): on return, lanes 2i and 2i + 1 both
+// hold the warp sum of value scatter12_index(2i), or a padding zero when
+// that index is -1.
+__device__ __forceinline__ float warp_reduce_scatter12(const float v[12], int lane) {
+    float w[6], x[3], y[2];
+    const bool b4 = lane & 16;  // 12 -> 6
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const float send = up ? v[i] : v[i + 5];
-            const float keep = up ? v[i + 5] : v[i];
-            w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
-        w[5] = 0.0f;
+    for (int i = 0; i < 6; ++i) {
+        const float send = b4 ? v[i] : v[i + 6];
+        const float keep = b4 ? v[i + 6] : v[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    {
-        const bool up = lane & 8;  // 5 (+1) -> 3
+    const bool b3 = lane & 8;  // 6 -> 3
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float send = up ? w[i] : w[i + 3];
-            const float keep = up ? w[i + 3] : w[i];
-            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-        x[3] = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        const float send = b3 ? w[i] : w[i + 3];
+        const float keep = b3 ? w[i + 3] : w[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
-    {
-        const bool up = lane & 4;  // 3 (+1) -> 2
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float send = up ? x[i] : x[i + 2];
-            const float keep = up ? x[i + 2] : x[i];
-            y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-        }
-    }
-    const bool up = lane & 2;  // 2 -> 1
-    const float z = (up ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, up ? y[0] : y[1], 2);
+    const bool b2 = lane & 4;  // 3 (+1) -> 2
+    y[0] = (b2 ? x[2] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[2], 4);
+    y[1] = (b2 ? 0.0f : x[1]) + __shfl_xor_sync(0xffffffffu, b2 ? x[1] : 0.0f, 4);
+    const bool b1 = lane & 2;  // 2 -> 1
+    const float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, b1 ? y[0] : y[1], 2);
     return z + __shfl_xor_sync(0xffffffffu, z, 1);
 }
 
-// The value index warp_reduce_scatter10 leaves in `lane`: 5 b4 + 3 b3 +
-// 2 b2 + b1 (b_k = bit k of the lane) when that slot holds a value, else -1.
-__device__ __forceinline__ int scatter10_index(int lane) {
-    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
-    const int loc = 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
-    return loc < (b3 ? 2 : 3) ? 5 * b4 + 3 * b3 + loc : -1;
+// The value index warp_reduce_scatter12 leaves in `lane`:
+// 6 b4 + 3 b3 + (b2 ? 2 : b1), padding (-1) when b2 = b1 = 1.
+__device__ __forceinline__ int scatter12_index(int lane) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    const int base = 6 * b4 + 3 * b3;
+    return b2 ? (b1 ? -1 : base + 2) : base + b1;
 }
 
 // Warp sum by the integer warp reduction of Sec. 3.1: the largest exponent
@@ -320,7 +350,9 @@ __device__ __forceinline__ float warp_sum_int(float x) {
     return (float)tot * __uint_as_float((emax - 25u) << 23);  // 2^(emax - 152)
 }
 
-// One tile of the backward pass, by the whole CTA.
+// One tile of the backward pass, by the whole CTA (kBwdThreads): warp w
+// owns quadrant w, lane l the pixel pair (2 (l & 3), l >> 2) of it, as in
+// the forward.
 template <int PREC>
 __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                                          const uint32_t *__restrict__ vals,
@@ -328,8 +360,7 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                                          int tile, const float *__restrict__ finalT,
                                          const int32_t *__restrict__ last,
                                          const float *__restrict__ dLdI, float *__restrict__ gacc,
-                                         SplatS *s_sp, uint32_t *s_id, uint8_t *s_fl,
-                                         int &s_maxlast) {
+                                         RasterSmem &sm) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
     const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
@@ -358,116 +389,106 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
         accg[h] = 0.0f;
     }
     const int32_t wmax = __reduce_max_sync(0xffffffffu, max(lst[0], lst[1]));
-    if (threadIdx.x == 0) s_maxlast = 0;
+    if (threadIdx.x == 0) sm.maxlast = 0;
     __syncthreads();
-    if (lane == 0) atomicMax(&s_maxlast, wmax);
+    if (lane == 0) atomicMax(&sm.maxlast, wmax);
     __syncthreads();
-    const int maxlast = s_maxlast;
+    const int maxlast = sm.maxlast;
+    const int vi = scatter12_index(lane);
     // positions maxlast-1 .. 0 of the tile list, 128 at a time from the back
     for (int end = maxlast; end > 0; end -= kBatch) {
         const int cnt = min(kBatch, end);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t j = vals[r0 + end - 1 - threadIdx.x];
-            s_id[threadIdx.x] = j;
-            s_fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, j, tx0, ty0, s_sp[threadIdx.x]);
-        }
+        if ((int)threadIdx.x < cnt)
+            sm.fl[threadIdx.x] =
+                (uint8_t)stage<PREC>(rec, vals[r0 + end - 1 - threadIdx.x], tx0, ty0, sm.sp[threadIdx.x]);
         __syncthreads();
 #pragma unroll 1
         for (int q = 0; q < kBatch / 32; ++q) {
             const int t = 32 * q + lane;
             uint32_t m = __ballot_sync(0xffffffffu, t < cnt && end - 1 - t < wmax &&
-                                                        ((s_fl[t] >> w) & 1u));
+                                                        ((sm.fl[t] >> w) & 1u));
             while (m) {
                 const int k = 32 * q + __ffs(m) - 1;
                 m &= m - 1;
                 const int pos = end - 1 - k;
-                const SplatS s = s_sp[k];
-                float v[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-                float p0, p1, G0, G1, a0, a1;
-                bool c0, c1;
-                power2(s, fx, fy, p0, p1);
-                blend2<PREC>(s, p0, p1, G0, G1, a0, a1, c0, c1);
-                float gr = 0.f, gg = 0.f, gb = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f,
-                      syy = 0.f, dO = 0.f, S = 0.f;
-                uint32_t n = 0;
-                const float dy = __fsub_rn(s.v, fy);
+                const SplatS s = sm.sp[k];
+                float dy, bdy, cdy2, dx[2], p[2], G[2], al[2];
+                bool cl[2];
+                row_terms(s, fy, dy, bdy, cdy2);
+                power2(s, fx, bdy, cdy2, dx[0], dx[1], p[0], p[1]);
+                blend2<PREC>(s, p[0], p[1], G[0], G[1], al[0], al[1], cl[0], cl[1]);
+                // lane sums over its pixels: colour, opacity, opacity moment,
+                // and Q0 = sum qq, Q1 = sum dx qq, Q2 = sum dx^2 qq, qq = dL/dpower
+                float gr = 0.f, gg = 0.f, gb = 0.f, dO = 0.f, S = 0.f, Q0 = 0.f, Q1 = 0.f, Q2 = 0.f;
+                float n = 0.f;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float a = h ? a1 : a0;
-                    if (pos < lst[h] && a >= kAlphaMin) {
-                        const float G = h ? G1 : G0;
-                        const bool clamped = h ? c1 : c0;
-                        const float rom = __fdividef(1.0f, 1.0f - a);
+                    if (pos < lst[h] && al[h] >= kAlphaMin) {
+                        const float rom = __fdividef(1.0f, 1.0f - al[h]);
                         const float Tk = T[h] * rom;
                         const float dd = s.r * g0[h] + s.g * g1[h] + s.bl * g2[h] - accg[h];
                         const float dLda = Tk * dd - bgT[h] * rom;
-                        const float wT = a * Tk;
+                        const float wT = al[h] * Tk;
                         gr = fmaf(wT, g0[h], gr);
                         gg = fmaf(wT, g1[h], gg);
                         gb = fmaf(wT, g2[h], gb);
-                        if (!clamped) {
-                            const float dx = __fsub_rn(s.u, __fadd_rn(fx, (float)h));
-                            const float dLdo = G * dLda, qq = a * dLda;
+                        if (!cl[h]) {
+                            const float dLdo = G[h] * dLda, qq = al[h] * dLda;
                             dO += dLdo;
                             S = fmaf(dLdo, dLdo, S);
-                            const float qx = dx * qq, qy = dy * qq;
-                            sx += qx;
-                            sy += qy;
-                            sxx = fmaf(dx, qx, sxx);
-                            sxy = fmaf(dy, qx, sxy);
-                            syy = fmaf(dy, qy, syy);
+                            const float qx = dx[h] * qq;
+                            Q0 += qq;
+                            Q1 += qx;
+                            Q2 = fmaf(dx[h], qx, Q2);
                         }
-                        ++n;
-                        accg[h] = fmaf(a, dd, accg[h]);
+                        n += 1.0f;
+                        accg[h] = fmaf(al[h], dd, accg[h]);
                         T[h] = Tk;
                     }
                 }
-                if (__any_sync(0xffffffffu, n != 0u)) {
-                    // -(A sx + B sy), -(B sx + C sy), -sxx/2, -sxy, -syy/2 with
-                    // A = -2a, B = -b, C = -2c; then dL/do, dL/dcolour, S. The
-                    // row's M (slot 10) is the same sum as dL/do, C (11) the
-                    // integer count of contributing pixels.
-                    float v[10];
-                    v[0] = 2.0f * s.a * sx + s.b * sy;
-                    v[1] = s.b * sx + 2.0f * s.c * sy;
-                    v[2] = -0.5f * sxx;
-                    v[3] = -sxy;
-                    v[4] = -0.5f * syy;
-                    v[5] = dO;
-                    v[6] = gr;
-                    v[7] = gg;
-                    v[8] = gb;
-                    v[9] = S;
-                    const uint32_t cnt = __reduce_add_sync(0xffffffffu, n);
-                    float *row = gacc + 16 * (int64_t)s_id[k];
-                    if constexpr (int_reduce(PREC)) {
-                        const int vi = lane >> 1;
-                        float mine = 0.f;
+                if (!__any_sync(0xffffffffu, n != 0.0f)) continue;
+                // with a, b, c in base 2: -(A sx + B sy) = ln2 (2 a sx + b sy),
+                // likewise for v; sx = Q1, sy = dy Q0, sxx = Q2, sxy = dy Q1,
+                // syy = dy^2 Q0. Then dL/do, dL/dcolour, S, M (= dL/do) and
+                // the fragment count (exact in FP32).
+                const float dyQ0 = dy * Q0;
+                float v[12];
+                v[0] = kLn2 * (2.0f * s.a * Q1 + s.b * dyQ0);
+                v[1] = kLn2 * (s.b * Q1 + 2.0f * s.c * dyQ0);
+                v[2] = -0.5f * Q2;
+                v[3] = -dy * Q1;
+                v[4] = -0.5f * dy * dyQ0;
+                v[5] = dO;
+                v[6] = gr;
+                v[7] = gg;
+                v[8] = gb;
+                v[9] = S;
+                v[10] = dO;
+                v[11] = n;
+                float *row = gacc + 16 * (int64_t)s.id;
+                if constexpr (int_reduce(PREC)) {
+                    const int mi = lane >> 1;
+                    float mine = 0.f;
 #pragma unroll
-                        for (int i = 0; i < 10; ++i) {
-                            const float t = warp_sum_int(v[i]);
-                            if (vi == i || (i == 5 && vi == 10)) mine = t;  // M = the opacity sum
-                        }
-                        if ((lane & 1) == 0) {
-                            if (vi < 11)
-                                atomicAdd(row + vi, mine);
-                            else if (vi == 11)
-                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11), cnt);
-                        }
-                    } else {
-                        const float red = warp_reduce_scatter10(v, lane);
-                        if ((lane & 1) == 0) {
-                            const int vi = scatter10_index(lane);
-                            if (vi >= 0) {
-                                atomicAdd(row + vi, red);
-                                if (vi == 5) atomicAdd(row + 10, red);
-                            } else if (lane == 12) {
-                                atomicAdd(reinterpret_cast<unsigned int *>(row + 11), cnt);
-                            }
-                        }
+                    for (int i = 0; i < 10; ++i) {
+                        const float t = warp_sum_int(v[i]);
+                        if (mi == i || (i == 5 && mi == 10)) mine = t;  // M = the opacity sum
+                    }
+                    const uint32_t cnt_w = __reduce_add_sync(0xffffffffu, (uint32_t)n);
+                    if ((lane & 1) == 0) {
+                        if (mi < 11)
+                            atomicAdd(row + mi, mine);
+                        else if (mi == 11)
+                            atomicAdd(reinterpret_cast<unsigned int *>(row + 11), cnt_w);
+                    }
+                } else {
+                    const float red = warp_reduce_scatter12(v, lane);
+                    if ((lane & 1) == 0 && vi >= 0) {
+                        if (vi < 11)
+                            atomicAdd(row + vi, red);
+                        else
+                            atomicAdd(reinterpret_cast<unsigned int *>(row + 11), (unsigned int)red);
                     }
                 }
             }
@@ -476,16 +497,12 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kBatch) k_raster_bwd(
+__global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ ranges, RCam K, const float *__restrict__ finalT,
     const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc) {
-    __shared__ SplatS s_sp[kBatch];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ uint8_t s_fl[kBatch];
-    __shared__ int s_maxlast;
-    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, s_sp, s_id, s_fl,
-                   s_maxlast);
+    __shared__ RasterSmem sm;
+    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,11 +528,10 @@ __device__ __forceinline__ RCam view_rcam(const lgs_view &V) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kBatch) k_raster_fwd_batch(const lgs_view *__restrict__ views,
-                                                           int n_views, uint32_t total_tiles,
-                                                           uint32_t *counter) {
-    __shared__ SplatS s_sp[kBatch];
-    __shared__ uint8_t s_fl[kBatch];
+__global__ void __launch_bounds__(kFwdThreads) k_raster_fwd_batch(const lgs_view *__restrict__ views,
+                                                             int n_views, uint32_t total_tiles,
+                                                             uint32_t *counter) {
+    __shared__ RasterSmem sm;
     __shared__ uint32_t s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
@@ -526,19 +542,16 @@ __global__ void __launch_bounds__(kBatch) k_raster_fwd_batch(const lgs_view *__r
         const lgs_view &V = views[v];
         const RCam K = view_rcam(V);
         fwd_tile<PREC>(V.rec, V.vals, V.tile_ranges, K, (int)(t - V.tile_offset), V.image,
-                       V.final_T, V.last_contrib, s_sp, s_fl);
+                       V.final_T, V.last_contrib, sm);
         __syncthreads();
     }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kBatch) k_raster_bwd_batch(const lgs_view *__restrict__ views,
-                                                           int n_views, uint32_t total_tiles,
-                                                           uint32_t *counter) {
-    __shared__ SplatS s_sp[kBatch];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ uint8_t s_fl[kBatch];
-    __shared__ int s_maxlast;
+__global__ void __launch_bounds__(kBwdThreads) k_raster_bwd_batch(const lgs_view *__restrict__ views,
+                                                             int n_views, uint32_t total_tiles,
+                                                             uint32_t *counter) {
+    __shared__ RasterSmem sm;
     __shared__ uint32_t s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
@@ -549,7 +562,7 @@ __global__ void __launch_bounds__(kBatch) k_raster_bwd_batch(const lgs_view *__r
         const lgs_view &V = views[v];
         const RCam K = view_rcam(V);
         bwd_tile<PREC>(V.rec, V.vals, V.tile_ranges, K, (int)(t - V.tile_offset), V.final_T,
-                       V.last_contrib, V.dL_dimage, V.grad_acc, s_sp, s_id, s_fl, s_maxlast);
+                       V.last_contrib, V.dL_dimage, V.grad_acc, sm);
         __syncthreads();
     }
 }
@@ -611,13 +624,13 @@ lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
     count_launch();
     switch (precision) {
         case LGS_FP32:
-            k_raster_fwd<LGS_FP32><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+            k_raster_fwd<LGS_FP32><<<grid, kFwdThreads, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
             break;
         case LGS_MIXED_FP16:
-            k_raster_fwd<LGS_MIXED_FP16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+            k_raster_fwd<LGS_MIXED_FP16><<<grid, kFwdThreads, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
             break;
         case LGS_MIXED_BF16:
-            k_raster_fwd<LGS_MIXED_BF16><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
+            k_raster_fwd<LGS_MIXED_BF16><<<grid, kFwdThreads, 0, s>>>(sp->rec, vals, ranges, K, image, finalT, last);
             break;
         default:
             return LGS_ERR_INVALID_ARG;
@@ -636,7 +649,7 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
     const RCam K = make_rcam(cam, tw, th);
     const unsigned grid = (unsigned)K.ntiles;
     count_launch();
-#define LGS_RBW(P) k_raster_bwd<P><<<grid, kBatch, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc)
+#define LGS_RBW(P) k_raster_bwd<P><<<grid, kBwdThreads, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc)
     switch (precision) {
         case LGS_FP32: LGS_RBW(LGS_FP32); break;
         case LGS_MIXED_FP16: LGS_RBW(LGS_MIXED_FP16); break;
@@ -654,15 +667,15 @@ lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles
     cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     int per_sm = 0;
     if (backward)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd_batch<LGS_FP32>, kBatch, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd_batch<LGS_FP32>, kBwdThreads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd_batch<LGS_FP32>, kBatch, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd_batch<LGS_FP32>, kFwdThreads, 0);
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(total_tiles < cap ? total_tiles : cap);
     if (grid == 0) return LGS_OK;
     count_launch();
-#define LGS_RB(P) do { if (backward) k_raster_bwd_batch<P><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); \
-                       else k_raster_fwd_batch<blend_of(P)><<<grid, kBatch, 0, s>>>(views, n_views, total_tiles, counter); } while (0)
+#define LGS_RB(P) do { if (backward) k_raster_bwd_batch<P><<<grid, kBwdThreads, 0, s>>>(views, n_views, total_tiles, counter); \
+                       else k_raster_fwd_batch<blend_of(P)><<<grid, kFwdThreads, 0, s>>>(views, n_views, total_tiles, counter); } while (0)
     switch (precision) {
         case LGS_MIXED_FP16: LGS_RB(LGS_MIXED_FP16); break;
         case LGS_MIXED_BF16: LGS_RB(LGS_MIXED_BF16); break;
