@@ -15,6 +15,8 @@ fragment is stored between the two passes.
 
 Every call returns fresh output and saved buffers from torch's caching
 allocator, so several forwards may be pending before their backwards run.
+The backward reads the forward's pair count (one host synchronisation) and
+raises LgsError if the binning needed more pairs than `pair_capacity`.
 The optional `metric` tensor [n] receives the densification statistic
 C Var = S - M^2/C (Sec. 3.3) of the visible Gaussians when backward runs;
 rows of culled clusters are left as they are.
@@ -91,14 +93,22 @@ class _Rasterize(torch.autograd.Function):
         B.lgs_raster_fwd(sp, vals, ranges, cs, tw, th, image, final_T, last,
                          precision=PRECISIONS[r.precision])
         ctx.r, ctx.cs, ctx.metric = r, cs, metric
-        ctx.save_for_backward(planes, rowmap, d_V, rec, depth, radius, vals, ranges, final_T, last)
+        ctx.save_for_backward(planes, rowmap, d_V, rec, depth, radius, vals, ranges, final_T, last,
+                              d_P)
         ctx.mark_non_differentiable(final_T)
         return image
 
     @staticmethod
     def backward(ctx, dL_dimage):
-        planes, rowmap, d_V, rec, depth, radius, vals, ranges, final_T, last = ctx.saved_tensors
+        planes, rowmap, d_V, rec, depth, radius, vals, ranges, final_T, last, d_P = ctx.saved_tensors
         r, cs = ctx.r, ctx.cs
+        # the binning writes at most r.cap pairs; more means the forward's
+        # tile lists were cut and neither its image nor these gradients hold
+        # (one host read of the pair count per backward)
+        P = int(d_P.item())
+        if P > r.cap:
+            raise B.LgsError(f"tile binning needed {P} pairs but pair_capacity is {r.cap}; "
+                             "construct GaussianRasterizer with a larger pair_capacity")
         tw, th = r.tile
         sp = B.splats_struct(rec, depth, radius)
         gacc = torch.empty((r.n, B.GRAD_FLOATS), dtype=torch.float32, device=r.dev)

@@ -76,6 +76,11 @@ class StepConfig:
     ccc: bool = True
     # raster blend precision: B.LGS_FP32, LGS_MIXED_FP16 or LGS_MIXED_BF16
     precision: int = 0
+    # every this many steps, step() reads the binning's overflow flag (a
+    # host synchronisation; skipped while a CUDA graph is being captured)
+    # and raises if any binning since the last read needed more pairs than
+    # pair_capacity: the tile lists were then truncated (0: never)
+    overflow_check_every: int = 64
 
 
 class Trainer:
@@ -265,15 +270,31 @@ class Trainer:
             self.n = n
             self.step_count = int(z["step_count"])
 
+    def check_overflow(self) -> None:
+        """Raises LgsError if a binning since the last check needed more
+        (tile, splat) pairs than the pair capacity: its tile lists were cut
+        at the capacity, so images and gradients of those steps were wrong.
+        Reads the library's overflow flag, which synchronises the device and
+        clears the flag (it is shared by every caller in the process)."""
+        needed = B.lgs_get_overflow()
+        if needed:
+            raise B.LgsError(f"tile binning needed {needed} pairs but pair_capacity is {self.cap}; "
+                             "raise StepConfig.pair_capacity")
+
     def step(self, cam: dict | B.LgsCamera, target: torch.Tensor, reorder: bool = True,
              fused: bool = True):
-        """One full training step a1..a10."""
+        """One full training step a1..a10 (and, every
+        cfg.overflow_check_every steps outside graph capture, the overflow
+        check of check_overflow())."""
         if reorder:
             self.morton_reorder()
         cs = cam if isinstance(cam, B.LgsCamera) else B.camera_struct(cam)
         self.render(None, cs)
         self.backward(cs, target)
         self.optimize(cs, fused=fused)
+        every = self.cfg.overflow_check_every
+        if every and self.step_count % every == 0 and not torch.cuda.is_current_stream_capturing():
+            self.check_overflow()
         return self.loss
 
 

@@ -75,3 +75,28 @@ def test_iteration_captured_in_a_cuda_graph():
     # the two runs' float atomics cannot flip a sign
     close = np.abs(a - b) <= 1e-6 + 1e-6 * np.abs(a)
     assert close.mean() > 0.999
+
+
+def test_pair_overflow_raises_in_training_and_autograd():
+    """A pair capacity below what the binning needs cuts the tile lists; the
+    Trainer's periodic check and the autograd backward both raise instead of
+    training on them, and a large enough capacity trains normally."""
+    from paper_2503_01199_gb300 import autograd as AG
+    d = scenegen.uniform_box_scene(3000, 0, 31, 96, 96, focal=96.0)
+    tgt = U.t(d["target"])
+    B.lgs_get_overflow()                      # clear the shared flag
+    tr = PL.Trainer(d["scene"], 96, 96, PL.StepConfig(pair_capacity=100, overflow_check_every=1))
+    with pytest.raises(B.LgsError, match="pair_capacity"):
+        tr.step(d["camera"], tgt, reorder=False)
+    ok = PL.Trainer(d["scene"], 96, 96, PL.StepConfig(overflow_check_every=1))
+    ok.step(d["camera"], tgt, reorder=False)
+    planes, n = U.planes_tensor(d["scene"])
+    small = AG.GaussianRasterizer(n, 0, 96, 96, pair_capacity=100)
+    img = AG.rasterize(planes.requires_grad_(True), d["camera"], small)
+    with pytest.raises(B.LgsError, match="pair_capacity"):
+        img.sum().backward()
+    B.lgs_get_overflow()
+    big = AG.GaussianRasterizer(n, 0, 96, 96)
+    planes.grad = None
+    AG.rasterize(planes, d["camera"], big).sum().backward()
+    assert planes.grad is not None and torch.isfinite(planes.grad).all()
