@@ -112,6 +112,7 @@ def lib():
             "or_tile_reachable": (None, [i64, P, P, P, P, P, P, i32, i32, P]),
             "or_tile_near_pairs": (i64, [i64, P, P, P, P, P, i32, i32, i32, i32, i64, P]),
             "or_set_tau_margin": (None, [f64]),
+            "or_set_threads": (i32, [i32]),
             "or_opacity_decay": (None, [i64, P]),
             "or_moments_accumulate": (None, [i64, P, P, P, P, P, P, P]),
         }
@@ -144,12 +145,18 @@ def set_margins(alpha: float, T: float, px: float, radius: float, depth: float) 
 
 
 def threads() -> int:
-    """Threads the oracle uses (OpenMP default, else 1)."""
+    """Threads the oracle uses (OpenMP's current setting, else 1)."""
     lib()
     if not OMP:
         return 1
-    n = os.environ.get("OMP_NUM_THREADS")
-    return int(n) if n else (os.cpu_count() or 1)
+    return int(_lib.or_set_threads(-1))
+
+
+def set_threads(n: int | None) -> int:
+    """Use n threads in the oracle's parallel loops (None: all processors);
+    returns the number in use."""
+    lib()
+    return int(_lib.or_set_threads(int(n) if n else 0))
 
 
 def _p(a: np.ndarray):

@@ -26,6 +26,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -57,6 +60,19 @@ void or_set_margins(double alpha, double T, double px, double radius, double dep
 }
 
 int or_version(void) { return 1; }
+
+/* Threads of the OpenMP loops: n > 0 sets n, n = 0 the number of
+ * processors, n < 0 only queries; returns the number in use. Only the
+ * parallel split changes, never the arithmetic. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 0) omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* camera                                                                   */

@@ -29,10 +29,18 @@ def test_reference_arm_prints_one_line_of_the_bench_metric():
     assert out["impl"] == "reference"
     assert out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
     assert out["higher_is_better"] is True and out["steps"] == 1 and out["warmup"] == 1
-    assert out["config"]["workload"] == bench.WORKLOAD
+    assert out["config"] == bench.bench_config(1)
     assert out["value"] > 0 and out["ms_per_step"] > 0
+    # the line says what it measured: sampled time per step, and the full
+    # iteration's rate extrapolated from it
+    assert out["extrapolated"] is True
+    ex = out["extrapolation"]
+    assert ex["sampled_ms_per_step"] == out["ms_per_step"]
+    assert abs(1e3 / ex["full_iteration_ms"] - out["value"]) <= 0.01 * out["value"]
+    assert ex["full_iteration_ms"] > out["ms_per_step"] and ex["tiles_per_step"] == 64
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1
+    assert cb["extrapolated"] is True
     assert cb["unit"] == bench.UNIT and cb["sample"]
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["unit"] == bench.UNIT
