@@ -371,7 +371,10 @@ def run_gpu(args) -> dict | None:
     target = torch.from_numpy(tgt_np).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(events=None, precision=B.LGS_FP32, reorder=False):
+    det_ws = None
+
+    def step(events=None, precision=B.LGS_FP32, reorder=False, deterministic=False):
+        nonlocal det_ws
         def mark(i):
             if events is not None:
                 events[i].record(stream)
@@ -393,8 +396,16 @@ def run_gpu(args) -> dict | None:
         mark(5)
         B.lgs_loss_l1(tr.image, target, tr.dLdI, tr.loss)
         mark(6)
-        B.lgs_raster_bwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.finalT, tr.last,
-                         tr.dLdI, tr.gacc, precision=precision)
+        if deterministic:  # bit-reproducible accumulation (fixed-point limbs)
+            if det_ws is None:
+                det_ws = torch.empty(B.lgs_raster_bwd_det_workspace_size(tr.gacc.shape[0]),
+                                     dtype=torch.uint8, device=dev)
+            B.lgs_raster_bwd_deterministic(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1],
+                                           tr.finalT, tr.last, tr.dLdI, tr.gacc, det_ws,
+                                           precision=precision)
+        else:
+            B.lgs_raster_bwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.finalT,
+                             tr.last, tr.dLdI, tr.gacc, precision=precision)
         mark(7)
         B.lgs_opacity_variance(tr.gacc, tr.rowmap, tr.d_V, tr.n, tr.metric)
         mark(8)
@@ -466,17 +477,20 @@ def run_gpu(args) -> dict | None:
     e2e_ms = e0.elapsed_time(e1)
     # ---- the same step with the mixed-precision raster (FP16 / BF16 blend)
     mixed = {}
-    for name, prec in (("fp16", B.LGS_MIXED_FP16), ("bf16", B.LGS_MIXED_BF16),
-                       ("fp32_warp_reduce_int", B.LGS_FP32 | B.LGS_WARP_REDUCE_INT)):
+    for name, prec, dm in (("fp16", B.LGS_MIXED_FP16, False), ("bf16", B.LGS_MIXED_BF16, False),
+                           ("fp32_warp_reduce_int", B.LGS_FP32 | B.LGS_WARP_REDUCE_INT, False),
+                           ("fp32_deterministic", B.LGS_FP32, True),
+                           ("fp32_warp_reduce_int_deterministic",
+                            B.LGS_FP32 | B.LGS_WARP_REDUCE_INT, True)):
         for _ in range(2):
-            step(precision=prec)
+            step(precision=prec, deterministic=dm)
         mev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
         torch.cuda.synchronize()
         m0 = torch.cuda.Event(enable_timing=True)
         m1 = torch.cuda.Event(enable_timing=True)
         m0.record(stream)
         for k in range(args.steps):
-            step(mev[k], precision=prec)
+            step(mev[k], precision=prec, deterministic=dm)
         m1.record(stream)
         torch.cuda.synchronize()
         mms = m0.elapsed_time(m1)

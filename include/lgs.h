@@ -354,7 +354,8 @@ lgs_status lgs_loss_l1(const float *image, const float *target, int64_t n, float
  *   dL/dc = alpha T dL/dI,
  *   dL/dalpha = T (c - acc) . dL/dI - T_final bg . dL/dI / (1 - alpha),
  * acc = colour composited behind. Per splat the per-pixel terms are summed
- * within the tile before one atomic add per value per tile.
+ * over each 8 x 8 quadrant of the tile (a warp's reduction) before one
+ * atomic add per value: up to four atomics per value per tile.
  * grad_acc (device) [max_splats][16] floats, row j:
  *   0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 do (activated opacity), 6..8 dr dg db,
  *   9 S = sum of (dL/do per pixel)^2, 10 M = sum of dL/do per pixel,
@@ -368,6 +369,38 @@ lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
                           int32_t tile_h, int32_t precision, const float *final_T,
                           const int32_t *last_contrib, const float *dL_dimage, float *grad_acc,
                           int64_t max_splats, int32_t accumulate, lgs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * a7, bit-reproducible (the accumulation of Sec. 3.1's integer warp
+ * reduction carried through to the gradient rows). The same gradients and
+ * moments as lgs_raster_bwd, but every (quadrant, splat) contribution is
+ * added to its splat as an exact integer in units of 2^-96 (128-bit two's
+ * complement, kept as three 64-bit limbs in the workspace) instead of by a
+ * float atomic, so the result does not depend on the order in which the
+ * GPU's warps add to a row: two calls on the same inputs give identical
+ * bits. With LGS_WARP_REDUCE_INT the warp's exact integer sum is added as
+ * it is, so the only error beyond the per-fragment FP32 arithmetic is the
+ * integer reduction's truncation (at most 2^-25 of the warp's largest term
+ * per lane) and the final rounding of each value to FP32.
+ * grad_acc rows j < max_splats are OVERWRITTEN (no accumulate option); the
+ * row layout is lgs_raster_bwd's. workspace (device, 16-byte aligned, any
+ * contents) of lgs_raster_bwd_det_workspace_size(max_splats) bytes =
+ * 240 bytes per row. A contribution of magnitude >= 2^30 is left out and
+ * counted (lgs_get_det_overflow). Errors: LGS_ERR_INVALID_ARG for the
+ * arguments lgs_raster_bwd rejects or a workspace that is too small.
+ * ---------------------------------------------------------------------- */
+size_t lgs_raster_bwd_det_workspace_size(int64_t max_splats);
+lgs_status lgs_raster_bwd_deterministic(const lgs_splats *sp, const uint32_t *vals,
+                                        const uint32_t *tile_ranges, const lgs_camera *cam,
+                                        int32_t tile_w, int32_t tile_h, int32_t precision,
+                                        const float *final_T, const int32_t *last_contrib,
+                                        const float *dL_dimage, float *grad_acc,
+                                        int64_t max_splats, void *workspace,
+                                        size_t workspace_bytes, lgs_stream stream);
+/* Synchronises the device; *count receives the number of contributions
+ * lgs_raster_bwd_deterministic left out as out of range since the last
+ * query, and the count is cleared. LGS_ERR_CAPACITY if non-zero. */
+lgs_status lgs_get_det_overflow(uint32_t *count);
 
 /* ------------------------------------------------------------------------
  * a8. Densification metric (Sec. 3.3): C Var = S - M^2 / C (0 if C = 0) for

@@ -30,7 +30,9 @@ ENTRY_POINTS = (
     "lgs_compact_gather", "lgs_preprocess",
     "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_get_wait_timeouts",
     "lgs_raster_fwd",
-    "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd", "lgs_opacity_variance", "lgs_preprocess_bwd",
+    "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd",
+    "lgs_raster_bwd_det_workspace_size", "lgs_raster_bwd_deterministic", "lgs_get_det_overflow",
+    "lgs_opacity_variance", "lgs_preprocess_bwd",
     "lgs_adam_step", "lgs_preprocess_bwd_adam", "lgs_moments_accumulate", "lgs_moments_metric",
     "lgs_densify_workspace_size", "lgs_densify", "lgs_opacity_decay",
 )
@@ -109,6 +111,10 @@ def load(build_if_missing: bool = True):
         "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P]),
         "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
         "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P, i64, i32, P]),
+        "lgs_raster_bwd_det_workspace_size": (sz, [i64]),
+        "lgs_raster_bwd_deterministic": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P, i64, P, sz,
+                                                P]),
+        "lgs_get_det_overflow": (i32, [P]),
         "lgs_opacity_variance": (i32, [P, P, P, i64, P, P]),
         "lgs_preprocess_bwd": (i32, [P, P, P, P, P, P, i32, P]),
         "lgs_raster_fwd_batch": (i32, [P, i32, u32, i32, P, P]),
@@ -358,6 +364,31 @@ def lgs_raster_bwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, til
                             tile_w, tile_h, int(precision), _ptr(final_T), _ptr(last_contrib),
                             _ptr(dL_dimage), _ptr(grad_acc), grad_acc.shape[0],
                             int(bool(accumulate)), _stream(stream)), "lgs_raster_bwd")
+
+
+def lgs_raster_bwd_det_workspace_size(max_splats: int) -> int:
+    return int(load().lgs_raster_bwd_det_workspace_size(int(max_splats)))
+
+
+def lgs_raster_bwd_deterministic(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h,
+                                 final_T, last_contrib, dL_dimage, grad_acc, workspace,
+                                 stream=None, precision=LGS_FP32):
+    L = load()
+    _check(L.lgs_raster_bwd_deterministic(
+        ctypes.byref(sp), _ptr(vals), _ptr(tile_ranges), ctypes.byref(cam), tile_w, tile_h,
+        int(precision), _ptr(final_T), _ptr(last_contrib), _ptr(dL_dimage), _ptr(grad_acc),
+        grad_acc.shape[0], _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream)), "lgs_raster_bwd_deterministic")
+
+
+def lgs_get_det_overflow() -> int:
+    """Contributions the deterministic backward left out as out of range."""
+    L = load()
+    count = ctypes.c_uint32(0)
+    st = L.lgs_get_det_overflow(ctypes.byref(count))
+    if st not in (LGS_OK, LGS_ERR_CAPACITY):
+        _check(st, "lgs_get_det_overflow")
+    return int(count.value)
 
 
 def lgs_opacity_variance(grad_acc, map_, d_num_visible, max_rows, metric, stream=None):

@@ -47,6 +47,12 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
                       const lgs_camera *cam, int tw, int th, int precision, const float *finalT,
                       const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
                       int accumulate, cudaStream_t s);
+size_t raster_bwd_det_workspace_size(int64_t max_splats);
+lgs_status raster_bwd_det(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
+                          const lgs_camera *cam, int tw, int th, int precision, const float *finalT,
+                          const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
+                          void *ws, size_t ws_bytes, cudaStream_t s);
+lgs_status det_overflow(uint32_t *count);
 lgs_status loss_l1(const float *img, const float *tgt, int64_t n, float *g, float *loss,
                    cudaStream_t s);
 lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles, int precision,
@@ -285,6 +291,33 @@ lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
     return raster_bwd(sp, vals, tile_ranges, cam, tile_w, tile_h, precision, final_T,
                       last_contrib, dL_dimage, grad_acc, max_splats, accumulate,
                       as_stream(stream));
+}
+
+size_t lgs_raster_bwd_det_workspace_size(int64_t max_splats) {
+    return raster_bwd_det_workspace_size(max_splats);
+}
+
+lgs_status lgs_raster_bwd_deterministic(const lgs_splats *sp, const uint32_t *vals,
+                                        const uint32_t *tile_ranges, const lgs_camera *cam,
+                                        int32_t tile_w, int32_t tile_h, int32_t precision,
+                                        const float *final_T, const int32_t *last_contrib,
+                                        const float *dL_dimage, float *grad_acc,
+                                        int64_t max_splats, void *workspace,
+                                        size_t workspace_bytes, lgs_stream stream) {
+    if (bad_camera(cam) || bad_splats(sp, 0) || !vals || !tile_ranges || !final_T ||
+        !last_contrib || !dL_dimage || !grad_acc || !aligned16(grad_acc) || max_splats < 0 ||
+        !aligned16(workspace) || bad_tiles(cam, tile_w, tile_h) ||
+        (precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 ||
+        (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
+        return LGS_ERR_INVALID_ARG;
+    return raster_bwd_det(sp, vals, tile_ranges, cam, tile_w, tile_h, precision, final_T,
+                          last_contrib, dL_dimage, grad_acc, max_splats, workspace,
+                          workspace_bytes, as_stream(stream));
+}
+
+lgs_status lgs_get_det_overflow(uint32_t *count) {
+    if (!count) return LGS_ERR_INVALID_ARG;
+    return det_overflow(count);
 }
 
 lgs_status lgs_opacity_variance(const float *grad_acc, const uint32_t *map,

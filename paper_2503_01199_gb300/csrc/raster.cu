@@ -64,8 +64,10 @@ struct RCam {
 
 // PREC = blend precision (LGS_FP32 / LGS_MIXED_FP16 / LGS_MIXED_BF16),
 // optionally | LGS_WARP_REDUCE_INT for the backward's warp sums.
+constexpr int kDetFlag = 64;  // internal: fixed-point accumulation (deterministic backward)
 constexpr int blend_of(int prec) { return prec & 3; }
 constexpr bool int_reduce(int prec) { return (prec & LGS_WARP_REDUCE_INT) != 0; }
+constexpr bool det_of(int prec) { return (prec & kDetFlag) != 0; }
 
 template <int PREC>
 __device__ __forceinline__ uint32_t pack_pair(float x) {
@@ -337,17 +339,114 @@ __device__ __forceinline__ int scatter12_index(int lane) {
 
 // Warp sum by the integer warp reduction of Sec. 3.1: the largest exponent
 // (warp max), every value scaled to an integer aligned to it (26 bits, so
-// that 32 of them cannot overflow 32 bits), an exact integer warp sum, and
-// the float result rebuilt. Truncation costs at most 2^-25 of the largest
-// term per lane; the sum does not depend on the order of the lanes.
-__device__ __forceinline__ float warp_sum_int(float x) {
+// that 32 of them cannot overflow 32 bits), an exact integer warp sum: the
+// sum is tot 2^(emax - 152) (0 when emax < 26, every |x| < 2^-100).
+// Truncation costs at most 2^-25 of the largest term per lane; the sum does
+// not depend on the order of the lanes.
+__device__ __forceinline__ void warp_sum_int(float x, int &tot, uint32_t &emax) {
     const uint32_t e = (__float_as_uint(x) >> 23) & 0xffu;
-    const uint32_t emax = __reduce_max_sync(0xffffffffu, e);
-    if (emax < 26u) return 0.0f;  // every |x| < 2^-100
+    emax = __reduce_max_sync(0xffffffffu, e);
+    tot = 0;
+    if (emax < 26u) return;
     const float up = __uint_as_float((279u - emax) << 23);  // 2^(152 - emax)
-    const int q = __float2int_rz(x * up);
-    const int tot = __reduce_add_sync(0xffffffffu, q);
-    return (float)tot * __uint_as_float((emax - 25u) << 23);  // 2^(emax - 152)
+    tot = __reduce_add_sync(0xffffffffu, __float2int_rz(x * up));
+}
+
+__device__ __forceinline__ float int_sum_value(int tot, uint32_t emax) {
+    return emax < 26u ? 0.0f : (float)tot * __uint_as_float((emax - 25u) << 23);  // 2^(emax - 152)
+}
+
+// ---------------------------------------------------------------------------
+// Order-independent accumulation (lgs_raster_bwd_deterministic). Every
+// contribution M 2^k (M a signed integer: a float's significand, or the
+// integer warp sum of Sec. 3.1's reduction with its exponent) is added as
+// the exact 128-bit two's-complement integer N = M 2^(k + 96), i.e. in units
+// of 2^-96, split into three limbs: bits 0-31 and bits 32-63 each summed in
+// its own unsigned 64-bit word (2^32 contributions cannot overflow it) and
+// bits 64-127 summed modulo 2^64 in a third word. Integer addition commutes,
+// so the limbs, and the value they make, do not depend on the order in
+// which tiles and quadrants add to a splat. A contribution whose N would
+// need more than 126 bits (|value| >= 2^30) is counted in g_det_overflow and
+// left out; bits below 2^-96 are truncated toward zero.
+// ---------------------------------------------------------------------------
+constexpr int kDetValues = 10;  // du dv dA dB dC do dr dg db S (M = do; C is an integer)
+constexpr int kDetLimbs = 3;
+
+__device__ unsigned int g_det_overflow;
+
+__device__ __forceinline__ void fixed_add(unsigned long long *acc, long long M, int k) {
+    if (M == 0) return;
+    const bool neg = M < 0;
+    const uint64_t mag = neg ? (uint64_t)(-M) : (uint64_t)M;
+    const int sh = k + 96;
+    uint64_t lo, hi;
+    if (sh >= 0) {
+        if (64 - __clzll((long long)mag) + sh > 126) {
+            atomicAdd(&g_det_overflow, 1u);
+            return;
+        }
+        if (sh == 0) {
+            lo = mag;
+            hi = 0;
+        } else if (sh < 64) {
+            lo = mag << sh;
+            hi = mag >> (64 - sh);
+        } else {
+            lo = 0;
+            hi = mag << (sh - 64);
+        }
+    } else {
+        if (sh <= -64) return;
+        lo = mag >> (-sh);
+        hi = 0;
+        if (lo == 0) return;
+    }
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    atomicAdd(acc, (unsigned long long)(lo & 0xffffffffull));
+    atomicAdd(acc + 1, (unsigned long long)(lo >> 32));
+    atomicAdd(acc + 2, (unsigned long long)hi);
+}
+
+// A float x = M 2^k exactly (M its signed significand).
+__device__ __forceinline__ void fixed_add_float(unsigned long long *acc, float x) {
+    const uint32_t b = __float_as_uint(x);
+    const int E = (int)((b >> 23) & 0xffu);
+    if (E == 255) {
+        atomicAdd(&g_det_overflow, 1u);
+        return;
+    }
+    const long long m = E ? (long long)((b & 0x7fffffu) | 0x800000u) : (long long)(b & 0x7fffffu);
+    fixed_add(acc, (b >> 31) ? -m : m, (E ? E : 1) - 150);
+}
+
+// Rows of grad_acc from the limbs: for every row j < rows, value v of the
+// kDetValues is (limb0 + limb1 2^32 + limb2 2^64) 2^-96 taken as a signed
+// 128-bit integer, rounded to double (exactly enough: the magnitude's two
+// 64-bit halves are converted separately) and then to float; M = do.
+__global__ void __launch_bounds__(256) k_det_finalize(const unsigned long long *__restrict__ acc,
+                                                     int64_t rows, float *__restrict__ gacc) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < rows;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long *a = acc + (size_t)j * (kDetValues * kDetLimbs);
+        float *row = gacc + 16 * j;
+#pragma unroll
+        for (int v = 0; v < kDetValues; ++v) {
+            const uint64_t l0 = a[kDetLimbs * v], l1 = a[kDetLimbs * v + 1], l2 = a[kDetLimbs * v + 2];
+            uint64_t lo = l0 + (l1 << 32);
+            uint64_t hi = l2 + (l1 >> 32) + (lo < l0 ? 1ull : 0ull);
+            const bool neg = (int64_t)hi < 0;
+            if (neg) {
+                lo = ~lo + 1ull;
+                hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+            }
+            const double d = ((double)hi * 18446744073709551616.0 + (double)lo) * 0x1p-96;
+            row[v] = (float)(neg ? -d : d);
+        }
+        row[10] = row[5];
+    }
 }
 
 // One tile of the backward pass, by the whole CTA (kBwdThreads): warp w
@@ -360,7 +459,7 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                                          int tile, const float *__restrict__ finalT,
                                          const int32_t *__restrict__ last,
                                          const float *__restrict__ dLdI, float *__restrict__ gacc,
-                                         RasterSmem &sm) {
+                                         unsigned long long *__restrict__ det, RasterSmem &sm) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
     const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
@@ -467,28 +566,44 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                 v[10] = dO;
                 v[11] = n;
                 float *row = gacc + 16 * (int64_t)s.id;
+                unsigned long long *drow = det + (size_t)s.id * (kDetValues * kDetLimbs);
                 if constexpr (int_reduce(PREC)) {
                     const int mi = lane >> 1;
-                    float mine = 0.f;
+                    int mt = 0;
+                    uint32_t me = 0;
 #pragma unroll
                     for (int i = 0; i < 10; ++i) {
-                        const float t = warp_sum_int(v[i]);
-                        if (mi == i || (i == 5 && mi == 10)) mine = t;  // M = the opacity sum
+                        int t;
+                        uint32_t e;
+                        warp_sum_int(v[i], t, e);
+                        if (mi == i || (i == 5 && mi == 10)) {  // M = the opacity sum
+                            mt = t;
+                            me = e;
+                        }
                     }
                     const uint32_t cnt_w = __reduce_add_sync(0xffffffffu, (uint32_t)n);
                     if ((lane & 1) == 0) {
-                        if (mi < 11)
-                            atomicAdd(row + mi, mine);
-                        else if (mi == 11)
+                        if (mi < 11) {
+                            if constexpr (det_of(PREC)) {
+                                if (mi < kDetValues && me >= 26u)
+                                    fixed_add(drow + kDetLimbs * mi, (long long)mt, (int)me - 152);
+                            } else {
+                                atomicAdd(row + mi, int_sum_value(mt, me));
+                            }
+                        } else if (mi == 11) {
                             atomicAdd(reinterpret_cast<unsigned int *>(row + 11), cnt_w);
+                        }
                     }
                 } else {
                     const float red = warp_reduce_scatter12(v, lane);
                     if ((lane & 1) == 0 && vi >= 0) {
-                        if (vi < 11)
-                            atomicAdd(row + vi, red);
-                        else
+                        if (vi == 11)
                             atomicAdd(reinterpret_cast<unsigned int *>(row + 11), (unsigned int)red);
+                        else if constexpr (det_of(PREC)) {
+                            if (vi < kDetValues) fixed_add_float(drow + kDetLimbs * vi, red);
+                        } else {
+                            atomicAdd(row + vi, red);
+                        }
                     }
                 }
             }
@@ -500,9 +615,10 @@ template <int PREC>
 __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ ranges, RCam K, const float *__restrict__ finalT,
-    const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc) {
+    const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc,
+    unsigned long long *__restrict__ det) {
     __shared__ RasterSmem sm;
-    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, sm);
+    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, det, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -562,7 +678,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd_batch(const lgs_view
         const lgs_view &V = views[v];
         const RCam K = view_rcam(V);
         bwd_tile<PREC>(V.rec, V.vals, V.tile_ranges, K, (int)(t - V.tile_offset), V.final_T,
-                       V.last_contrib, V.dL_dimage, V.grad_acc, sm);
+                       V.last_contrib, V.dL_dimage, V.grad_acc, nullptr, sm);
         __syncthreads();
     }
 }
@@ -649,7 +765,7 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
     const RCam K = make_rcam(cam, tw, th);
     const unsigned grid = (unsigned)K.ntiles;
     count_launch();
-#define LGS_RBW(P) k_raster_bwd<P><<<grid, kBwdThreads, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc)
+#define LGS_RBW(P) k_raster_bwd<P><<<grid, kBwdThreads, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc, nullptr)
     switch (precision) {
         case LGS_FP32: LGS_RBW(LGS_FP32); break;
         case LGS_MIXED_FP16: LGS_RBW(LGS_MIXED_FP16); break;
@@ -660,6 +776,58 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
     }
 #undef LGS_RBW
     return check_launch();
+}
+
+size_t raster_bwd_det_workspace_size(int64_t max_splats) {
+    return (size_t)(max_splats > 0 ? max_splats : 0) * kDetValues * kDetLimbs *
+           sizeof(unsigned long long);
+}
+
+lgs_status raster_bwd_det(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
+                          const lgs_camera *cam, int tw, int th, int precision, const float *finalT,
+                          const int32_t *last, const float *dLdI, float *gacc, int64_t max_splats,
+                          void *ws, size_t ws_bytes, cudaStream_t s) {
+    if (tw != kTile || th != kTile) return LGS_ERR_INVALID_ARG;
+    if ((precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 || (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
+        return LGS_ERR_INVALID_ARG;
+    const size_t need = raster_bwd_det_workspace_size(max_splats);
+    if (ws_bytes < need || (need && !ws)) return LGS_ERR_INVALID_ARG;
+    unsigned long long *det = static_cast<unsigned long long *>(ws);
+    cudaMemsetAsync(gacc, 0, (size_t)max_splats * 16 * sizeof(float), s);
+    cudaMemsetAsync(det, 0, need, s);
+    const RCam K = make_rcam(cam, tw, th);
+    const unsigned grid = (unsigned)K.ntiles;
+    count_launch();
+#define LGS_RBD(P) k_raster_bwd<(P) | kDetFlag><<<grid, kBwdThreads, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc, det)
+    switch (precision) {
+        case LGS_FP32: LGS_RBD(LGS_FP32); break;
+        case LGS_MIXED_FP16: LGS_RBD(LGS_MIXED_FP16); break;
+        case LGS_MIXED_BF16: LGS_RBD(LGS_MIXED_BF16); break;
+        case LGS_FP32 | LGS_WARP_REDUCE_INT: LGS_RBD(LGS_FP32 | LGS_WARP_REDUCE_INT); break;
+        case LGS_MIXED_FP16 | LGS_WARP_REDUCE_INT: LGS_RBD(LGS_MIXED_FP16 | LGS_WARP_REDUCE_INT); break;
+        default: LGS_RBD(LGS_MIXED_BF16 | LGS_WARP_REDUCE_INT); break;
+    }
+#undef LGS_RBD
+    lgs_status st = check_launch();
+    if (st != LGS_OK) return st;
+    if (max_splats > 0) {
+        count_launch();
+        k_det_finalize<<<grid_for(max_splats, 256), 256, 0, s>>>(det, max_splats, gacc);
+        st = check_launch();
+    }
+    return st;
+}
+
+lgs_status det_overflow(uint32_t *count) {
+    unsigned int h = 0, zero = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(&h, g_det_overflow, sizeof(h)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_det_overflow, &zero, sizeof(zero)) != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    *count = h;
+    return h ? LGS_ERR_CAPACITY : LGS_OK;
 }
 
 lgs_status raster_batch(const lgs_view *views, int n_views, uint32_t total_tiles, int precision,

@@ -138,6 +138,9 @@ def gpu_raster(sp: dict, cam: dict, tile=(16, 16), dLdI=None, cull=1, precision=
     out.update(image=image.cpu().numpy(), T=T.cpu().numpy(), last=last.cpu().numpy(),
                vals=vals.cpu().numpy().view(np.uint32)[:P], ranges=ranges.cpu().numpy().view(np.uint32),
                P=P)
+    # the device buffers, for further calls on the same binning and forward
+    out["dev"] = {"splats": spl, "keep": (rec, d, r), "vals": vals, "ranges": ranges, "T": T,
+                  "last": last, "cam": cs, "n": n}
     return out
 
 

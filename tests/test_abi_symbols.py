@@ -111,3 +111,19 @@ def test_capacity_and_grid_rules_are_checked_on_the_host():
     assert fused(g16, sp) == bad                                     # FP32 colour planes only
     skew = B.LgsGaussians(planes.value, n, stride + 2, deg, B.LGS_SH_F32, None)
     assert fused(skew, sp) == bad                                    # stride a multiple of 4
+
+    # the deterministic backward: its workspace size and the raster rules
+    assert L.lgs_raster_bwd_det_workspace_size(n) == 240 * n
+    img = buf(4 * 128 * 128 * 3)
+    fT, lastc = buf(4 * 128 * 128), buf(4 * 128 * 128)
+    dws = buf(240 * n)
+
+    def det(tw=16, ws_=dws, wsb=240 * n, prec=B.LGS_FP32, gacc_=gacc, rows=n):
+        return L.lgs_raster_bwd_deterministic(ctypes.byref(sp), vals, ranges, ctypes.byref(cam), tw,
+                                              16, prec, fT, lastc, img, gacc_, rows, ws_, wsb, None)
+
+    assert det(wsb=240 * n - 1) == bad                               # workspace too small
+    assert det(ws_=ctypes.c_void_p(dws.value + 8)) == bad            # workspace not 16-byte aligned
+    assert det(tw=8) == bad                                          # 16 x 16 tiles only
+    assert det(prec=3) == bad                                        # unknown precision
+    assert det(gacc_=ctypes.c_void_p(gacc.value + 4)) == bad         # gradient rows unaligned
