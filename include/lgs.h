@@ -64,6 +64,7 @@ typedef int32_t lgs_status;
 #define LGS_ERR_CUDA 3
 #define LGS_ERR_TIMEOUT 4
 #define LGS_ERR_TOO_LARGE 5 /* size beyond a fixed maximum of this library */
+#define LGS_ERR_BOUNDS 6    /* a bounds check of the debug build failed */
 
 typedef void *lgs_stream; /* cudaStream_t */
 
@@ -270,6 +271,37 @@ lgs_status lgs_get_overflow(int64_t *needed);
  * non-zero, else LGS_OK. */
 lgs_status lgs_get_wait_timeouts(uint32_t *count);
 
+/* Synchronises the device and sets how many times a bounded device wait
+ * polls a predecessor that has not published before it gives up (default
+ * LGS_DEFAULT_WAIT_LIMIT; 0 gives up at the first such poll). It exists to
+ * exercise the give-up path in tests: a wait that gives up takes the
+ * partial prefix it has summed, never larger than the true one, so every
+ * position computed from it stays inside its output (the result is wrong
+ * and lgs_get_wait_timeouts reports it) and nothing hangs. No paper
+ * counterpart. */
+#define LGS_DEFAULT_WAIT_LIMIT 4194304u
+lgs_status lgs_set_wait_limit(uint32_t spins);
+
+/* The bounds-checked debug build (liblgs_debug.so, compiled with
+ * -DLGS_DEBUG; no paper counterpart). Its kernels check the indices they
+ * take from their inputs before using them: splat indices of the tile
+ * lists against the splat rows (lgs_splats.capacity) in the raster calls,
+ * gradient rows against max_splats in the backward, the radix sort's
+ * scatter positions against the key count, the Morton gather's source rows
+ * and the compaction-map rows of the preprocess, its backward and the
+ * plain Adam step against the row count. A failed check skips the access
+ * and records its site and source line; the fused backward + Adam call,
+ * the binning and the densification are not checked. lgs_debug_build()
+ * returns 1 in that build, 0 in the release build.
+ * lgs_get_debug_error() synchronises the device; *code = (site << 32) |
+ * line of the first failed check since the last query (0: none), cleared
+ * on read; LGS_ERR_BOUNDS if one failed, else LGS_OK (always LGS_OK in the
+ * release build, whose kernels carry no checks). Sites: 1 tile-list splat
+ * index, 2 gradient row, 3 sort scatter, 4 gather row, 5 preprocess map
+ * row, 6 Adam map row. */
+int32_t lgs_debug_build(void);
+lgs_status lgs_get_debug_error(uint64_t *code);
+
 /* Arithmetic of the per-pixel blend in lgs_raster_fwd / lgs_raster_bwd.
  * LGS_FP32: everything in FP32. LGS_MIXED_FP16 / LGS_MIXED_BF16 (the
  * mixed-precision raster of Sec. 3.1, with BF16 as a second 16-bit type):
@@ -374,18 +406,19 @@ lgs_status lgs_raster_bwd(const lgs_splats *sp, const uint32_t *vals,
  * a7, bit-reproducible (the accumulation of Sec. 3.1's integer warp
  * reduction carried through to the gradient rows). The same gradients and
  * moments as lgs_raster_bwd, but every (quadrant, splat) contribution is
- * added to its splat as an exact integer in units of 2^-96 (128-bit two's
- * complement, kept as three 64-bit limbs in the workspace) instead of by a
+ * added to its splat as an integer in units of 2^-64 (96-bit two's
+ * complement, kept as two 64-bit limbs in the workspace) instead of by a
  * float atomic, so the result does not depend on the order in which the
  * GPU's warps add to a row: two calls on the same inputs give identical
  * bits. With LGS_WARP_REDUCE_INT the warp's exact integer sum is added as
  * it is, so the only error beyond the per-fragment FP32 arithmetic is the
  * integer reduction's truncation (at most 2^-25 of the warp's largest term
- * per lane) and the final rounding of each value to FP32.
+ * per lane), at most 2^-64 per contribution below the unit, and the final
+ * rounding of each value to FP32.
  * grad_acc rows j < max_splats are OVERWRITTEN (no accumulate option); the
  * row layout is lgs_raster_bwd's. workspace (device, 16-byte aligned, any
  * contents) of lgs_raster_bwd_det_workspace_size(max_splats) bytes =
- * 240 bytes per row. A contribution of magnitude >= 2^30 is left out and
+ * 160 bytes per row. A contribution of magnitude >= 2^30 is left out and
  * counted (lgs_get_det_overflow). Errors: LGS_ERR_INVALID_ARG for the
  * arguments lgs_raster_bwd rejects or a workspace that is too small.
  * ---------------------------------------------------------------------- */

@@ -7,6 +7,7 @@ not available, the calls raise.
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 import numpy as np
@@ -16,6 +17,7 @@ from . import build as _build
 
 LGS_OK, LGS_ERR_INVALID_ARG, LGS_ERR_CAPACITY, LGS_ERR_CUDA, LGS_ERR_TIMEOUT = 0, 1, 2, 3, 4
 LGS_ERR_TOO_LARGE = 5
+LGS_ERR_BOUNDS = 6
 LGS_FP32, LGS_MIXED_FP16, LGS_MIXED_BF16 = 0, 1, 2
 LGS_WARP_REDUCE_INT = 16
 LGS_SH_F32, LGS_SH_BF16, LGS_SH_F16 = 0, 1, 2
@@ -28,7 +30,8 @@ ENTRY_POINTS = (
     "lgs_version", "lgs_last_cuda_error", "lgs_kernel_launches", "lgs_morton_workspace_size", "lgs_morton_reorder",
     "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_cluster_cull_compact_noalloc",
     "lgs_compact_gather", "lgs_preprocess",
-    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_get_wait_timeouts",
+    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_get_wait_timeouts", "lgs_set_wait_limit",
+    "lgs_debug_build", "lgs_get_debug_error",
     "lgs_raster_fwd",
     "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd",
     "lgs_raster_bwd_det_workspace_size", "lgs_raster_bwd_deterministic", "lgs_get_det_overflow",
@@ -77,7 +80,9 @@ _lib = None
 
 
 def library_path() -> Path:
-    return _build.LIB
+    """The release library, or the bounds-checked debug build when the
+    environment sets LGS_DEBUG=1 (read when the library is first loaded)."""
+    return _build.DEBUG_LIB if os.environ.get("LGS_DEBUG") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -108,6 +113,9 @@ def load(build_if_missing: bool = True):
         "lgs_bin_sort": (i32, [P, P, i64, P, i32, i32, i32, P, i64, P, P, P, sz, P]),
         "lgs_get_overflow": (i32, [P]),
         "lgs_get_wait_timeouts": (i32, [P]),
+        "lgs_set_wait_limit": (i32, [u32]),
+        "lgs_debug_build": (i32, []),
+        "lgs_get_debug_error": (i32, [P]),
         "lgs_raster_fwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P]),
         "lgs_loss_l1": (i32, [P, P, i64, P, P, P]),
         "lgs_raster_bwd": (i32, [P, P, P, P, i32, i32, i32, P, P, P, P, i64, i32, P]),
@@ -301,6 +309,25 @@ def lgs_get_wait_timeouts() -> int:
     if st not in (LGS_OK, LGS_ERR_TIMEOUT):
         _check(st, "lgs_get_wait_timeouts")
     return int(count.value)
+
+
+def lgs_get_debug_error() -> int:
+    """(site << 32) | line of the first failed bounds check of the debug
+    build since the last query (0: none; always 0 in the release build)."""
+    L = load()
+    code = ctypes.c_uint64(0)
+    st = L.lgs_get_debug_error(ctypes.byref(code))
+    if st not in (LGS_OK, LGS_ERR_BOUNDS):
+        _check(st, "lgs_get_debug_error")
+    return int(code.value)
+
+
+LGS_DEFAULT_WAIT_LIMIT = 4194304
+
+
+def lgs_set_wait_limit(spins: int) -> None:
+    """Polls after which a bounded device wait gives up (testing the give-up path)."""
+    _check(load().lgs_set_wait_limit(int(spins)), "lgs_set_wait_limit")
 
 
 def lgs_raster_fwd(sp: LgsSplats, vals, tile_ranges, cam: LgsCamera, tile_w, tile_h, image,

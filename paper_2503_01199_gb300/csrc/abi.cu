@@ -230,8 +230,47 @@ lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int6
 
 lgs_status lgs_get_overflow(int64_t *needed) { return get_overflow(needed); }
 
+int32_t lgs_debug_build(void) {
+#ifdef LGS_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lgs_status lgs_get_debug_error(uint64_t *code) {
+    if (!code) return LGS_ERR_INVALID_ARG;
+    *code = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    lgs_status (*const readers[])(uint64_t *) = {debug_error_raster, debug_error_sort,
+                                                 debug_error_ccc, debug_error_preprocess};
+    for (auto rd : readers) {
+        uint64_t c = 0;
+        const lgs_status st = rd(&c);
+        if (st != LGS_OK) return st;
+        if (c && !*code) *code = c;
+    }
+    return *code ? LGS_ERR_BOUNDS : LGS_OK;
+}
+
+lgs_status lgs_set_wait_limit(uint32_t spins) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    const lgs_status a = sort_set_spin_limit(spins);
+    return a != LGS_OK ? a : bin_set_spin_limit(spins);
+}
+
 lgs_status lgs_get_wait_timeouts(uint32_t *count) {
     if (!count) return LGS_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
     uint32_t a = 0, b = 0;
     const lgs_status sa = sort_wait_timeouts(&a);
     const lgs_status sb = bin_wait_timeouts(&b);

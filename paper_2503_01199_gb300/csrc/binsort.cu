@@ -288,10 +288,11 @@ __device__ __forceinline__ uint32_t super_count(const int4 rc, S &&span_of) {
 // Look-back status of a group of 32 splats: flag in the top two bits, the
 // group's item count (AGG) or the inclusive item count of groups <= it (PRE).
 constexpr uint64_t kGrpAgg = 1ull << 62, kGrpPre = 2ull << 62, kGrpVal = (1ull << 62) - 1ull;
-constexpr uint32_t kGrpMaxSpin = 1u << 22;
 constexpr int kItemCap = 384;  // items per warp staged in shared memory
 
 __device__ unsigned int g_bin_wait_timeouts;
+// polls of an unpublished predecessor group before the look-back gives up
+__device__ uint32_t g_bin_spin_limit = kDefaultSpinLimit;
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 #pragma unroll
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_super_items(
                 const int stop = pre ? __ffs(pre) - 1 : 31;
                 const uint32_t need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
                 if (wait & need) {
-                    if (++spins > kGrpMaxSpin) {
+                    if (++spins > g_bin_spin_limit) {
                         if (lane == 0) atomicAdd(&g_bin_wait_timeouts, 1u);
                         break;
                     }
@@ -823,6 +824,14 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
     k_chunk_emit<<<gc, kThreads, 0, s>>>(svals, L.ctab, L.cbase, L.ccount, L.tstart, G, cap,
                                         vals);
     return check_launch();
+}
+
+lgs_status bin_set_spin_limit(uint32_t spins) {
+    if (cudaMemcpyToSymbol(g_bin_spin_limit, &spins, sizeof(spins)) != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    return LGS_OK;
 }
 
 lgs_status bin_wait_timeouts(uint32_t *count) {

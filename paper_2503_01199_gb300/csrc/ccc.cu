@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_planes(const float *__restr
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = perm[i];
+        if (!LGS_DCHECK(r < n_max, kSiteGatherPerm)) continue;
         for (int k = 0; k < n_planes; ++k) dst[k * dst_stride + i] = src[k * src_stride + r];
     }
 }
@@ -242,6 +243,8 @@ lgs_status morton_reorder(const float *src, float *dst, int64_t n, int64_t strid
 // ---------------------------------------------------------------------------
 // a2
 // ---------------------------------------------------------------------------
+DEBUG_TU(ccc)
+
 size_t ccc_workspace_size(int64_t n, int cs) {
     const int64_t ncl = ceil_div(n, cs);
     return al256((size_t)ncl * 4) + al256((size_t)ncl * 8) + al256(8) + al256(scan_scratch_bytes());

@@ -36,6 +36,57 @@ inline unsigned grid_for(int64_t n, int threads, int per_sm = 8) {
 }
 
 // ---------------------------------------------------------------------------
+// Bounds checks of the debug build (compiled with -DLGS_DEBUG). LGS_DCHECK
+// (cond, site) is true when cond holds; when it does not, the first failure
+// of the translation unit is recorded in its error word as
+// (site << 32) | source line, and the caller skips the access it guards.
+// Release builds compile it to `true`. Each translation unit has its own
+// word (the library is built without relocatable device code); DEBUG_TU
+// defines the host function that reads and clears it.
+// ---------------------------------------------------------------------------
+enum DebugSite : uint32_t {
+    kSiteRasterSplat = 1,   // splat index of a tile list < splat rows
+    kSiteRasterRow = 2,     // gradient row < grad_acc rows
+    kSiteSortScatter = 3,   // radix sort output position < key count
+    kSiteGatherPerm = 4,    // Morton gather source row < rows
+    kSitePreMap = 5,        // preprocess compaction-map row < rows
+    kSiteAdamMap = 6,       // backward / Adam compaction-map row < rows
+};
+
+#ifdef LGS_DEBUG
+namespace {
+__device__ unsigned long long g_debug_error;
+__device__ __forceinline__ bool dcheck(bool ok, uint32_t site, uint32_t line) {
+    if (!ok) atomicCAS(&g_debug_error, 0ull, ((unsigned long long)site << 32) | line);
+    return ok;
+}
+}  // namespace
+#define LGS_DCHECK(cond, site) ::lgs::dcheck((cond), (site), __LINE__)
+#define DEBUG_TU(name)                                                                      \
+    lgs_status debug_error_##name(uint64_t *code) {                                        \
+        unsigned long long h = 0, zero = 0;                                                 \
+        if (cudaMemcpyFromSymbol(&h, g_debug_error, sizeof(h)) != cudaSuccess ||           \
+            cudaMemcpyToSymbol(g_debug_error, &zero, sizeof(zero)) != cudaSuccess) {       \
+            set_cuda_error(cudaGetLastError());                                            \
+            return LGS_ERR_CUDA;                                                           \
+        }                                                                                   \
+        *code = h;                                                                          \
+        return LGS_OK;                                                                      \
+    }
+#else
+#define LGS_DCHECK(cond, site) true
+#define DEBUG_TU(name)                                                                      \
+    lgs_status debug_error_##name(uint64_t *code) {                                        \
+        *code = 0;                                                                          \
+        return LGS_OK;                                                                      \
+    }
+#endif
+lgs_status debug_error_raster(uint64_t *code);
+lgs_status debug_error_sort(uint64_t *code);
+lgs_status debug_error_ccc(uint64_t *code);
+lgs_status debug_error_preprocess(uint64_t *code);
+
+// ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int load_count(const int32_t *d_count, int64_t fallback) {
@@ -192,6 +243,14 @@ size_t radix_sort_workspace(int64_t n, int key_bytes);
 // clears the count.
 size_t radix_hist_bytes(int64_t n_max);
 lgs_status sort_wait_timeouts(uint32_t *count);
+// Polls of an unpublished predecessor after which the look-backs of the
+// radix sort and of the binning give up (counted, see above); the default
+// is kDefaultSpinLimit. A look-back that gives up takes the partial prefix
+// it has summed, which is never larger than the true one, so every output
+// position it computes stays below the true one and inside the output.
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;
+lgs_status sort_set_spin_limit(uint32_t spins);
+lgs_status bin_set_spin_limit(uint32_t spins);
 // The same count for the binning's look-back over groups of splats.
 lgs_status bin_wait_timeouts(uint32_t *count);
 // 16-bit keys carry 64-bit values.

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(const float *__restrict
         const int64_t row = map ? map[j] : j;
         Fwd f;
         float4 *r4 = reinterpret_cast<float4 *>(rec + 12 * j);
-        if (!geom_forward(K, P, stride, row, f)) {
+        if (!LGS_DCHECK(row < n, kSitePreMap) || !geom_forward(K, P, stride, row, f)) {
             r4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             r4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -582,6 +582,7 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_bwd(const float *__rest
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = map ? map[j] : j;
+        if (!LGS_DCHECK(row < n, kSitePreMap)) continue;
         GradSink sink{gout, stride, row, accumulate != 0};
         backward<DEG>(K, P, stride, row, gacc + 16 * j, sink);
     }
@@ -860,6 +861,7 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float
         const int k = (int)(t / V);
         const int64_t j = t - (int64_t)k * V;
         const int64_t row = map ? map[j] : j;
+        if (!LGS_DCHECK(row < max_rows, kSiteAdamMap)) continue;
         const int64_t i = k * stride + row;
         float p = P[i], m = Mo[i], v = Vo[i];
         adam_update(p, m, v, G[i], a.lr[k], a);
@@ -879,6 +881,8 @@ AdamArgs make_adam(const float *lr, int np, float b1, float b2, float eps, int s
 }
 
 }  // namespace
+
+DEBUG_TU(preprocess)
 
 lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
                       const lgs_camera *cam, int tw, int th, const lgs_splats *out,

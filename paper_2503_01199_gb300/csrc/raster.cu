@@ -60,6 +60,7 @@ struct __align__(16) SplatS {
 struct RCam {
     int W, H, gx, ntiles;
     float bg[3];
+    int64_t splat_rows, grad_rows;  // bounds the debug build checks indices against
 };
 
 // PREC = blend precision (LGS_FP32 / LGS_MIXED_FP16 / LGS_MIXED_BF16),
@@ -105,8 +106,12 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // y extent and the interval are widened by 2e-3 of the ellipse's extent plus
 // 1e-2 pixel. A conic that is not positive definite reaches every quadrant.
 template <int PREC>
-__device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_t j, float x0,
-                                          float y0, SplatS &s) {
+__device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_t j,
+                                          int64_t nrows, float x0, float y0, SplatS &s) {
+    if (!LGS_DCHECK((int64_t)j < nrows, kSiteRasterSplat)) {
+        s = SplatS{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, 0.f};
+        return 0u;  // reaches no quadrant
+    }
     const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)j);
     const float4 x = __ldg(p), y = __ldg(p + 1);
     const float2 z = __ldg(reinterpret_cast<const float2 *>(rec + 12 * (int64_t)j + 8));
@@ -239,7 +244,7 @@ __device__ __forceinline__ void fwd_tile(const float *__restrict__ rec,
         if (__syncthreads_count(live != 0) == 0) break;
         const uint32_t idx = b0 + threadIdx.x;
         if (idx < r1)
-            sm.fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, vals[idx], tx0, ty0, sm.sp[threadIdx.x]);
+            sm.fl[threadIdx.x] = (uint8_t)stage<PREC>(rec, vals[idx], K.splat_rows, tx0, ty0, sm.sp[threadIdx.x]);
         __syncthreads();
         const int cnt = (int)min((uint32_t)kBatch, r1 - b0);
 #pragma unroll 1
@@ -360,17 +365,17 @@ __device__ __forceinline__ float int_sum_value(int tot, uint32_t emax) {
 // Order-independent accumulation (lgs_raster_bwd_deterministic). Every
 // contribution M 2^k (M a signed integer: a float's significand, or the
 // integer warp sum of Sec. 3.1's reduction with its exponent) is added as
-// the exact 128-bit two's-complement integer N = M 2^(k + 96), i.e. in units
-// of 2^-96, split into three limbs: bits 0-31 and bits 32-63 each summed in
-// its own unsigned 64-bit word (2^32 contributions cannot overflow it) and
-// bits 64-127 summed modulo 2^64 in a third word. Integer addition commutes,
-// so the limbs, and the value they make, do not depend on the order in
-// which tiles and quadrants add to a splat. A contribution whose N would
-// need more than 126 bits (|value| >= 2^30) is counted in g_det_overflow and
-// left out; bits below 2^-96 are truncated toward zero.
+// the 96-bit two's-complement integer N = M 2^(k + 64), i.e. in units of
+// 2^-64, split into two limbs: bits 0-31 summed in an unsigned 64-bit word
+// (2^32 contributions cannot overflow it) and bits 32-95 summed modulo 2^64
+// in a second word. Integer addition commutes, so the limbs, and the value
+// they make, do not depend on the order in which tiles and quadrants add to
+// a splat. A contribution whose N would need more than 94 bits
+// (|value| >= 2^30) is counted in g_det_overflow and left out; bits below
+// 2^-64 are truncated toward zero (at most 2^-64 per contribution).
 // ---------------------------------------------------------------------------
 constexpr int kDetValues = 10;  // du dv dA dB dC do dr dg db S (M = do; C is an integer)
-constexpr int kDetLimbs = 3;
+constexpr int kDetLimbs = 2;
 
 __device__ unsigned int g_det_overflow;
 
@@ -378,36 +383,38 @@ __device__ __forceinline__ void fixed_add(unsigned long long *acc, long long M, 
     if (M == 0) return;
     const bool neg = M < 0;
     const uint64_t mag = neg ? (uint64_t)(-M) : (uint64_t)M;
-    const int sh = k + 96;
-    uint64_t lo, hi;
+    const int sh = k + 64;
+    uint64_t lo, hi;  // N = hi 2^32 + lo, lo < 2^32
     if (sh >= 0) {
-        if (64 - __clzll((long long)mag) + sh > 126) {
+        if (64 - __clzll((long long)mag) + sh > 94) {
             atomicAdd(&g_det_overflow, 1u);
             return;
         }
-        if (sh == 0) {
-            lo = mag;
-            hi = 0;
-        } else if (sh < 64) {
-            lo = mag << sh;
-            hi = mag >> (64 - sh);
-        } else {
+        // mag 2^sh: low 32 bits and the rest (at most 62 bits)
+        if (sh >= 32) {
             lo = 0;
-            hi = mag << (sh - 64);
+            hi = mag << (sh - 32);
+        } else {
+            lo = (mag << sh) & 0xffffffffull;
+            hi = sh ? (mag >> (32 - sh)) : (mag >> 32);
         }
     } else {
         if (sh <= -64) return;
-        lo = mag >> (-sh);
-        hi = 0;
-        if (lo == 0) return;
+        const uint64_t t = mag >> (-sh);
+        if (t == 0) return;
+        lo = t & 0xffffffffull;
+        hi = t >> 32;
     }
-    if (neg) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    if (neg) {  // -(hi 2^32 + lo) = hi' 2^32 + lo' with lo' in [0, 2^32)
+        if (lo) {
+            lo = (1ull << 32) - lo;
+            hi = ~hi;  // -(hi + 1)
+        } else {
+            hi = ~hi + 1ull;
+        }
     }
-    atomicAdd(acc, (unsigned long long)(lo & 0xffffffffull));
-    atomicAdd(acc + 1, (unsigned long long)(lo >> 32));
-    atomicAdd(acc + 2, (unsigned long long)hi);
+    atomicAdd(acc, (unsigned long long)lo);
+    atomicAdd(acc + 1, (unsigned long long)hi);
 }
 
 // A float x = M 2^k exactly (M its signed significand).
@@ -423,9 +430,9 @@ __device__ __forceinline__ void fixed_add_float(unsigned long long *acc, float x
 }
 
 // Rows of grad_acc from the limbs: for every row j < rows, value v of the
-// kDetValues is (limb0 + limb1 2^32 + limb2 2^64) 2^-96 taken as a signed
-// 128-bit integer, rounded to double (exactly enough: the magnitude's two
-// 64-bit halves are converted separately) and then to float; M = do.
+// kDetValues is (limb0 + limb1 2^32) 2^-64 taken as a signed 96-bit integer
+// (limb1 modulo 2^64 carries the sign), rounded to double (the magnitude's
+// two 64-bit halves converted separately) and then to float; M = do.
 __global__ void __launch_bounds__(256) k_det_finalize(const unsigned long long *__restrict__ acc,
                                                      int64_t rows, float *__restrict__ gacc) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < rows;
@@ -434,15 +441,16 @@ __global__ void __launch_bounds__(256) k_det_finalize(const unsigned long long *
         float *row = gacc + 16 * j;
 #pragma unroll
         for (int v = 0; v < kDetValues; ++v) {
-            const uint64_t l0 = a[kDetLimbs * v], l1 = a[kDetLimbs * v + 1], l2 = a[kDetLimbs * v + 2];
+            const uint64_t l0 = a[kDetLimbs * v], l1 = a[kDetLimbs * v + 1];
+            // 128-bit N = l0 + l1 2^32 with l1 sign-extended
             uint64_t lo = l0 + (l1 << 32);
-            uint64_t hi = l2 + (l1 >> 32) + (lo < l0 ? 1ull : 0ull);
+            uint64_t hi = (uint64_t)((int64_t)l1 >> 32) + (lo < l0 ? 1ull : 0ull);
             const bool neg = (int64_t)hi < 0;
             if (neg) {
                 lo = ~lo + 1ull;
                 hi = ~hi + (lo == 0ull ? 1ull : 0ull);
             }
-            const double d = ((double)hi * 18446744073709551616.0 + (double)lo) * 0x1p-96;
+            const double d = ((double)hi * 18446744073709551616.0 + (double)lo) * 0x1p-64;
             row[v] = (float)(neg ? -d : d);
         }
         row[10] = row[5];
@@ -500,7 +508,8 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
         __syncthreads();
         if ((int)threadIdx.x < cnt)
             sm.fl[threadIdx.x] =
-                (uint8_t)stage<PREC>(rec, vals[r0 + end - 1 - threadIdx.x], tx0, ty0, sm.sp[threadIdx.x]);
+                (uint8_t)stage<PREC>(rec, vals[r0 + end - 1 - threadIdx.x], K.splat_rows, tx0, ty0,
+                                     sm.sp[threadIdx.x]);
         __syncthreads();
 #pragma unroll 1
         for (int q = 0; q < kBatch / 32; ++q) {
@@ -565,6 +574,7 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                 v[9] = S;
                 v[10] = dO;
                 v[11] = n;
+                if (!LGS_DCHECK((int64_t)s.id < K.grad_rows, kSiteRasterRow)) continue;
                 float *row = gacc + 16 * (int64_t)s.id;
                 unsigned long long *drow = det + (size_t)s.id * (kDetValues * kDetLimbs);
                 if constexpr (int_reduce(PREC)) {
@@ -640,6 +650,7 @@ __device__ __forceinline__ RCam view_rcam(const lgs_view &V) {
     K.bg[0] = V.bg[0];
     K.bg[1] = V.bg[1];
     K.bg[2] = V.bg[2];
+    K.splat_rows = K.grad_rows = INT64_MAX;  // a view carries no row counts
     return K;
 }
 
@@ -719,8 +730,10 @@ __global__ void __launch_bounds__(256) k_variance(const float *__restrict__ gacc
     }
 }
 
-RCam make_rcam(const lgs_camera *c, int tw, int th) {
+RCam make_rcam(const lgs_camera *c, int tw, int th, int64_t splat_rows, int64_t grad_rows) {
     RCam k;
+    k.splat_rows = splat_rows;
+    k.grad_rows = grad_rows;
     k.W = c->width;
     k.H = c->height;
     k.gx = (int)ceil_div(c->width, tw);
@@ -731,11 +744,13 @@ RCam make_rcam(const lgs_camera *c, int tw, int th) {
 
 }  // namespace
 
+DEBUG_TU(raster)
+
 lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
                       const lgs_camera *cam, int tw, int th, int precision, float *image,
                       float *finalT, int32_t *last, cudaStream_t s) {
     if (tw != kTile || th != kTile) return LGS_ERR_INVALID_ARG;
-    const RCam K = make_rcam(cam, tw, th);
+    const RCam K = make_rcam(cam, tw, th, sp->capacity, INT64_MAX);
     const unsigned grid = (unsigned)K.ntiles;
     count_launch();
     switch (precision) {
@@ -762,7 +777,7 @@ lgs_status raster_bwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t
     if ((precision & ~LGS_WARP_REDUCE_INT) < LGS_FP32 || (precision & ~LGS_WARP_REDUCE_INT) > LGS_MIXED_BF16)
         return LGS_ERR_INVALID_ARG;
     if (!accumulate) cudaMemsetAsync(gacc, 0, (size_t)max_splats * 16 * sizeof(float), s);
-    const RCam K = make_rcam(cam, tw, th);
+    const RCam K = make_rcam(cam, tw, th, sp->capacity, max_splats);
     const unsigned grid = (unsigned)K.ntiles;
     count_launch();
 #define LGS_RBW(P) k_raster_bwd<P><<<grid, kBwdThreads, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc, nullptr)
@@ -795,7 +810,7 @@ lgs_status raster_bwd_det(const lgs_splats *sp, const uint32_t *vals, const uint
     unsigned long long *det = static_cast<unsigned long long *>(ws);
     cudaMemsetAsync(gacc, 0, (size_t)max_splats * 16 * sizeof(float), s);
     cudaMemsetAsync(det, 0, need, s);
-    const RCam K = make_rcam(cam, tw, th);
+    const RCam K = make_rcam(cam, tw, th, sp->capacity, max_splats);
     const unsigned grid = (unsigned)K.ntiles;
     count_launch();
 #define LGS_RBD(P) k_raster_bwd<(P) | kDetFlag><<<grid, kBwdThreads, 0, s>>>(sp->rec, vals, ranges, K, finalT, last, dLdI, gacc, det)

@@ -103,10 +103,11 @@ __device__ uint64_t block_exclusive_scan(uint64_t x, uint64_t *smem /* [33] */, 
 constexpr uint32_t kFlagAgg = 1u << 30;   // tile's own counts published
 constexpr uint32_t kFlagPre = 2u << 30;   // inclusive prefix over tiles <= t published
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
-constexpr uint32_t kMaxSpin = 1u << 22;
 constexpr int kMaxPasses = 8;
 
 __device__ unsigned int g_sort_wait_timeouts;
+// polls of an unpublished predecessor before a look-back gives up
+__device__ uint32_t g_sort_spin_limit = kDefaultSpinLimit;
 
 // Digit counts of every pass in one read of the keys (hist zeroed).
 // Also clears the tile status words and the tile counter of the first pass.
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
                     const uint32_t w = *(volatile const uint32_t *)(status + k * kRadix + d);
                     const uint32_t fl = w & ~kCountMask;
                     if (fl == 0u) {
-                        if (++spins > kMaxSpin) {
+                        if (++spins > g_sort_spin_limit) {
                             atomicAdd(&g_sort_wait_timeouts, 1u);
                             break;
                         }
@@ -261,8 +262,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
             const K k = s_keys[i];
             const int d = digit_of(k, shift);
             const uint32_t o = s_base[d] + (uint32_t)i - s_start[d];
-            keys_out[o] = k;
-            vals_out[o] = s_vals[i];
+            if (LGS_DCHECK((int64_t)o < n, kSiteSortScatter)) {
+                keys_out[o] = k;
+                vals_out[o] = s_vals[i];
+            }
         }
         __syncthreads();
     }
@@ -377,6 +380,16 @@ int radix_passes(int bits) { return bits <= 0 ? 1 : (bits + 7) / 8; }
 size_t radix_hist_bytes(int64_t n_max) {
     return sizeof(uint32_t) * ((size_t)kMaxPasses * kRadix + 64 +
                                2 * (size_t)sort_tiles(n_max > 0 ? n_max : 1) * kRadix);
+}
+
+DEBUG_TU(sort)
+
+lgs_status sort_set_spin_limit(uint32_t spins) {
+    if (cudaMemcpyToSymbol(g_sort_spin_limit, &spins, sizeof(spins)) != cudaSuccess) {
+        set_cuda_error(cudaGetLastError());
+        return LGS_ERR_CUDA;
+    }
+    return LGS_OK;
 }
 
 lgs_status sort_wait_timeouts(uint32_t *count) {

@@ -30,6 +30,17 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     assert set(B.ENTRY_POINTS) == declared()
     assert B.lgs_version().startswith("lgs")
+    assert lib.lgs_debug_build() == 0
+
+
+def test_debug_build_exports_the_same_symbols():
+    """The bounds-checked build is the same ABI with checks compiled in."""
+    from paper_2503_01199_gb300 import build as LB
+    LB.build()
+    lib = ctypes.CDLL(str(LB.DEBUG_LIB))
+    missing = [n for n in sorted(declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert lib.lgs_debug_build() == 1
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu():
@@ -113,16 +124,16 @@ def test_capacity_and_grid_rules_are_checked_on_the_host():
     assert fused(skew, sp) == bad                                    # stride a multiple of 4
 
     # the deterministic backward: its workspace size and the raster rules
-    assert L.lgs_raster_bwd_det_workspace_size(n) == 240 * n
+    assert L.lgs_raster_bwd_det_workspace_size(n) == 160 * n
     img = buf(4 * 128 * 128 * 3)
     fT, lastc = buf(4 * 128 * 128), buf(4 * 128 * 128)
-    dws = buf(240 * n)
+    dws = buf(160 * n)
 
-    def det(tw=16, ws_=dws, wsb=240 * n, prec=B.LGS_FP32, gacc_=gacc, rows=n):
+    def det(tw=16, ws_=dws, wsb=160 * n, prec=B.LGS_FP32, gacc_=gacc, rows=n):
         return L.lgs_raster_bwd_deterministic(ctypes.byref(sp), vals, ranges, ctypes.byref(cam), tw,
                                               16, prec, fT, lastc, img, gacc_, rows, ws_, wsb, None)
 
-    assert det(wsb=240 * n - 1) == bad                               # workspace too small
+    assert det(wsb=160 * n - 1) == bad                               # workspace too small
     assert det(ws_=ctypes.c_void_p(dws.value + 8)) == bad            # workspace not 16-byte aligned
     assert det(tw=8) == bad                                          # 16 x 16 tiles only
     assert det(prec=3) == bad                                        # unknown precision
