@@ -597,8 +597,11 @@ def run_gpu(args) -> dict | None:
 SERVE_SCENES = ((500_000, 10), (1_000_000, 11), (2_000_000, 12), (3_000_000, 13))
 SERVE_RES = ((640, 360), (1280, 720), (1920, 1080))
 SERVE_RATE = 200.0
-SERVE_PAIR_CAPACITY = 128_000_000  # largest seen: 97.7M pairs (3M Gaussians, 1920x1080)
-SERVE_SLOTS = 4  # the HBM budget pays for scratch of about 4 concurrent 1080p requests
+SERVE_PAIR_CAPACITY = 128_000_000  # 1920x1080 class; largest seen: 97.7M pairs (3M, 1920x1080)
+SERVE_BUDGET_LARGE = 4.2  # budget: 4.2 x a 1920x1080 slot (about 14 GB), deliberately small
+SERVE_SWEEP = (500.0, 1000.0, 2000.0, 4000.0)
+SERVE_SWEEP_SECONDS = 2.0
+SERVE_SIDE_SECONDS = 20.0  # the grouped executor and the plain loop at the configured rate
 
 
 def run_serving(seconds: float) -> dict:
@@ -613,42 +616,53 @@ def run_serving(seconds: float) -> dict:
     scenes = [SV.ResidentScene(scenegen.surface_scene(n, SH_DEG, seed, 64, 64)["scene"])
               for n, seed in SERVE_SCENES]
     origin = (0.0, 0.0, 0.0)
-    need = SV.slot_bytes(max(n for n, _ in SERVE_SCENES), 1920, 1080, SERVE_PAIR_CAPACITY)
-    budget = int(SERVE_SLOTS * need + need // 5)
-    # a short discarded stream first (process warm-up after the training runs)
-    SV.serve(scenes, scenegen.render_requests(21, 1.0, SERVE_RATE, len(scenes), list(SERVE_RES),
-                                              center=origin),
-             budget, list(SERVE_RES), SERVE_PAIR_CAPACITY)
-    gc.collect()
-    torch.cuda.empty_cache()
-    reqs = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES),
-                                     center=origin)
-    served = SV.serve(scenes, reqs, budget, list(SERVE_RES), SERVE_PAIR_CAPACITY)
-    st = served["stats"]
-    del served
-    torch.cuda.empty_cache()
-    reqs_g = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES),
-                                     center=origin)
-    grouped = SV.serve(scenes, reqs_g, budget, list(SERVE_RES), SERVE_PAIR_CAPACITY,
-                       grouped=True)
-    gst = grouped["stats"]
-    del grouped
-    torch.cuda.empty_cache()
-    reqs2 = scenegen.render_requests(20, seconds, SERVE_RATE, len(scenes), list(SERVE_RES),
-                                     center=origin)
-    plain = SV.plain_loop(scenes, reqs2, list(SERVE_RES), SERVE_PAIR_CAPACITY)["stats"]
+    max_n = max(n for n, _ in SERVE_SCENES)
+    classes = [(w, h, SV.class_capacity(w, h, max_n, 1920, 1080, SERVE_PAIR_CAPACITY))
+               for w, h in SERVE_RES]
+    budget = int(SERVE_BUDGET_LARGE * SV.slot_bytes(max_n, 1920, 1080, SERVE_PAIR_CAPACITY))
+    res = list(SERVE_RES)
+
+    def stream(seed, secs, rate):
+        return scenegen.render_requests(seed, secs, rate, len(scenes), res, center=origin)
+
+    def run(kind, reqs):
+        gc.collect()
+        torch.cuda.empty_cache()
+        if kind == "plain_loop":
+            return SV.plain_loop(scenes, reqs, res, SERVE_PAIR_CAPACITY)["stats"]
+        out = SV.serve(scenes, reqs, budget, res, SERVE_PAIR_CAPACITY, classes=classes,
+                       grouped=(kind == "grouped"))
+        st = out["stats"]
+        del out
+        return st
+
+    keys = ("p50_ms", "p99_ms", "mean_ms", "frames_per_s", "requests", "pair_overflow")
+    run("per_request_graphs", stream(21, 1.0, SERVE_RATE))   # discarded warm-up stream
+    st = run("per_request_graphs", stream(20, seconds, SERVE_RATE))
+    side = min(seconds, SERVE_SIDE_SECONDS)
+    gst = run("grouped", stream(20, side, SERVE_RATE))
+    plain = run("plain_loop", stream(20, side, SERVE_RATE))
+    sweep = []
+    for i, rate in enumerate(SERVE_SWEEP):
+        row = {"rate_req_per_s": rate, "seconds": SERVE_SWEEP_SECONDS}
+        for kind in ("per_request_graphs", "grouped", "plain_loop"):
+            r = run(kind, stream(40 + i, SERVE_SWEEP_SECONDS, rate))
+            row[kind] = {k: r[k] for k in ("p50_ms", "p99_ms", "frames_per_s", "requests")}
+            if kind != "plain_loop":
+                row[kind]["retries"] = r["retries"]
+        sweep.append(row)
     return {"workload": ("4 resident scenes (config-1 surface generator, SH3, BF16 colour + "
                          "FP32 geometry): 0.5M/1M/2M/3M Gaussians, seeds 10-13; Poisson arrivals "
-                         f"at 200 req/s for {seconds:g} s, resolution uniform over 640x360/"
-                         "1280x720/1920x1080, orbit cameras around the origin; forward render + "
-                         "image to pinned host"),
-            "hbm_budget_bytes": budget, **{k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms",
-                                                               "frames_per_s", "requests",
-                                                               "slots", "max_inflight",
-                                                               "pair_overflow")},
-            "grouped_batched_raster": {k: gst[k] for k in ("p50_ms", "p99_ms", "mean_ms",
-                                                           "frames_per_s", "max_group")},
-            "plain_loop": {k: plain[k] for k in ("p50_ms", "p99_ms", "mean_ms", "frames_per_s")}}
+                         f"at {SERVE_RATE:g} req/s for {seconds:g} s, resolution uniform over "
+                         "640x360/1280x720/1920x1080, orbit cameras around the origin; forward "
+                         "render + image to pinned host"),
+            "hbm_budget_bytes": budget, "slot_classes": st["slot_classes"],
+            **{k: st[k] for k in keys}, "slots": st["slots"], "max_inflight": st["max_inflight"],
+            "retries": st["retries"],
+            "grouped_batched_raster": {**{k: gst[k] for k in keys}, "seconds": side,
+                                       "max_group": gst["max_group"]},
+            "plain_loop": {**{k: plain[k] for k in keys}, "seconds": side},
+            "load_sweep": sweep}
 
 
 # ---------------------------------------------------------------------------
@@ -840,7 +854,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-gaussians", type=int, default=None,
                     help="smaller scene for profiling captures (not a bench line)")
-    ap.add_argument("--serve-seconds", type=float, default=15.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served-render request stream (0: skip)")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the Cluster-Cull-Compact / storage-order ablation")

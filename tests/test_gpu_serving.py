@@ -58,6 +58,43 @@ def test_each_request_same_alone_and_in_the_mix(scenes, grouped):
         assert np.isfinite(q["image"]).all() and q["image"].max() > 0
 
 
+@pytest.mark.parametrize("grouped", [False, True])
+def test_slot_classes_and_overflow_retry(scenes, grouped):
+    """Slots of three classes (one per resolution); the smallest class's pair
+    capacity is set below what some of its requests need, so those are run
+    again in a larger class. Every request completes once, with an image
+    bit-identical to its render alone, and none is returned truncated."""
+    reqs = scenegen.render_requests(8, 0.05, 1500.0, len(scenes), RES)
+    alone = SV.GpuExecutor(scenes, 1, RES, 4_000_000, use_graphs=False, keep_images=True)
+    need = {}
+    for i, r in enumerate(reqs):
+        q = {"scene": r["scene"], "camera": r["camera"]}
+        alone.start(0, q)
+        alone.slots[0].event.synchronize()
+        assert alone.finish(0, q)
+        need[i] = (q["pairs"], q["image"])
+    small = [need[i][0] for i, r in enumerate(reqs) if r["camera"]["width"] == RES[0][0]]
+    cap0 = int(np.median(small))                      # about half of them overflow
+    classes = [(96, 64, cap0), (160, 96, 4_000_000), (200, 120, 4_000_000)]
+    for i, r in enumerate(reqs):
+        r["i"] = i
+    max_n = max(sc.n for sc in scenes)
+    budget = 2 * sum(SV.slot_bytes(max_n, w, h, cap) for w, h, cap in classes)
+    out = SV.serve(scenes, reqs, hbm_budget_bytes=budget, resolutions=RES,
+                   pair_capacity=4_000_000, keep_images=True, classes=classes, grouped=grouped)
+    st = out["stats"]
+    assert st["requests"] == len(reqs) and st["pair_overflow"] == 0
+    assert st["retries"] == sum(p > cap0 for p in small) > 0
+    assert len(st["slot_classes"]) == 3 and st["slots"] >= 6
+    assert st["slot_classes"][0]["slot_bytes"] < st["slot_classes"][2]["slot_bytes"]
+    ex = out["executor"]
+    for r in out["completed"]:
+        slot = ex.slots[r["slot"]]
+        w, h = r["camera"]["width"], r["camera"]["height"]
+        assert slot.fits(w, h) and r["pairs"] <= slot.cap
+        np.testing.assert_array_equal(r["image"], need[r["i"]][1])
+
+
 def test_device_pose_equals_host_pose(scenes):
     cam = scenegen.orbit_camera(4.0, 1.1, 0.2, 160, 96, center=scenegen.BOX_CENTER)
     ex_graph = SV.GpuExecutor(scenes, 1, [(160, 96)], 4_000_000, use_graphs=True, keep_images=True)
