@@ -477,11 +477,25 @@ def run_gpu(args) -> dict | None:
     e2e_ms = e0.elapsed_time(e1)
     # ---- the same step with the mixed-precision raster (FP16 / BF16 blend)
     mixed = {}
-    for name, prec, dm in (("fp16", B.LGS_MIXED_FP16, False), ("bf16", B.LGS_MIXED_BF16, False),
-                           ("fp32_warp_reduce_int", B.LGS_FP32 | B.LGS_WARP_REDUCE_INT, False),
-                           ("fp32_deterministic", B.LGS_FP32, True),
-                           ("fp32_warp_reduce_int_deterministic",
-                            B.LGS_FP32 | B.LGS_WARP_REDUCE_INT, True)):
+    sh_types = {"fp16": torch.float16, "bf16": torch.bfloat16}
+    # every variant starts from the same parameters and moments (the steps
+    # train, and a drifting scene would change the work between variants)
+    snapshot = tr.state[tr.cur].clone()
+    step_count0 = tr.step_count
+    for name, prec, dm, sh in (
+            ("fp32", B.LGS_FP32, False, None),
+            ("fp16", B.LGS_MIXED_FP16, False, None), ("bf16", B.LGS_MIXED_BF16, False, None),
+            ("fp16_sh16", B.LGS_MIXED_FP16, False, "fp16"),
+            ("bf16_sh16", B.LGS_MIXED_BF16, False, "bf16"),
+            ("fp32_warp_reduce_int", B.LGS_FP32 | B.LGS_WARP_REDUCE_INT, False, None),
+            ("fp32_deterministic", B.LGS_FP32, True, None),
+            ("fp32_warp_reduce_int_deterministic", B.LGS_FP32 | B.LGS_WARP_REDUCE_INT, True,
+             None)):
+        tr.state[tr.cur].copy_(snapshot)
+        tr.step_count = step_count0
+        if sh:  # colour coefficients read in 16 bits (the fused Adam keeps the copy)
+            tr.sh16 = torch.zeros((tr.np_ - 11, tr.stride), dtype=sh_types[sh], device=dev)
+            tr._round_sh16()
         for _ in range(2):
             step(precision=prec, deterministic=dm)
         mev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
@@ -500,7 +514,15 @@ def run_gpu(args) -> dict | None:
             "a5_raster_fwd_ms": round(float(np.mean([mev[k][4].elapsed_time(mev[k][5])
                                                      for k in range(args.steps)])), 4),
             "a7_raster_bwd_ms": round(float(np.mean([mev[k][6].elapsed_time(mev[k][7])
-                                                     for k in range(args.steps)])), 4)}
+                                                     for k in range(args.steps)])), 4),
+            "a3_preprocess_ms": round(float(np.mean([mev[k][2].elapsed_time(mev[k][3])
+                                                     for k in range(args.steps)])), 4),
+            "a9a10_bwd_adam_ms": round(float(np.mean([mev[k][8].elapsed_time(mev[k][9])
+                                                      for k in range(args.steps)])), 4)}
+        tr.sh16 = None
+    tr.state[tr.cur].copy_(snapshot)
+    tr.step_count = step_count0
+    del snapshot
     multiview = run_multiview(tr, max(args.steps // 2, 3), 2) if world == 1 else None
     clk = clocks.stop()
     loss_val = float(loss_host.item())

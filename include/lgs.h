@@ -100,8 +100,10 @@ typedef struct lgs_gaussians {
     /* Storage of the colour coefficients: LGS_SH_F32 (planes 11.. of data)
      * or LGS_SH_BF16 / LGS_SH_F16: 16-bit planes at sh16 + k * stride,
      * k = 3 coefficient + channel (planes 0..10 stay float32 in data).
-     * 16-bit storage is for rendering: only lgs_cluster_cull_compact and
-     * lgs_preprocess accept it; the backward and optimizer calls reject it. */
+     * 16-bit storage is for rendering (lgs_cluster_cull_compact,
+     * lgs_preprocess) and for the fused lgs_preprocess_bwd_adam, which keeps
+     * FP32 masters in data and writes the rounded copy; the other backward
+     * and optimizer calls reject it. */
     int32_t sh_dtype;
     const void *sh16;
 } lgs_gaussians;
@@ -475,12 +477,26 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
  * sp (may be NULL): the splat records lgs_preprocess wrote for this camera
  * from these parameters (rows j < V read, capacity >= g->n). With them the colour clamp
  * is taken from the stored colours instead of recomputing the colours, so
- * the SH planes are read once; without them the colours are recomputed. */
+ * the SH planes are read once; without them the colours are recomputed.
+ * 16-bit colour (the mixed-precision variant that keeps SH in FP16 / BF16
+ * for the forward): with g->sh_dtype LGS_SH_BF16 / LGS_SH_F16, g->data still
+ * holds all num_planes FP32 planes, which are the Adam masters, and every
+ * colour coefficient the step updates is also written, rounded to nearest
+ * even, to the 16-bit plane at g->sh16 (an output here); sp is then
+ * required. A forward on the same g (lgs_preprocess) reads the 16-bit
+ * planes. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
                                    const lgs_camera *cam, const lgs_splats *sp, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream);
+
+/* dst[k][i] = src[k][i] rounded to nearest even in dtype (LGS_SH_BF16 or
+ * LGS_SH_F16), planes k < n_planes, rows i < n; src float32 planes of stride
+ * src_stride, dst 16-bit planes of stride dst_stride (device). The 16-bit
+ * colour copy of FP32 colour planes (e.g. after a Morton re-sort). */
+lgs_status lgs_round_planes(const float *src, int64_t src_stride, void *dst, int64_t dst_stride,
+                            int32_t n_planes, int64_t n, int32_t dtype, lgs_stream stream);
 
 /* ------------------------------------------------------------------------
  * Densification (Sec. 3.3; the step after a8 that consumes its metric).

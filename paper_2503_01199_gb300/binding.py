@@ -36,7 +36,7 @@ ENTRY_POINTS = (
     "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd",
     "lgs_raster_bwd_det_workspace_size", "lgs_raster_bwd_deterministic", "lgs_get_det_overflow",
     "lgs_opacity_variance", "lgs_preprocess_bwd",
-    "lgs_adam_step", "lgs_preprocess_bwd_adam", "lgs_moments_accumulate", "lgs_moments_metric",
+    "lgs_adam_step", "lgs_preprocess_bwd_adam", "lgs_round_planes", "lgs_moments_accumulate", "lgs_moments_metric",
     "lgs_densify_workspace_size", "lgs_densify", "lgs_opacity_decay",
 )
 
@@ -130,6 +130,7 @@ def load(build_if_missing: bool = True):
         "lgs_adam_step": (i32, [P, P, P, P, i64, i32, P, f32, f32, f32, i32, P, P, i64, P]),
         "lgs_preprocess_bwd_adam": (i32, [P, P, P, P, P, P, P, P, P, f32, f32, f32, i32, P]),
         "lgs_moments_accumulate": (i32, [P, P, P, i64, P, P, P, P]),
+        "lgs_round_planes": (i32, [P, i64, P, i64, i32, i64, i32, P]),
         "lgs_moments_metric": (i32, [P, P, P, i64, P, P]),
         "lgs_densify_workspace_size": (sz, [i64]),
         "lgs_densify": (i32, [P, P, P, P, i64, f32, P, P, P, P, sz, P]),
@@ -406,6 +407,14 @@ def lgs_raster_bwd_deterministic(sp: LgsSplats, vals, tile_ranges, cam: LgsCamer
         int(precision), _ptr(final_T), _ptr(last_contrib), _ptr(dL_dimage), _ptr(grad_acc),
         grad_acc.shape[0], _ptr(workspace), workspace.numel() * workspace.element_size(),
         _stream(stream)), "lgs_raster_bwd_deterministic")
+
+
+def lgs_round_planes(src, dst, n_planes: int, n: int, stream=None):
+    """dst (bfloat16 / float16 planes) = src (float32 planes) rounded, rows < n."""
+    L = load()
+    dtype = {torch.bfloat16: LGS_SH_BF16, torch.float16: LGS_SH_F16}[dst.dtype]
+    _check(L.lgs_round_planes(_ptr(src), src.shape[-1], _ptr(dst), dst.shape[-1], int(n_planes),
+                              int(n), dtype, _stream(stream)), "lgs_round_planes")
 
 
 def lgs_get_det_overflow() -> int:

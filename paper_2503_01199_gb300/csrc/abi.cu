@@ -32,6 +32,8 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
                                const int32_t *d_V, const lgs_camera *cam, const float *rec,
                                float *gacc, const float *lr, float b1, float b2, float eps,
                                int step, cudaStream_t s);
+lgs_status round_planes(const float *src, int64_t src_stride, void *dst, int64_t dst_stride,
+                        int n_planes, int64_t n, int dtype, cudaStream_t s);
 lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t stride, int np,
                      const float *lr, float b1, float b2, float eps, int step, const uint32_t *map,
                      const int32_t *d_V, int64_t max_rows, cudaStream_t s);
@@ -395,13 +397,24 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const lgs_camera *cam, const lgs_splats *sp, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
                                    int32_t step, lgs_stream stream) {
+    // 16-bit colour planes are accepted here as an extra output (the rounded
+    // copy of the updated FP32 coefficients), with the splat records only
     if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||
-        !aligned16(grad_acc) || !aligned16(m) || !aligned16(v) || training_only(g, cam) ||
-        (sp && bad_splats(sp, g->n)))
+        !aligned16(grad_acc) || !aligned16(m) || !aligned16(v) || cam->d_pose ||
+        (g->sh_dtype != LGS_SH_F32 && !sp) || (sp && bad_splats(sp, g->n)))
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
     return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, sp ? sp->rec : nullptr, grad_acc,
                                lr, beta1, beta2, eps, step, as_stream(stream));
+}
+
+lgs_status lgs_round_planes(const float *src, int64_t src_stride, void *dst, int64_t dst_stride,
+                            int32_t n_planes, int64_t n, int32_t dtype, lgs_stream stream) {
+    if (!src || !dst || n_planes < 0 || n < 0 || src_stride < n || dst_stride < n ||
+        (dtype != LGS_SH_BF16 && dtype != LGS_SH_F16))
+        return LGS_ERR_INVALID_ARG;
+    if (n_planes == 0 || n == 0) return LGS_OK;
+    return round_planes(src, src_stride, dst, dst_stride, n_planes, n, dtype, as_stream(stream));
 }
 
 lgs_status lgs_moments_accumulate(const float *grad_acc, const uint32_t *map,

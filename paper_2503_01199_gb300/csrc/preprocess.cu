@@ -4,6 +4,7 @@
 // One thread per compacted Gaussian j; row = map[j]. Parameter planes are
 // read with unit stride across the warp: a visible cluster is a run of
 // consecutive rows, so reads through the map stay coalesced.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -736,11 +737,21 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
 // then completes the centre's gradient and applies Adam to planes 0..2.
 constexpr int kStagesRec = 3;
 
+// FP32 x rounded to nearest even in the 16-bit colour storage type.
+__device__ __forceinline__ uint16_t round16(float x, int sh_dtype) {
+    return sh_dtype == LGS_SH_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(x))
+                                   : __half_as_ushort(__float2half_rn(x));
+}
+
+// With sh16 (16-bit colour planes of type sh_dtype, the planes' stride), every
+// colour coefficient the Adam step updates is also written there, rounded,
+// so that a forward that reads the 16-bit planes sees the updated values.
 template <int DEG>
 __global__ void __launch_bounds__(256, 4) k_bwd_adam_rec(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
     int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
-    const float *__restrict__ gacc, const float *__restrict__ rec, AdamArgs a) {
+    const float *__restrict__ gacc, const float *__restrict__ rec, AdamArgs a,
+    uint16_t *__restrict__ sh16, int sh_dtype) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
     __shared__ float s_g[3][256], s_d[3][256], s_c[4][256];  // s_c: centre gradient, 1 / dist
     __shared__ int64_t s_row[256];
@@ -827,6 +838,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_rec(
                     P[at + ch * stride] = p;
                     Mo[at + ch * stride] = m;
                     Vo[at + ch * stride] = v;
+                    if (sh16) sh16[(3 * k + ch) * stride + row] = round16(p, sh_dtype);
                 }
                 sh_grad_single(k, dx, dy, dz, w, gdx, gdy, gdz);
             }
@@ -880,9 +892,31 @@ AdamArgs make_adam(const float *lr, int np, float b1, float b2, float eps, int s
     return a;
 }
 
+// dst[k][i] = src[k][i] rounded to the 16-bit type, rows i < n of n_planes.
+__global__ void __launch_bounds__(256) k_round_planes(const float *__restrict__ src,
+                                                     int64_t src_stride,
+                                                     uint16_t *__restrict__ dst,
+                                                     int64_t dst_stride, int n_planes, int64_t n,
+                                                     int dtype) {
+    const int64_t total = (int64_t)n_planes * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / n, i = t - k * n;
+        dst[k * dst_stride + i] = round16(src[k * src_stride + i], dtype);
+    }
+}
+
 }  // namespace
 
 DEBUG_TU(preprocess)
+
+lgs_status round_planes(const float *src, int64_t src_stride, void *dst, int64_t dst_stride,
+                        int n_planes, int64_t n, int dtype, cudaStream_t s) {
+    count_launch();
+    k_round_planes<<<grid_for((int64_t)n_planes * n, 256, 16), 256, 0, s>>>(
+        src, src_stride, static_cast<uint16_t *>(dst), dst_stride, n_planes, n, dtype);
+    return check_launch();
+}
 
 lgs_status preprocess(const lgs_gaussians *g, const uint32_t *map, const int32_t *d_V,
                       const lgs_camera *cam, int tw, int th, const lgs_splats *out,
@@ -932,11 +966,14 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
     const unsigned gf = grid_for(g->n, 256, 8);
     count_launch();
     if (rec) {
+        uint16_t *sh16 = g->sh_dtype != LGS_SH_F32
+                             ? static_cast<uint16_t *>(const_cast<void *>(g->sh16)) : nullptr;
+        const int st = g->sh_dtype;
         switch (g->sh_degree) {
-        case 0: k_bwd_adam_rec<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
-        case 1: k_bwd_adam_rec<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
-        case 2: k_bwd_adam_rec<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
-        default: k_bwd_adam_rec<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a); break;
+        case 0: k_bwd_adam_rec<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
+        case 1: k_bwd_adam_rec<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
+        case 2: k_bwd_adam_rec<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
+        default: k_bwd_adam_rec<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
         }
         return check_launch();
     }

@@ -76,6 +76,10 @@ class StepConfig:
     ccc: bool = True
     # raster blend precision: B.LGS_FP32, LGS_MIXED_FP16 or LGS_MIXED_BF16
     precision: int = 0
+    # colour coefficients read by the forward: "fp32", or "bf16" / "fp16" (a
+    # rounded 16-bit copy of the FP32 planes, which stay the Adam masters;
+    # the fused optimizer keeps the copy up to date, so fused=True only)
+    sh_precision: str = "fp32"
     # every this many steps, step() reads the binning's overflow flag (a
     # host synchronisation; skipped while a CUDA graph is being captured)
     # and raises if any binning since the last read needed more pairs than
@@ -141,6 +145,14 @@ class Trainer:
         self.lr = lr_per_plane(self.sh_degree, self.cfg.lr)
         self.step_count = 0
         self.splats = B.splats_struct(self.rec, self.depth, self.radius)
+        sh_types = {"fp32": None, "bf16": torch.bfloat16, "fp16": torch.float16}
+        if self.cfg.sh_precision not in sh_types:
+            raise ValueError(f"sh_precision must be one of {sorted(sh_types)}")
+        self.sh16 = None
+        if sh_types[self.cfg.sh_precision] is not None:
+            self.sh16 = torch.zeros((self.np_ - 11, self.stride),
+                                    dtype=sh_types[self.cfg.sh_precision], device=dev)
+            self._round_sh16()
 
     # -- views ------------------------------------------------------------
     def _map(self):
@@ -162,7 +174,17 @@ class Trainer:
         return self.state[self.cur, 2]
 
     def gaussians(self) -> B.LgsGaussians:
+        return B.gaussians_struct(self.params, self.n, self.sh_degree, sh16=self.sh16)
+
+    def _g32(self) -> B.LgsGaussians:
+        """The parameters with their FP32 colour planes (the calls that
+        change parameters other than through Adam take these)."""
         return B.gaussians_struct(self.params, self.n, self.sh_degree)
+
+    def _round_sh16(self):
+        """The 16-bit colour copy of the FP32 colour planes (all live rows)."""
+        if self.sh16 is not None:
+            B.lgs_round_planes(self.params[11:], self.sh16, self.np_ - 11, self.n)
 
     # -- steps ------------------------------------------------------------
     def morton_reorder(self):
@@ -171,6 +193,7 @@ class Trainer:
         dst = self.state[self.cur ^ 1].view(3 * self.np_, self.stride)
         B.lgs_morton_reorder(src, dst, self.n, 3 * self.np_, self.codes, self.perm, self.ws_morton)
         self.cur ^= 1
+        self._round_sh16()
 
     def render(self, cam: dict, camst: B.LgsCamera | None = None):
         """a2..a5 for one camera: cull, preprocess, bin, forward."""
@@ -205,7 +228,7 @@ class Trainer:
         variance summed over the views since the last call, then Morton
         re-sort (Sec. 3.2.1). Returns the number of Gaussians added."""
         max_new = min(int(max_new), self.capacity - self.n)
-        g = self.gaussians()
+        g = self._g32()
         B.lgs_moments_metric(self.S_acc, self.M_acc, self.C_acc, self.n, self.metric)
         gen = torch.Generator(device=self.dev).manual_seed(seed)
         normals = torch.randn((max(max_new, 1), 2, 3), generator=gen, device=self.dev)
@@ -222,7 +245,7 @@ class Trainer:
 
     def opacity_decay(self):
         """Halves every activated opacity (Sec. 3.3)."""
-        B.lgs_opacity_decay(self.gaussians())
+        B.lgs_opacity_decay(self._g32())
 
     def optimize(self, cs: B.LgsCamera, fused=True):
         """a9 + a10: preprocess backward and Adam on the visible rows."""
@@ -234,6 +257,8 @@ class Trainer:
                                       self.lr, c.beta1, c.beta2, c.eps, self.step_count,
                                       splats=self.splats)
         else:
+            if self.sh16 is not None:
+                raise ValueError("a 16-bit colour copy is kept up to date by the fused optimizer only")
             if self.grad_planes is None:
                 self.grad_planes = torch.zeros((self.np_, self.stride), dtype=torch.float32,
                                                device=self.dev)
@@ -269,6 +294,7 @@ class Trainer:
                 st[k, :, :n].copy_(torch.from_numpy(np.ascontiguousarray(z[name])).to(self.dev))
             self.n = n
             self.step_count = int(z["step_count"])
+        self._round_sh16()
 
     def check_overflow(self) -> None:
         """Raises LgsError if a binning since the last check needed more

@@ -192,7 +192,8 @@ class ResidentScene:
         ws = torch.empty(B.lgs_morton_workspace_size(self.n), dtype=torch.uint8, device=device)
         B.lgs_morton_reorder(full, dst, self.n, npl, codes, perm, ws)
         self.geom = dst[:11].contiguous()
-        self.sh16 = dst[11:].to(sh_dtype).contiguous()
+        self.sh16 = torch.zeros((npl - 11, self.stride), dtype=sh_dtype, device=device)
+        B.lgs_round_planes(dst[11:], self.sh16, npl - 11, self.n)
         del full, dst, codes, perm, ws
 
     def struct(self) -> B.LgsGaussians:

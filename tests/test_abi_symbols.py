@@ -119,7 +119,12 @@ def test_capacity_and_grid_rules_are_checked_on_the_host():
     posed.d_pose = buf(48).value                                     # training takes a host pose
     assert fused(g, sp, cam_=posed) == bad
     g16 = B.LgsGaussians(planes.value, n, stride, deg, B.LGS_SH_BF16, buf(2 * 48 * stride).value)
-    assert fused(g16, sp) == bad                                     # FP32 colour planes only
+    assert fused(g16, None) == bad                                   # 16-bit copy needs the records
+    assert L.lgs_preprocess_bwd(ctypes.byref(g16), rowmap, nvis, ctypes.byref(cam), gacc,
+                                buf(4 * 59 * stride), 0, None) == bad  # separate backward: FP32 only
+    h16 = buf(2 * 48 * stride)
+    assert L.lgs_round_planes(planes, stride, h16, stride, 48, n, 7, None) == bad   # bad dtype
+    assert L.lgs_round_planes(planes, stride, h16, n - 1, 48, n, B.LGS_SH_BF16, None) == bad
     skew = B.LgsGaussians(planes.value, n, stride + 2, deg, B.LGS_SH_F32, None)
     assert fused(skew, sp) == bad                                    # stride a multiple of 4
 

@@ -59,3 +59,51 @@ def test_mixed_precision_error_within_stated_bounds(oracle_cases, scene, prec):
         r = U.rel_l2(gg[sl][:, rows], og[sl][:, rows])
         assert r <= b["grad"], (name, r)
     assert U.rel_l2(gm[rows], om[rows]) <= b["metric"]
+
+
+SH16_BOUNDS = {"fp16": {"img_max": 5e-3, "img_mean": 5e-5, "grad": 1e-2, "metric": 1e-2},
+               "bf16": {"img_max": 2e-2, "img_mean": 5e-4, "grad": 8e-2, "metric": 2e-1}}
+
+
+@pytest.mark.parametrize("sh", ["fp16", "bf16"])
+def test_sixteen_bit_colour_training_step(orc, sh):
+    """The mixed variant with the colour coefficients in 16 bits as well
+    (blend and SH in FP16 / BF16, FP32 masters for Adam): after a step the
+    16-bit copy is the rounded FP32 masters bit for bit; the image against
+    the FP64 oracle and the raster gradients and metric against the FP32
+    step within the stated bounds (the blend's and about the coefficients'
+    relative rounding, 2^-11 / 2^-8)."""
+    import torch
+    from paper_2503_01199_gb300 import binding as B
+    from paper_2503_01199_gb300 import pipeline as PL
+    d = scenegen.uniform_box_scene(20000, 3, 3, 256, 256)
+    sc, cam, tgt = d["scene"], d["camera"], U.t(d["target"])
+    prec = {"fp16": B.LGS_MIXED_FP16, "bf16": B.LGS_MIXED_BF16}[sh]
+    tr = PL.Trainer(sc, 256, 256, PL.StepConfig(precision=prec, sh_precision=sh))
+    ref = PL.Trainer(sc, 256, 256, PL.StepConfig())
+    for t in (tr, ref):
+        t.step(cam, tgt, reorder=True, fused=True)
+    torch.cuda.synchronize()
+    n = tr.n
+    masters = tr.params[11:, :n].contiguous()
+    np.testing.assert_array_equal(tr.sh16[:, :n].view(torch.int16).cpu().numpy(),
+                                  masters.to(tr.sh16.dtype).view(torch.int16).cpu().numpy())
+    with pytest.raises(ValueError):
+        tr.optimize(B.camera_struct(cam), fused=False)
+    b = SH16_BOUNDS[sh]
+    _, perm = orc.morton_reorder(sc)
+    s2 = {k: (np.asarray(v, np.float64)[perm] if k != "sh_degree" else v) for k, v in sc.items()}
+    cc = orc.cluster_cull(s2, cam, 128)
+    sub = {k: (v[cc["map"]] if k != "sh_degree" else v) for k, v in s2.items()}
+    oimg = orc.render_scene(sub, cam)["image"]
+    e = np.abs(tr.image.cpu().numpy() - oimg)
+    assert e.max() <= b["img_max"], e.max()
+    assert e.mean() <= b["img_mean"], e.mean()
+    V = int(tr.d_V.item())
+    assert V == int(ref.d_V.item())
+    ga, gr = tr.gacc[:V].cpu().numpy(), ref.gacc[:V].cpu().numpy()
+    for name, cols in (("centre", [0, 1]), ("conic", [2, 3, 4]), ("opacity", [5]),
+                       ("colour", [6, 7, 8])):
+        r = U.rel_l2(ga[:, cols], gr[:, cols])
+        assert r <= b["grad"], (name, r)
+    assert U.rel_l2(tr.metric[:n].cpu().numpy(), ref.metric[:n].cpu().numpy()) <= b["metric"]
