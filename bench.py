@@ -247,7 +247,7 @@ def run_multiview(tr, steps: int, warmup: int) -> dict:
             "pairs_per_view": pairs}
 
 
-def run_ccc_ablation(steps: int = 8, warmup: int = 2) -> dict:
+def run_ccc_ablation(steps: int = 24, warmup: int = 3) -> dict:
     """Iteration time (a2-a10) with Cluster-Cull-Compact on / off and with
     Morton-sorted / randomly shuffled storage (Sec. 3.2; the E3/E6 analogue),
     on the 500K surface scene with its orbit camera and on interior scenes
@@ -280,15 +280,19 @@ def run_ccc_ablation(steps: int = 8, warmup: int = 2) -> dict:
                 for _ in range(warmup):
                     tr.step(cs, target, reorder=False)
                 torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(steps):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+                ev[0].record()
+                for k in range(steps):
                     tr.step(cs, target, reorder=False)
-                e1.record()
+                    ev[k + 1].record()
                 torch.cuda.synchronize()
+                per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
                 V = int(tr.d_V.item()) if ccc else n
                 res[f"{order}_{'ccc' if ccc else 'no_ccc'}"] = {
-                    "ms_per_iter": round(e0.elapsed_time(e1) / steps, 4), "rows_processed": V}
+                    "ms_per_iter": round(float(per.mean()), 4),
+                    "ms_p10": round(float(np.percentile(per, 10)), 4),
+                    "ms_p90": round(float(np.percentile(per, 90)), 4),
+                    "steps": steps, "rows_processed": V}
                 del tr
                 torch.cuda.empty_cache()
         out[name] = res
