@@ -187,8 +187,11 @@ lgs_status lgs_cluster_cull_compact(const lgs_gaussians *g, const lgs_camera *ca
  *     Gaussians at 128 per cluster); larger inputs return LGS_ERR_TOO_LARGE
  *     and enqueue nothing.
  *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current). Make that first call before any
- *     stream capture.
+ *     per device, with that device current) and keeps it for the life of the
+ *     process. Make that first call before any stream capture. Calls must
+ *     not cross a device reset (cudaDeviceReset, or anything else that
+ *     destroys and re-creates the device's primary context): the kept
+ *     address would then be stale.
  *   - All calls share the one array, which keeps the last call's contents
  *     (nothing in it needs to start at zero). Calls that overlap on the GPU,
  *     e.g. on two streams without ordering between them, race on it: order

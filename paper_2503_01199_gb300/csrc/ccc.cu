@@ -312,7 +312,9 @@ std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[64] = {nullptr};
 
 // Device address of g_noalloc_scratch on the current device (looked up once
-// per device; in host code the symbol itself is not a device address).
+// per device and kept for the life of the process; in host code the symbol
+// itself is not a device address). A device reset would leave the kept
+// address stale; the entry point's contract excludes calls across one.
 lgs_status noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
