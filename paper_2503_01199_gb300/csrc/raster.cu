@@ -12,9 +12,9 @@
 // horizontal pair of pixels of it, in both passes.
 // In the backward each lane first sums a splat's per-pixel terms over its
 // two pixels (App. A.1's thread-local sum), the warp reduces the 12 sums
-// (9 gradients, S, M and the fragment count) with a reduce-scatter
-// butterfly (13 shuffles; value i ends on lanes 2i', 2i' + 1) and one lane
-// per value issues one atomic: one atomic per value per splat and quadrant
+// (9 gradients, S, M and the fragment count) through a transpose in shared
+// memory (value i ends on lanes 2i, 2i + 1) and one lane per value issues
+// one atomic: one atomic per value per splat and quadrant
 // (App. A.1 Eq. 5-6, the tile's reduction split over its four quadrant
 // warps). The per-pixel exponent moments are summed as sum qq, sum dx qq and
 // sum dx^2 qq over the lane's row (dy is the same for both pixels), which
@@ -305,41 +305,32 @@ __global__ void __launch_bounds__(kFwdThreads) k_raster_fwd(const float *__restr
     fwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, image, finalT, last, sm);
 }
 
-// Reduce-scatter of 12 values across the warp in 13 shuffles (halving the
-// vector at the butterfly stages on lane bits 4..1, 3 values padded to 4,
-// then one all-reduce step on bit 0): on return, lanes 2i and 2i + 1 both
-// hold the warp sum of value scatter12_index(2i), or a padding zero when
-// that index is -1.
-__device__ __forceinline__ float warp_reduce_scatter12(const float v[12], int lane) {
-    float w[6], x[3], y[2];
-    const bool b4 = lane & 16;  // 12 -> 6
+// Warp sums of 12 values through a transpose in shared memory: every lane
+// stores its 12 values as column `lane` of a 12 x 32 block (rows padded to
+// kRedStride floats, so that the 128-bit row reads below take no bank
+// conflict), then lane 2i + h (i < 12) adds the 16 entries of row i in
+// columns [16 h, 16 h + 16) in a fixed tree and one shuffle joins the two
+// halves: lanes 2i and 2i + 1 both return the warp sum of value i, lanes
+// 24..31 return 0. 12 stores, 4 loads, 17 additions and one shuffle in
+// place of a butterfly's 13 shuffles and their selects; the order of the
+// additions is fixed, so the result does not depend on timing.
+constexpr int kRedValues = 12;
+constexpr int kRedStride = 36;
+__device__ __forceinline__ float warp_sum12(const float v[kRedValues], float *buf, int lane) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const float send = b4 ? v[i] : v[i + 6];
-        const float keep = b4 ? v[i + 6] : v[i];
-        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    for (int i = 0; i < kRedValues; ++i) buf[i * kRedStride + lane] = v[i];
+    __syncwarp();
+    float r = 0.0f;
+    if (lane < 2 * kRedValues) {
+        const float4 *src =
+            reinterpret_cast<const float4 *>(buf + (lane >> 1) * kRedStride + 16 * (lane & 1));
+        const float4 p = src[0], q = src[1], t = src[2], u = src[3];
+        r = (((p.x + p.y) + (p.z + p.w)) + ((q.x + q.y) + (q.z + q.w))) +
+            (((t.x + t.y) + (t.z + t.w)) + ((u.x + u.y) + (u.z + u.w)));
     }
-    const bool b3 = lane & 8;  // 6 -> 3
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float send = b3 ? w[i] : w[i + 3];
-        const float keep = b3 ? w[i + 3] : w[i];
-        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    const bool b2 = lane & 4;  // 3 (+1) -> 2
-    y[0] = (b2 ? x[2] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[2], 4);
-    y[1] = (b2 ? 0.0f : x[1]) + __shfl_xor_sync(0xffffffffu, b2 ? x[1] : 0.0f, 4);
-    const bool b1 = lane & 2;  // 2 -> 1
-    const float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, b1 ? y[0] : y[1], 2);
-    return z + __shfl_xor_sync(0xffffffffu, z, 1);
-}
-
-// The value index warp_reduce_scatter12 leaves in `lane`:
-// 6 b4 + 3 b3 + (b2 ? 2 : b1), padding (-1) when b2 = b1 = 1.
-__device__ __forceinline__ int scatter12_index(int lane) {
-    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
-    const int base = 6 * b4 + 3 * b3;
-    return b2 ? (b1 ? -1 : base + 2) : base + b1;
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    __syncwarp();  // the block is reused by the warp's next splat
+    return r;
 }
 
 // Warp sum by the integer warp reduction of Sec. 3.1: the largest exponent
@@ -467,7 +458,8 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                                          int tile, const float *__restrict__ finalT,
                                          const int32_t *__restrict__ last,
                                          const float *__restrict__ dLdI, float *__restrict__ gacc,
-                                         unsigned long long *__restrict__ det, RasterSmem &sm) {
+                                         unsigned long long *__restrict__ det, RasterSmem &sm,
+                                         float *red_buf) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
     const int x = tx * kTile + 8 * (w & 1) + 2 * (lane & 3), y = ty * kTile + 8 * (w >> 1) + (lane >> 2);
@@ -501,7 +493,8 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
     if (lane == 0) atomicMax(&sm.maxlast, wmax);
     __syncthreads();
     const int maxlast = sm.maxlast;
-    const int vi = scatter12_index(lane);
+    const int vi = lane < 2 * kRedValues ? lane >> 1 : -1;
+    float *const wred = red_buf + w * (kRedValues * kRedStride);
     // positions maxlast-1 .. 0 of the tile list, 128 at a time from the back
     for (int end = maxlast; end > 0; end -= kBatch) {
         const int cnt = min(kBatch, end);
@@ -561,7 +554,7 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                 // syy = dy^2 Q0. Then dL/do, dL/dcolour, S, M (= dL/do) and
                 // the fragment count (exact in FP32).
                 const float dyQ0 = dy * Q0;
-                float v[12];
+                float v[kRedValues];
                 v[0] = kLn2 * (2.0f * s.a * Q1 + s.b * dyQ0);
                 v[1] = kLn2 * (s.b * Q1 + 2.0f * s.c * dyQ0);
                 v[2] = -0.5f * Q2;
@@ -605,7 +598,7 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                         }
                     }
                 } else {
-                    const float red = warp_reduce_scatter12(v, lane);
+                    const float red = warp_sum12(v, wred, lane);
                     if ((lane & 1) == 0 && vi >= 0) {
                         if (vi == 11)
                             atomicAdd(reinterpret_cast<unsigned int *>(row + 11), (unsigned int)red);
@@ -628,7 +621,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(
     const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc,
     unsigned long long *__restrict__ det) {
     __shared__ RasterSmem sm;
-    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, det, sm);
+    __shared__ __align__(16) float red[(kBwdThreads / 32) * kRedValues * kRedStride];
+    bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, det, sm, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -679,6 +673,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd_batch(const lgs_view
                                                              int n_views, uint32_t total_tiles,
                                                              uint32_t *counter) {
     __shared__ RasterSmem sm;
+    __shared__ __align__(16) float red[(kBwdThreads / 32) * kRedValues * kRedStride];
     __shared__ uint32_t s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
@@ -689,7 +684,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd_batch(const lgs_view
         const lgs_view &V = views[v];
         const RCam K = view_rcam(V);
         bwd_tile<PREC>(V.rec, V.vals, V.tile_ranges, K, (int)(t - V.tile_offset), V.final_T,
-                       V.last_contrib, V.dL_dimage, V.grad_acc, nullptr, sm);
+                       V.last_contrib, V.dL_dimage, V.grad_acc, nullptr, sm, red);
         __syncthreads();
     }
 }

@@ -2,8 +2,8 @@
 cross-tile accumulation of Sec. 3.1's reduction made order-independent by
 exact fixed-point integer sums.
 
-- Two calls on the same inputs give identical bits, with the float
-  reduce-scatter and with the integer warp reduction, and at the full-size
+- Two calls on the same inputs give identical bits, with the float warp
+  sum and with the integer warp reduction, and at the full-size
   bench workload.
 - The values are the oracle's within the FP32 gradient tolerance, and the
   float-atomic path's within the rounding of its atomics.
