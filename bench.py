@@ -368,7 +368,10 @@ def run_gpu(args) -> dict | None:
     if not morton:  # rows in a random order, never re-sorted (profiling evidence only)
         perm = np.random.default_rng(9).permutation(sc["mean"].shape[0])
         sc = {k: (np.asarray(v)[perm] if k != "sh_degree" else v) for k, v in sc.items()}
-    tr = PL.Trainer(sc, W_IMG, H_IMG, PL.StepConfig(tile=TILE, pair_capacity=128_000_000),
+    # the profiling case's pair capacity scales with its scene, so that a
+    # capture of it holds a small device footprint (22.1M pairs at 3M)
+    cap = 128_000_000 if not args.n_gaussians else max(16_000_000, 16 * args.n_gaussians)
+    tr = PL.Trainer(sc, W_IMG, H_IMG, PL.StepConfig(tile=TILE, pair_capacity=cap),
                     device=str(dev))
     del sc
     cs = B.camera_struct(cam)
@@ -527,7 +530,8 @@ def run_gpu(args) -> dict | None:
     tr.state[tr.cur].copy_(snapshot)
     tr.step_count = step_count0
     del snapshot
-    multiview = run_multiview(tr, max(args.steps // 2, 3), 2) if world == 1 else None
+    multiview = (run_multiview(tr, max(args.steps // 2, 3), 2)
+                 if world == 1 and not args.n_gaussians else None)
     clk = clocks.stop()
     loss_val = float(loss_host.item())
     if world > 1:
