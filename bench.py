@@ -185,6 +185,17 @@ def recorded_traffic(key: str, units: float | None = None) -> int | None:
     return None
 
 
+def recorded_count(key: str) -> int | None:
+    """An ncu event count of one launch of the recorded kernel `key` at the
+    bench workload (count_per_launch); None when its sources changed since
+    the capture or nothing was recorded."""
+    rec = traffic_record().get(key, {})
+    files = tuple(rec.get("source_files", FUSED_SOURCES))
+    if not rec or rec.get("source") != source_digest(files) or "count_per_launch" not in rec:
+        return None
+    return int(rec["count_per_launch"])
+
+
 def max_over_ranks(values, device) -> list:
     """Elementwise maximum of every rank's values (the slowest rank's times),
     over the initialised process group; the values themselves with none."""
@@ -346,6 +357,44 @@ def run_extra_configs(steps: int, warmup: int) -> dict:
 
 STAGES = ["a1_morton", "a2_cull", "a3_preprocess", "a4_bin_sort", "a5_raster_fwd", "a6_loss",
           "a7_raster_bwd", "a8_variance", "a9a10_bwd_adam"]
+
+
+def measure_unit_peaks(dev, n_sms: int, reps: int = 5) -> dict:
+    """Unit rates of this GPU from the library's own microbenchmarks
+    (lgs_peak_*; outside every timed region): the special-function unit's
+    ex2, FP32 FMA in the scalar and the packed two-lane form, and float
+    reductions into global memory in the backward's pattern (12 lanes into
+    one 64-byte row) on 64 MB of rows (L2-resident) and on 192 MB (larger
+    than L2, the size class of the 3M scene's 175 MB of gradient rows).
+    Each rate is the operation count of `reps` calls over their CUDA-event
+    time, after one untimed call."""
+    import torch
+    from paper_2503_01199_gb300 import binding as B
+    blocks = n_sms * 8
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(blocks * B.PEAK_THREADS, dtype=torch.float32, device=dev)
+    rows_l2 = torch.zeros((1 << 20, 16), dtype=torch.float32, device=dev)
+    rows_big = torch.zeros((3 << 20, 16), dtype=torch.float32, device=dev)
+
+    def rate(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = sum(fn() for _ in range(reps))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return n / (e0.elapsed_time(e1) * 1e-3)
+
+    res = {"ex2_per_s": rate(lambda: B.lgs_peak_ex2(out, blocks, 256)),
+           "ffma_per_s": rate(lambda: B.lgs_peak_ffma(out, blocks, 1024, False)),
+           "ffma2_fma_per_s": rate(lambda: B.lgs_peak_ffma(out, blocks, 1024, True)),
+           "red_l2_per_s": rate(lambda: B.lgs_peak_red(rows_l2, rows_l2.shape[0], blocks, 1024)),
+           "red_192mb_per_s": rate(lambda: B.lgs_peak_red(rows_big, rows_big.shape[0], blocks,
+                                                           1024))}
+    del out, rows_l2, rows_big
+    return {**{k: float(f"{v:.4g}") for k, v in res.items()}, "blocks": blocks,
+            "method": "lgs_peak_ex2 / lgs_peak_ffma / lgs_peak_red, CUDA events, "
+                      f"{reps} calls after one untimed call"}
 
 
 def run_gpu(args) -> dict | None:
@@ -563,6 +612,29 @@ def run_gpu(args) -> dict | None:
     ops_bwd, ops_fwd = 30, 9
     bwd_t = F * ops_bwd / (stage_ms["a7_raster_bwd"] * 1e-3) / 1e12
     fwd_t = F * ops_fwd / (stage_ms["a5_raster_fwd"] * 1e-3) / 1e12
+    units = measure_unit_peaks(dev, n_sms)
+    # the raster's other units: one ex2 per fragment in each pass (the
+    # backward adds a reciprocal on the same unit), and the backward's float
+    # reductions (12 per contributing (quadrant warp, splat), counted by ncu
+    # on the bench workload; null when the raster sources changed since)
+    a5_s, a7_s = stage_ms["a5_raster_fwd"] * 1e-3, stage_ms["a7_raster_bwd"] * 1e-3
+    red_instr = (recorded_count("a7_raster_bwd_red")
+                 if not args.n_gaussians and morton else None)
+    red_per_s = 12 * red_instr / a7_s if red_instr else None
+    unit_rates = {
+        "measured": units,
+        "a5_ex2": {"per_launch": F, "achieved_per_s": float(f"{F / a5_s:.4g}"),
+                   "frac": round(F / a5_s / units["ex2_per_s"], 4)},
+        "a7_mufu": {"per_launch": 2 * F, "achieved_per_s": float(f"{2 * F / a7_s:.4g}"),
+                    "frac": round(2 * F / a7_s / units["ex2_per_s"], 4),
+                    "note": "ex2 and the reciprocal of 1 - alpha per fragment"},
+        "a7_red": {"per_launch": 12 * red_instr if red_instr else None,
+                   "achieved_per_s": float(f"{red_per_s:.4g}") if red_per_s else None,
+                   "frac_of_l2": round(red_per_s / units["red_l2_per_s"], 4) if red_per_s else None,
+                   "frac_of_192mb": (round(red_per_s / units["red_192mb_per_s"], 4)
+                                     if red_per_s else None)},
+        "fp32_lane_rate_vs_measured_ffma": round(fp32_peak * 1e12 / units["ffma_per_s"], 4),
+    }
     peak_src = (f"derived: {n_sms} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (sampled SM clock), "
                 "one operation per lane per cycle (an FMA as one operation)")
     roofline = {"kernel": "lgs_raster_bwd (k_raster_bwd<0>)", "bound": "alu",
@@ -603,6 +675,7 @@ def run_gpu(args) -> dict | None:
         "counts": {"visible_gaussians": V, "pairs": P, "fragments": F},
         "roofline": roofline,
         "roofline_other": other,
+        "unit_rates": unit_rates,
         "mixed": mixed,
         "batched_views": multiview,
         "a1_morton_resort": {

@@ -538,6 +538,40 @@ lgs_status lgs_densify(const lgs_gaussians *g, float *m, float *v, const float *
                        size_t workspace_bytes, lgs_stream stream);
 lgs_status lgs_opacity_decay(const lgs_gaussians *g, lgs_stream stream);
 
+/* ----------------------------------------------------------------------
+ * Unit-rate microbenchmarks (measurement helpers, not part of the training
+ * path): the denominators of the raster kernels' rooflines, measured on the
+ * device they run on. The caller times each call (CUDA events on `stream`)
+ * and divides the operation count below by the time. Each kernel runs
+ * `blocks` CTAs of 256 threads (1 <= blocks <= 2^20; a multiple of the SM
+ * count times 8 fills every SM); iters >= 1; every loop has a fixed trip
+ * count, so a call cannot hang.
+ *
+ * lgs_peak_ex2: each thread a dependent chain of 32 * iters base-2
+ * exponentials on the special-function unit (ex2.approx, as in the raster),
+ * x <- 2^x - 1.5: blocks * 256 * 32 * iters exponentials. out: device,
+ * blocks * 256 floats (the chains' ends, so that the work is kept).
+ *
+ * lgs_peak_ffma: each thread a dependent chain of 32 * iters fused
+ * multiply-adds, scalar FP32 (packed = 0: blocks * 256 * 32 * iters FMAs)
+ * or the packed two-lane FP32 form on a float2 (packed = 1: twice as many
+ * FMAs in as many instructions). out as above.
+ *
+ * lgs_peak_red: each warp, iters times, draws a row in [0, n_rows) by a
+ * hash and its lanes 0..11 add 1.0f to floats 0..11 of that 16-float row
+ * with float reductions into global memory (the backward's pattern:
+ * 12 values of one 64-byte gradient row per warp instruction):
+ * blocks * 8 * 12 * iters reductions. rows: device, 16-byte aligned,
+ * n_rows * 16 floats (1 <= n_rows < 2^31), contents incremented.
+ * Errors: LGS_ERR_INVALID_ARG for a null buffer or an argument out of range
+ * (nothing enqueued), LGS_ERR_CUDA if the launch fails.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_peak_ex2(float *out, int32_t blocks, int32_t iters, lgs_stream stream);
+lgs_status lgs_peak_ffma(float *out, int32_t blocks, int32_t iters, int32_t packed,
+                         lgs_stream stream);
+lgs_status lgs_peak_red(float *rows, int64_t n_rows, int32_t blocks, int32_t iters,
+                        lgs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

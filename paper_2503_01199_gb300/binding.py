@@ -38,6 +38,7 @@ ENTRY_POINTS = (
     "lgs_opacity_variance", "lgs_preprocess_bwd",
     "lgs_adam_step", "lgs_preprocess_bwd_adam", "lgs_round_planes", "lgs_moments_accumulate", "lgs_moments_metric",
     "lgs_densify_workspace_size", "lgs_densify", "lgs_opacity_decay",
+    "lgs_peak_ex2", "lgs_peak_ffma", "lgs_peak_red",
 )
 
 
@@ -135,6 +136,9 @@ def load(build_if_missing: bool = True):
         "lgs_densify_workspace_size": (sz, [i64]),
         "lgs_densify": (i32, [P, P, P, P, i64, f32, P, P, P, P, sz, P]),
         "lgs_opacity_decay": (i32, [P, P]),
+        "lgs_peak_ex2": (i32, [P, i32, i32, P]),
+        "lgs_peak_ffma": (i32, [P, i32, i32, i32, P]),
+        "lgs_peak_red": (i32, [P, i64, i32, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -498,3 +502,31 @@ def lgs_densify(g: LgsGaussians, m, v, metric, max_new, split_scale, normals, d_
 def lgs_opacity_decay(g: LgsGaussians, stream=None):
     L = load()
     _check(L.lgs_opacity_decay(ctypes.byref(g), _stream(stream)), "lgs_opacity_decay")
+
+
+# ---- unit-rate microbenchmarks (measurement helpers; counts per call)
+PEAK_THREADS = 256
+PEAK_UNROLL = 32
+
+
+def lgs_peak_ex2(out, blocks: int, iters: int, stream=None) -> int:
+    """Enqueues the ex2 chain; returns the number of exponentials."""
+    L = load()
+    _check(L.lgs_peak_ex2(_ptr(out), int(blocks), int(iters), _stream(stream)), "lgs_peak_ex2")
+    return blocks * PEAK_THREADS * PEAK_UNROLL * iters
+
+
+def lgs_peak_ffma(out, blocks: int, iters: int, packed: bool, stream=None) -> int:
+    """Enqueues the FMA chain (scalar or packed); returns the number of FMAs."""
+    L = load()
+    _check(L.lgs_peak_ffma(_ptr(out), int(blocks), int(iters), int(bool(packed)), _stream(stream)),
+           "lgs_peak_ffma")
+    return blocks * PEAK_THREADS * PEAK_UNROLL * iters * (2 if packed else 1)
+
+
+def lgs_peak_red(rows, n_rows: int, blocks: int, iters: int, stream=None) -> int:
+    """Enqueues the float reductions into rows; returns their number."""
+    L = load()
+    _check(L.lgs_peak_red(_ptr(rows), int(n_rows), int(blocks), int(iters), _stream(stream)),
+           "lgs_peak_red")
+    return blocks * (PEAK_THREADS // 32) * 12 * iters

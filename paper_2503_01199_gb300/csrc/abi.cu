@@ -70,6 +70,9 @@ lgs_status moments_metric(const float *S, const float *M, const uint32_t *C, int
                           float *metric, cudaStream_t s);
 lgs_status opacity_variance(const float *gacc, const uint32_t *map, const int32_t *d_V,
                             int64_t max_rows, float *out, cudaStream_t s);
+lgs_status peak_ex2(float *out, int blocks, int iters, cudaStream_t s);
+lgs_status peak_ffma(float *out, int blocks, int iters, int packed, cudaStream_t s);
+lgs_status peak_red(float *rows, int64_t n_rows, int blocks, int iters, cudaStream_t s);
 
 namespace {
 thread_local int32_t t_last_error = 0;
@@ -451,6 +454,20 @@ lgs_status lgs_opacity_decay(const lgs_gaussians *g, lgs_stream stream) {
     if (bad_gaussians(g) || g->sh_dtype != LGS_SH_F32) return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
     return opacity_decay(g, as_stream(stream));
+}
+
+lgs_status lgs_peak_ex2(float *out, int32_t blocks, int32_t iters, lgs_stream stream) {
+    return peak_ex2(out, blocks, iters, as_stream(stream));
+}
+
+lgs_status lgs_peak_ffma(float *out, int32_t blocks, int32_t iters, int32_t packed,
+                         lgs_stream stream) {
+    return peak_ffma(out, blocks, iters, packed, as_stream(stream));
+}
+
+lgs_status lgs_peak_red(float *rows, int64_t n_rows, int32_t blocks, int32_t iters,
+                        lgs_stream stream) {
+    return peak_red(rows, n_rows, blocks, iters, as_stream(stream));
 }
 
 }  // extern "C"

@@ -52,6 +52,18 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert L.lgs_adam_step(None, None, None, None, 0, 0, None, 0.9, 0.999, 1e-15, 1, None, None, 0,
                            None) == B.LGS_ERR_INVALID_ARG
     assert L.lgs_bin_sort_workspace_size(1000, 100000, 64) > 100000 * 6
+    # unit-rate microbenchmarks: null buffers, sizes and counts out of range
+    assert L.lgs_peak_ex2(None, 8, 1, None) == B.LGS_ERR_INVALID_ARG
+    assert L.lgs_peak_ffma(None, 8, 1, 1, None) == B.LGS_ERR_INVALID_ARG
+    assert L.lgs_peak_red(None, 16, 8, 1, None) == B.LGS_ERR_INVALID_ARG
+    # (a host buffer: every call below is refused before any launch)
+    raw, addr = _aligned(16 * 16 * 4)
+    ptr = ctypes.c_void_p(addr)
+    assert L.lgs_peak_ex2(ptr, 0, 1, None) == B.LGS_ERR_INVALID_ARG
+    assert L.lgs_peak_ffma(ptr, 8, 0, 0, None) == B.LGS_ERR_INVALID_ARG
+    assert L.lgs_peak_red(ptr, 0, 8, 1, None) == B.LGS_ERR_INVALID_ARG
+    assert L.lgs_peak_red(ptr, 1 << 31, 8, 1, None) == B.LGS_ERR_INVALID_ARG
+    assert L.lgs_peak_red(ctypes.c_void_p(addr + 4), 16, 8, 1, None) == B.LGS_ERR_INVALID_ARG
 
 
 def _aligned(nbytes: int):
