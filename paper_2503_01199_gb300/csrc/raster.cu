@@ -19,6 +19,11 @@
 // warps). The per-pixel exponent moments are summed as sum qq, sum dx qq and
 // sum dx^2 qq over the lane's row (dy is the same for both pixels), which
 // gives the five conic and centre sums with dy applied once per splat.
+// The backward evaluates its two pixels with packed two-lane FP32
+// operations (one instruction for the pair, each lane rounded as the scalar
+// operation), from a staged splat that holds each value twice; the forward
+// keeps scalar operations, which measured faster there (a lane leaves its
+// splat loop when both its pixels have ended).
 //
 // The exponent is evaluated in base 2: power log2(e) = dx (a dx + b dy) +
 // c dy^2 with a = -A log2(e) / 2, b = -B log2(e), c = -C log2(e) / 2, so that
@@ -48,7 +53,7 @@ constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
-// A staged splat: 3 x 16 bytes, read with three vector loads.
+// A splat staged for the forward: 3 x 16 bytes, read with three vector loads.
 struct __align__(16) SplatS {
     float u, v, a, b, c, o;  // centre, exponent coefficients (base 2), opacity
     float r, g, bl;          // colour
@@ -56,6 +61,22 @@ struct __align__(16) SplatS {
     uint32_t id;             // splat index (gradient row)
     float pad;
 };
+
+// A splat staged for the backward: 5 x 16 bytes. A lane works on two
+// pixels at once in packed two-lane FP32 arithmetic (one instruction for both pixels, each
+// lane rounded as the scalar operation), so every value it combines with a
+// pixel pair is stored twice: a vector load then leaves the pair in a
+// register pair.
+struct __align__(16) SplatP {
+    float2 u, v;     // centre
+    float2 a, b, c;  // exponent coefficients (base 2)
+    float2 o;        // opacity
+    float2 r, g, bl; // colour
+    uint32_t oh;     // o as a 16-bit pair (mixed precision only)
+    uint32_t id;     // splat index (gradient row)
+};
+
+__device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
 struct RCam {
     int W, H, gx, ntiles;
@@ -105,16 +126,10 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // special-function unit), with slack far above that arithmetic's error: the
 // y extent and the interval are widened by 2e-3 of the ellipse's extent plus
 // 1e-2 pixel. A conic that is not positive definite reaches every quadrant.
+// The staged values of record j (x = u, v, A, B; y = C, o, r, g; z = b, tau):
+// the conic scaled to base 2, o also as a 16-bit pair, the row index.
 template <int PREC>
-__device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_t j,
-                                          int64_t nrows, float x0, float y0, SplatS &s) {
-    if (!LGS_DCHECK((int64_t)j < nrows, kSiteRasterSplat)) {
-        s = SplatS{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, 0.f};
-        return 0u;  // reaches no quadrant
-    }
-    const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)j);
-    const float4 x = __ldg(p), y = __ldg(p + 1);
-    const float2 z = __ldg(reinterpret_cast<const float2 *>(rec + 12 * (int64_t)j + 8));
+__device__ __forceinline__ void fill_splat(SplatS &s, float4 x, float4 y, float2 z, uint32_t j) {
     SplatS t;
     t.u = x.x;
     t.v = x.y;
@@ -129,6 +144,37 @@ __device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_
     t.id = j;
     t.pad = 0.0f;
     s = t;
+}
+
+template <int PREC>
+__device__ __forceinline__ void fill_splat(SplatP &s, float4 x, float4 y, float2 z, uint32_t j) {
+    SplatP t;
+    t.u = dup(x.x);
+    t.v = dup(x.y);
+    t.a = dup(__fmul_rn(x.z, -0.5f * kLog2e));
+    t.b = dup(__fmul_rn(x.w, -kLog2e));
+    t.c = dup(__fmul_rn(y.x, -0.5f * kLog2e));
+    t.o = dup(y.y);
+    t.r = dup(y.z);
+    t.g = dup(y.w);
+    t.bl = dup(z.x);
+    t.oh = pack_pair<PREC>(y.y);
+    t.id = j;
+    s = t;
+}
+
+template <int PREC, class S>
+__device__ __forceinline__ uint32_t stage(const float *__restrict__ rec, uint32_t j,
+                                          int64_t nrows, float x0, float y0, S &s) {
+    if (!LGS_DCHECK((int64_t)j < nrows, kSiteRasterSplat)) {
+        fill_splat<PREC>(s, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                         make_float2(0.f, 0.f), 0u);
+        return 0u;  // reaches no quadrant
+    }
+    const float4 *p = reinterpret_cast<const float4 *>(rec + 12 * (int64_t)j);
+    const float4 x = __ldg(p), y = __ldg(p + 1);
+    const float2 z = __ldg(reinterpret_cast<const float2 *>(rec + 12 * (int64_t)j + 8));
+    fill_splat<PREC>(s, x, y, z, j);
     const float A = x.z, B = x.w, C = y.x, tau = z.y;
     if (!(tau >= 0.0f)) return 0u;
     const float det = A * C - B * B;
@@ -215,11 +261,62 @@ __device__ __forceinline__ void blend2(const SplatS &s, float p0, float p1, floa
     }
 }
 
-struct RasterSmem {
-    SplatS sp[kBatch];
+// The backward's packed form of row_terms + power2: pixel centres
+// (fx, fy) and (fx + 1, fy) given as nfx = (-fx, -(fx + 1)) and
+// nfy = (-fy, -fy), so that the differences are packed additions:
+// dy = v - fy (both lanes), dx = (u - fx, u - fx - 1), and the exponent
+// p = dx (a dx + b dy) + c dy^2 at both pixels. Each lane performs the
+// forward's scalar operation with the same rounding, so the backward
+// re-derives exactly the exponents, and hence the alphas, the forward
+// composited.
+__device__ __forceinline__ void power_pair(const SplatP &s, float2 nfx, float2 nfy, float2 &dy,
+                                           float2 &dx, float2 &p) {
+    dy = __fadd2_rn(s.v, nfy);
+    const float2 bdy = __fmul2_rn(s.b, dy);
+    const float2 cdy2 = __fmul2_rn(__fmul2_rn(s.c, dy), dy);
+    dx = __fadd2_rn(s.u, nfx);
+    p = __ffma2_rn(dx, __ffma2_rn(s.a, dx, bdy), cdy2);
+}
+
+// The packed form of blend2 (the same operations per lane).
+template <int PREC>
+__device__ __forceinline__ void blend_pair(const SplatP &s, float2 p, float2 &G, float2 &al,
+                                           bool &cl0, bool &cl1) {
+    if constexpr (blend_of(PREC) == LGS_FP32) {
+        G = make_float2(ex2(p.x), ex2(p.y));
+        const float2 q = __fmul2_rn(s.o, G);
+        al = make_float2(fminf(kAlphaMax, q.x), fminf(kAlphaMax, q.y));
+        cl0 = q.x >= kAlphaMax;
+        cl1 = q.y >= kAlphaMax;
+    } else if constexpr (blend_of(PREC) == LGS_MIXED_FP16) {
+        const __half2 g = h2exp2(__floats2half2_rn(p.x, p.y));
+        const __half2 q = __hmul2(*reinterpret_cast<const __half2 *>(&s.oh), g);
+        const __half2 cap = __float2half2_rn(kAlphaMax);
+        const __half2 ge = __hge2(q, cap);
+        G = __half22float2(g);
+        al = __half22float2(__hmin2(q, cap));
+        cl0 = __low2float(ge) != 0.0f;
+        cl1 = __high2float(ge) != 0.0f;
+    } else {
+        const __nv_bfloat162 g = h2exp2(__floats2bfloat162_rn(p.x, p.y));
+        const __nv_bfloat162 q = __hmul2(*reinterpret_cast<const __nv_bfloat162 *>(&s.oh), g);
+        const __nv_bfloat162 cap = __float2bfloat162_rn(kAlphaMax);
+        const __nv_bfloat162 ge = __hge2(q, cap);
+        G = __bfloat1622float2(g);
+        al = __bfloat1622float2(__hmin2(q, cap));
+        cl0 = __low2float(ge) != 0.0f;
+        cl1 = __high2float(ge) != 0.0f;
+    }
+}
+
+template <class S>
+struct RasterSmemT {
+    S sp[kBatch];
     uint8_t fl[kBatch];
     int maxlast;
 };
+using RasterSmem = RasterSmemT<SplatS>;   // forward
+using RasterSmemP = RasterSmemT<SplatP>;  // backward
 
 // One tile of the forward pass, by the whole CTA (kFwdThreads): warp w
 // owns quadrant w (x0 + 8 (w & 1), y0 + 8 (w >> 1)), lane l the pixels
@@ -309,9 +406,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_raster_fwd(const float *__restr
 // stores its 12 values as column `lane` of a 12 x 32 block (rows padded to
 // kRedStride floats, so that the 128-bit row reads below take no bank
 // conflict), then lane 2i + h (i < 12) adds the 16 entries of row i in
-// columns [16 h, 16 h + 16) in a fixed tree and one shuffle joins the two
+// columns [16 h, 16 h + 16) in a fixed tree (packed two-lane additions down
+// to two partial sums, then one addition) and one shuffle joins the two
 // halves: lanes 2i and 2i + 1 both return the warp sum of value i, lanes
-// 24..31 return 0. 12 stores, 4 loads, 17 additions and one shuffle in
+// 24..31 return 0. 12 stores, 4 loads, 9 additions and one shuffle in
 // place of a butterfly's 13 shuffles and their selects; the order of the
 // additions is fixed, so the result does not depend on timing.
 constexpr int kRedValues = 12;
@@ -325,8 +423,12 @@ __device__ __forceinline__ float warp_sum12(const float v[kRedValues], float *bu
         const float4 *src =
             reinterpret_cast<const float4 *>(buf + (lane >> 1) * kRedStride + 16 * (lane & 1));
         const float4 p = src[0], q = src[1], t = src[2], u = src[3];
-        r = (((p.x + p.y) + (p.z + p.w)) + ((q.x + q.y) + (q.z + q.w))) +
-            (((t.x + t.y) + (t.z + t.w)) + ((u.x + u.y) + (u.z + u.w)));
+        const float2 a = __fadd2_rn(__fadd2_rn(make_float2(p.x, p.y), make_float2(p.z, p.w)),
+                                    __fadd2_rn(make_float2(q.x, q.y), make_float2(q.z, q.w)));
+        const float2 b = __fadd2_rn(__fadd2_rn(make_float2(t.x, t.y), make_float2(t.z, t.w)),
+                                    __fadd2_rn(make_float2(u.x, u.y), make_float2(u.z, u.w)));
+        const float2 c = __fadd2_rn(a, b);
+        r = c.x + c.y;
     }
     r += __shfl_xor_sync(0xffffffffu, r, 1);
     __syncwarp();  // the block is reused by the warp's next splat
@@ -458,7 +560,7 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                                          int tile, const float *__restrict__ finalT,
                                          const int32_t *__restrict__ last,
                                          const float *__restrict__ dLdI, float *__restrict__ gacc,
-                                         unsigned long long *__restrict__ det, RasterSmem &sm,
+                                         unsigned long long *__restrict__ det, RasterSmemP &sm,
                                          float *red_buf) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % K.gx, ty = tile / K.gx;
@@ -487,6 +589,12 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
         bgT[h] = T[h] * (K.bg[0] * g0[h] + K.bg[1] * g1[h] + K.bg[2] * g2[h]);
         accg[h] = 0.0f;
     }
+    // the same per-pixel state as pixel pairs for the packed arithmetic
+    float2 T2 = make_float2(T[0], T[1]), acc = make_float2(accg[0], accg[1]);
+    const float2 gI0 = make_float2(g0[0], g0[1]), gI1 = make_float2(g1[0], g1[1]),
+                 gI2 = make_float2(g2[0], g2[1]), nbgT = make_float2(-bgT[0], -bgT[1]);
+    const float2 nfx = make_float2(-fx, -__fadd_rn(fx, 1.0f)), nfy = dup(-fy);
+    const float2 one = dup(1.0f), neg1 = dup(-1.0f);
     const int32_t wmax = __reduce_max_sync(0xffffffffu, max(lst[0], lst[1]));
     if (threadIdx.x == 0) sm.maxlast = 0;
     __syncthreads();
@@ -513,53 +621,58 @@ __device__ __forceinline__ void bwd_tile(const float *__restrict__ rec,
                 const int k = 32 * q + __ffs(m) - 1;
                 m &= m - 1;
                 const int pos = end - 1 - k;
-                const SplatS s = sm.sp[k];
-                float dy, bdy, cdy2, dx[2], p[2], G[2], al[2];
-                bool cl[2];
-                row_terms(s, fy, dy, bdy, cdy2);
-                power2(s, fx, bdy, cdy2, dx[0], dx[1], p[0], p[1]);
-                blend2<PREC>(s, p[0], p[1], G[0], G[1], al[0], al[1], cl[0], cl[1]);
+                const SplatP &s = sm.sp[k];
+                float2 dy, dx, p, G, al;
+                bool cl0, cl1;
+                power_pair(s, nfx, nfy, dy, dx, p);
+                blend_pair<PREC>(s, p, G, al, cl0, cl1);
+                // pixel h takes part when the splat is before its last
+                // composited one and alpha >= 1/255 (m0, m1); its opacity
+                // and exponent terms also need the clamp off. A pixel that
+                // does not take part keeps T and acc exactly (factor 1,
+                // weight 0) and adds zeros to every sum.
+                const bool m0 = pos < lst[0] && al.x >= kAlphaMin;
+                const bool m1 = pos < lst[1] && al.y >= kAlphaMin;
+                if (!__any_sync(0xffffffffu, m0 || m1)) continue;  // no pixel of the warp takes part
+                const float2 oma = __ffma2_rn(al, neg1, one);  // 1 - alpha
+                const float2 rom = make_float2(m0 ? __fdividef(1.0f, oma.x) : 1.0f,
+                                               m1 ? __fdividef(1.0f, oma.y) : 1.0f);
+                const float2 Tk = __fmul2_rn(T2, rom);  // T before the splat
+                // dd = colour . dL/dI - acc (acc: the colour behind the splat)
+                float2 dd = __fmul2_rn(s.r, gI0);
+                dd = __ffma2_rn(s.g, gI1, dd);
+                dd = __ffma2_rn(s.bl, gI2, dd);
+                dd = __ffma2_rn(acc, neg1, dd);
+                const float2 dLda = __ffma2_rn(Tk, dd, __fmul2_rn(nbgT, rom));
+                const float2 alm = make_float2(m0 ? al.x : 0.0f, m1 ? al.y : 0.0f);
+                const float2 dLdam = make_float2(m0 && !cl0 ? dLda.x : 0.0f,
+                                                 m1 && !cl1 ? dLda.y : 0.0f);
+                const float2 wT = __fmul2_rn(alm, Tk);
+                const float2 pr = __fmul2_rn(wT, gI0), pg = __fmul2_rn(wT, gI1),
+                             pb = __fmul2_rn(wT, gI2);
+                const float2 dLdo = __fmul2_rn(G, dLdam), qq = __fmul2_rn(al, dLdam);
+                const float2 s2 = __fmul2_rn(dLdo, dLdo), qx = __fmul2_rn(dx, qq);
+                const float2 qxx = __fmul2_rn(dx, qx);
                 // lane sums over its pixels: colour, opacity, opacity moment,
                 // and Q0 = sum qq, Q1 = sum dx qq, Q2 = sum dx^2 qq, qq = dL/dpower
-                float gr = 0.f, gg = 0.f, gb = 0.f, dO = 0.f, S = 0.f, Q0 = 0.f, Q1 = 0.f, Q2 = 0.f;
-                float n = 0.f;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (pos < lst[h] && al[h] >= kAlphaMin) {
-                        const float rom = __fdividef(1.0f, 1.0f - al[h]);
-                        const float Tk = T[h] * rom;
-                        const float dd = s.r * g0[h] + s.g * g1[h] + s.bl * g2[h] - accg[h];
-                        const float dLda = Tk * dd - bgT[h] * rom;
-                        const float wT = al[h] * Tk;
-                        gr = fmaf(wT, g0[h], gr);
-                        gg = fmaf(wT, g1[h], gg);
-                        gb = fmaf(wT, g2[h], gb);
-                        if (!cl[h]) {
-                            const float dLdo = G[h] * dLda, qq = al[h] * dLda;
-                            dO += dLdo;
-                            S = fmaf(dLdo, dLdo, S);
-                            const float qx = dx[h] * qq;
-                            Q0 += qq;
-                            Q1 += qx;
-                            Q2 = fmaf(dx[h], qx, Q2);
-                        }
-                        n += 1.0f;
-                        accg[h] = fmaf(al[h], dd, accg[h]);
-                        T[h] = Tk;
-                    }
-                }
-                if (!__any_sync(0xffffffffu, n != 0.0f)) continue;
+                const float gr = pr.x + pr.y, gg = pg.x + pg.y, gb = pb.x + pb.y;
+                const float dO = dLdo.x + dLdo.y, S = s2.x + s2.y;
+                const float Q0 = qq.x + qq.y, Q1 = qx.x + qx.y, Q2 = qxx.x + qxx.y;
+                const float n = (float)((m0 ? 1 : 0) + (m1 ? 1 : 0));
+                acc = __ffma2_rn(alm, dd, acc);
+                T2 = Tk;
                 // with a, b, c in base 2: -(A sx + B sy) = ln2 (2 a sx + b sy),
                 // likewise for v; sx = Q1, sy = dy Q0, sxx = Q2, sxy = dy Q1,
                 // syy = dy^2 Q0. Then dL/do, dL/dcolour, S, M (= dL/do) and
                 // the fragment count (exact in FP32).
-                const float dyQ0 = dy * Q0;
+                const float dys = dy.x, dyQ0 = dys * Q0;
+                const float sa = s.a.x, sb = s.b.x, sc = s.c.x;
                 float v[kRedValues];
-                v[0] = kLn2 * (2.0f * s.a * Q1 + s.b * dyQ0);
-                v[1] = kLn2 * (s.b * Q1 + 2.0f * s.c * dyQ0);
+                v[0] = kLn2 * (2.0f * sa * Q1 + sb * dyQ0);
+                v[1] = kLn2 * (sb * Q1 + 2.0f * sc * dyQ0);
                 v[2] = -0.5f * Q2;
-                v[3] = -dy * Q1;
-                v[4] = -0.5f * dy * dyQ0;
+                v[3] = -dys * Q1;
+                v[4] = -0.5f * dys * dyQ0;
                 v[5] = dO;
                 v[6] = gr;
                 v[7] = gg;
@@ -620,7 +733,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(
     const uint32_t *__restrict__ ranges, RCam K, const float *__restrict__ finalT,
     const int32_t *__restrict__ last, const float *__restrict__ dLdI, float *__restrict__ gacc,
     unsigned long long *__restrict__ det) {
-    __shared__ RasterSmem sm;
+    __shared__ RasterSmemP sm;
     __shared__ __align__(16) float red[(kBwdThreads / 32) * kRedValues * kRedStride];
     bwd_tile<PREC>(rec, vals, ranges, K, blockIdx.x, finalT, last, dLdI, gacc, det, sm, red);
 }
@@ -672,7 +785,7 @@ template <int PREC>
 __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd_batch(const lgs_view *__restrict__ views,
                                                              int n_views, uint32_t total_tiles,
                                                              uint32_t *counter) {
-    __shared__ RasterSmem sm;
+    __shared__ RasterSmemP sm;
     __shared__ __align__(16) float red[(kBwdThreads / 32) * kRedValues * kRedStride];
     __shared__ uint32_t s_tile;
     for (;;) {
