@@ -334,10 +334,18 @@ class MultiView:
     into one gradient buffer (the parameters' gradient summed over views).
     `capture()` records the whole sequence as one CUDA graph; `run_sequential`
     is the same work with one plain launch sequence per view.
+
+    The views' front ends are independent of one another, so run_batched
+    spreads them over `streams` side streams (view k on slot k % streams,
+    each slot with its own cull and binning workspaces), forked from and
+    joined back into the calling stream; the small views' latency-bound
+    launches then overlap. Each look-back kernel waits only on CTAs of its
+    own launch, so launches running side by side never wait on each other.
     """
 
     def __init__(self, planes: torch.Tensor, n: int, sh_degree: int, cams: list, targets: list,
-                 pair_capacity: int, tile=(16, 16), cluster: int = 128, device="cuda"):
+                 pair_capacity: int, tile=(16, 16), cluster: int = 128, device="cuda",
+                 streams: int = 4):
         self.planes, self.n, self.deg = planes, int(n), int(sh_degree)
         self.cams = cams
         self.tile, self.cluster = tuple(tile), int(cluster)
@@ -347,11 +355,15 @@ class MultiView:
         self.g = B.gaussians_struct(planes, n, sh_degree)
         self.cs = [B.camera_struct(c) for c in cams]
         nt = [-(-c["width"] // tw) * -(-c["height"] // th) for c in cams]
-        self.ws_ccc = torch.empty(B.lgs_ccc_workspace_size(n, cluster), dtype=torch.uint8,
-                                  device=dev)
-        self.ws_bin = torch.empty(B.lgs_bin_sort_workspace_size(n, self.cap, max(nt)),
-                                  dtype=torch.uint8, device=dev)
-        self.cluster_visible = torch.empty(-(-n // cluster), dtype=torch.int32, device=dev)
+        self.n_slots = max(1, min(int(streams), len(cams)))
+        self.slots = [{"ws_ccc": torch.empty(B.lgs_ccc_workspace_size(n, cluster),
+                                             dtype=torch.uint8, device=dev),
+                       "ws_bin": torch.empty(B.lgs_bin_sort_workspace_size(n, self.cap, max(nt)),
+                                             dtype=torch.uint8, device=dev),
+                       "cluster_visible": torch.empty(-(-n // cluster), dtype=torch.int32,
+                                                      device=dev),
+                       "stream": torch.cuda.Stream(device=dev)}
+                      for _ in range(self.n_slots)]
         self.gacc = torch.zeros((len(cams), n, B.GRAD_FLOATS), dtype=torch.float32, device=dev)
         self.grad = torch.zeros_like(planes)
         self.counter = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -378,18 +390,32 @@ class MultiView:
         self.table, self.total_tiles = B.view_table(self.views, self.tile, device=dev)
         self.graph = None
 
-    def _front(self, k: int):
-        v, cs = self.views[k], self.cs[k]
+    def _front(self, k: int, slot: int = 0):
+        v, cs, sl = self.views[k], self.cs[k], self.slots[slot]
         tw, th = self.tile
-        B.lgs_cluster_cull_compact(self.g, cs, self.cluster, None, self.cluster_visible,
-                                   v["rowmap"], v["d_V"], self.ws_ccc)
+        B.lgs_cluster_cull_compact(self.g, cs, self.cluster, None, sl["cluster_visible"],
+                                   v["rowmap"], v["d_V"], sl["ws_ccc"])
         B.lgs_preprocess(self.g, v["rowmap"], v["d_V"], cs, tw, th, v["splats"])
         B.lgs_bin_sort(v["splats"], v["d_V"], self.n, cs, tw, th, v["vals"], v["d_P"],
-                       v["ranges"], self.ws_bin)
+                       v["ranges"], sl["ws_bin"])
+
+    def _fronts_concurrent(self):
+        main = torch.cuda.current_stream(self.dev)
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for sl in self.slots:
+            sl["stream"].wait_event(fork)
+        for k in range(len(self.views)):
+            slot = k % self.n_slots
+            with torch.cuda.stream(self.slots[slot]["stream"]):
+                self._front(k, slot)
+        for sl in self.slots:
+            done = torch.cuda.Event()
+            done.record(sl["stream"])
+            main.wait_event(done)
 
     def run_batched(self, precision=B.LGS_FP32):
-        for k in range(len(self.views)):
-            self._front(k)
+        self._fronts_concurrent()
         B.lgs_raster_fwd_batch(self.table, len(self.views), self.total_tiles, self.counter,
                                precision=precision)
         for v in self.views:

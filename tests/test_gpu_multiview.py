@@ -6,7 +6,8 @@ code is the same, only the scheduling differs); the parameter gradient,
 summed over views by the accumulating preprocess backward, equals the
 sequential single-view path up to the order of float atomics, and the
 oracle's sum over views within the gradient tolerance. A CUDA-graph replay
-of the batched sequence gives the same results as running it eagerly.
+of the batched sequence gives the same results as running it eagerly, with
+the views' front ends on one stream or spread over several.
 """
 import numpy as np
 import pytest
@@ -27,14 +28,15 @@ def _gpu():
     U.need_gpu()
 
 
-def _setup(n=20000, seed=5, res=RES):
+def _setup(n=20000, seed=5, res=RES, streams=4):
     d = scenegen.uniform_box_scene(n, 3, seed, 64, 64, with_target=False)
     sc = d["scene"]
     cams = scenegen.orbit_cameras(3, res, radius=4.0, elevation=0.2, center=scenegen.BOX_CENTER)
     rng = np.random.default_rng(seed)
     tgts = [U.t(rng.uniform(0, 1, (3, h, w)).astype(np.float32)) for w, h in res]
     planes, n = U.planes_tensor(sc)
-    return sc, cams, tgts, PL.MultiView(planes, n, 3, cams, tgts, pair_capacity=2_000_000)
+    return sc, cams, tgts, PL.MultiView(planes, n, 3, cams, tgts, pair_capacity=2_000_000,
+                                        streams=streams)
 
 
 def _snap(mv):
@@ -42,8 +44,12 @@ def _snap(mv):
     return ([v["image"].cpu().numpy() for v in mv.views], mv.grad.cpu().numpy().copy())
 
 
-def test_batched_views_equal_sequential_and_graph_replay():
-    _, _, _, mv = _setup()
+@pytest.mark.parametrize("streams", [1, 3])
+def test_batched_views_equal_sequential_and_graph_replay(streams):
+    """With the front ends on one stream, and spread over 3 side streams
+    (6 views: two per slot, sharing its workspaces in order)."""
+    _, _, _, mv = _setup(streams=streams)
+    assert mv.n_slots == streams
     mv.run_sequential()
     imgs_s, grad_s = _snap(mv)
     mv.run_batched()
