@@ -49,4 +49,21 @@ def test_committed_records_name_their_sources():
             continue
         assert rec["source_files"] and rec.get("command", "").startswith("ncu ")
         assert "--clock-control none" in rec["command"]
-        assert ("bytes_per_unit" in rec) != ("bytes_per_launch" in rec), key
+        # exactly one of: bytes per unit, bytes per launch, an event count per launch
+        kinds = [k in rec for k in ("bytes_per_unit", "bytes_per_launch", "count_per_launch")]
+        assert sum(kinds) == 1, key
+
+
+def test_recorded_count_checks_the_source_digest(monkeypatch):
+    digest = bench.source_digest(bench.RASTER_SOURCES)
+    recs = {"fresh": {"source": digest, "source_files": list(bench.RASTER_SOURCES),
+                      "count_per_launch": 77},
+            "stale": {"source": "0" * 16, "source_files": list(bench.RASTER_SOURCES),
+                      "count_per_launch": 77},
+            "bytes": {"source": digest, "source_files": list(bench.RASTER_SOURCES),
+                      "bytes_per_launch": 5}}
+    monkeypatch.setattr(bench, "traffic_record", lambda: recs)
+    assert bench.recorded_count("fresh") == 77
+    assert bench.recorded_count("stale") is None
+    assert bench.recorded_count("bytes") is None
+    assert bench.recorded_count("missing") is None
