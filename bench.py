@@ -367,8 +367,10 @@ def run_extra_configs(steps: int, warmup: int) -> dict:
     return out
 
 
+# a8 (the densification metric) is written by the fused a9 + a10 call from
+# the gradient rows it reads, so its time is part of "a9a10_bwd_adam"
 STAGES = ["a1_morton", "a2_cull", "a3_preprocess", "a4_bin_sort", "a5_raster_fwd", "a6_loss",
-          "a7_raster_bwd", "a8_variance", "a9a10_bwd_adam"]
+          "a7_raster_bwd", "a9a10_bwd_adam"]
 
 
 def measure_unit_peaks(dev, n_sms: int, reps: int = 5) -> dict:
@@ -475,13 +477,12 @@ def run_gpu(args) -> dict | None:
             B.lgs_raster_bwd(tr.splats, tr.vals, tr.ranges, cs, TILE[0], TILE[1], tr.finalT,
                              tr.last, tr.dLdI, tr.gacc, precision=precision)
         mark(7)
-        B.lgs_opacity_variance(tr.gacc, tr.rowmap, tr.d_V, tr.n, tr.metric)
-        mark(8)
         tr.step_count += 1
+        # a9 + a10, and the a8 metric from the same gradient rows
         B.lgs_preprocess_bwd_adam(tr.gaussians(), tr.m, tr.v, tr.rowmap, tr.d_V, cs, tr.gacc,
                                   tr.lr, tr.cfg.beta1, tr.cfg.beta2, tr.cfg.eps, tr.step_count,
-                                  splats=tr.splats)
-        mark(9)
+                                  splats=tr.splats, metric=tr.metric)
+        mark(8)
 
     for w in range(args.warmup):
         step(reorder=(w == 0 and morton))  # the timed steps run on Morton-sorted state
@@ -503,7 +504,8 @@ def run_gpu(args) -> dict | None:
     clocks = ClockSampler(bus)
     clocks.start()
     time.sleep(0.3)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+           for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -566,7 +568,8 @@ def run_gpu(args) -> dict | None:
             tr._round_sh16()
         for _ in range(2):
             step(precision=prec, deterministic=dm)
-        mev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
+        mev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+               for _ in range(args.steps)]
         torch.cuda.synchronize()
         m0 = torch.cuda.Event(enable_timing=True)
         m1 = torch.cuda.Event(enable_timing=True)
@@ -585,7 +588,7 @@ def run_gpu(args) -> dict | None:
                                                      for k in range(args.steps)])), 4),
             "a3_preprocess_ms": round(float(np.mean([mev[k][2].elapsed_time(mev[k][3])
                                                      for k in range(args.steps)])), 4),
-            "a9a10_bwd_adam_ms": round(float(np.mean([mev[k][8].elapsed_time(mev[k][9])
+            "a9a10_bwd_adam_ms": round(float(np.mean([mev[k][7].elapsed_time(mev[k][8])
                                                       for k in range(args.steps)])), 4)}
         tr.sh16 = None
     tr.state[tr.cur].copy_(snapshot)
@@ -611,10 +614,11 @@ def run_gpu(args) -> dict | None:
     # The lane rate is SMs (queried) x 128 FP32 lanes x the SM clock: the
     # median sampled during the timed region (else the maximum, 2070 MHz).
     # The forward (a5): about 9 per fragment. The largest HBM-bound call is
-    # the fused preprocess backward + Adam (k_bwd_adam_rec), 1480 B per
+    # the fused preprocess backward + Adam (k_bwd_adam_rec), 1484 B per
     # visible Gaussian at SH3: params, m, v read and written (6 x 59 x 4 B),
-    # the 9 gradients + S, M, C of its grad row (48 B), its map entry (4 B)
-    # and the 3 colours of its splat record (12 B).
+    # the 9 gradients + S, M, C of its grad row (48 B), its map entry (4 B),
+    # the 3 colours of its splat record (12 B) and the a8 metric it writes
+    # (4 B).
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
@@ -659,13 +663,14 @@ def run_gpu(args) -> dict | None:
                 "algorithmic_ops": int(F * ops_bwd), "fragments": F,
                 "ops_per_fragment": ops_bwd}
     npl = B.num_planes(SH_DEG)
-    per_unit = {"a9a10_bwd_adam": 6 * npl * 4 + 48 + 4 + 12,
+    per_unit = {"a9a10_bwd_adam": 6 * npl * 4 + 48 + 4 + 12 + 4,
                 "a3_preprocess": npl * 4 + 4 + 48 + 4 + 4}  # params + map in; record, depth, radius out
     dom = "a9a10_bwd_adam"
     achieved = V * per_unit[dom] / (stage_ms[dom] * 1e-3) / 1e9
     traffic = recorded_traffic(dom, V)
     pre_gbs = V * per_unit["a3_preprocess"] / (stage_ms["a3_preprocess"] * 1e-3) / 1e9
-    other = {"a9a10_bwd_adam": {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_rec<3>)",
+    other = {"a9a10_bwd_adam": {"kernel": "lgs_preprocess_bwd_adam (k_bwd_adam_rec<3>, "
+                                          "with the a8 metric)",
                                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                                 "unit": "GB/s",
                                 "peak_source": "measured" if hbm else "fallback",

@@ -487,12 +487,16 @@ lgs_status lgs_adam_step(float *params, const float *grads, float *m, float *v, 
  * colour coefficient the step updates is also written, rounded to nearest
  * even, to the 16-bit plane at g->sh16 (an output here); sp is then
  * required. A forward on the same g (lgs_preprocess) reads the 16-bit
- * planes. */
+ * planes.
+ * metric (device, may be NULL): when given, the call also writes the a8
+ * densification metric C Var = S - M^2 / C (0 if C = 0) of every row
+ * map[j], j < V, from grad_acc's S, M and C, bit for bit what
+ * lgs_opacity_variance writes, so that a step needs no separate a8 launch. */
 lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
                                    const lgs_camera *cam, const lgs_splats *sp, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
-                                   int32_t step, lgs_stream stream);
+                                   int32_t step, float *metric, lgs_stream stream);
 
 /* dst[k][i] = src[k][i] rounded to nearest even in dtype (LGS_SH_BF16 or
  * LGS_SH_F16), planes k < n_planes, rows i < n; src float32 planes of stride

@@ -129,7 +129,7 @@ def load(build_if_missing: bool = True):
         "lgs_raster_fwd_batch": (i32, [P, i32, u32, i32, P, P]),
         "lgs_raster_bwd_batch": (i32, [P, i32, u32, i32, P, P]),
         "lgs_adam_step": (i32, [P, P, P, P, i64, i32, P, f32, f32, f32, i32, P, P, i64, P]),
-        "lgs_preprocess_bwd_adam": (i32, [P, P, P, P, P, P, P, P, P, f32, f32, f32, i32, P]),
+        "lgs_preprocess_bwd_adam": (i32, [P, P, P, P, P, P, P, P, P, f32, f32, f32, i32, P, P]),
         "lgs_moments_accumulate": (i32, [P, P, P, i64, P, P, P, P]),
         "lgs_round_planes": (i32, [P, i64, P, i64, i32, i64, i32, P]),
         "lgs_moments_metric": (i32, [P, P, P, i64, P, P]),
@@ -461,16 +461,18 @@ def lgs_adam_step(params, grads, m, v, n_planes, lr, beta1, beta2, eps, step, ma
 
 
 def lgs_preprocess_bwd_adam(g: LgsGaussians, m, v, map_, d_num_visible, cam: LgsCamera, grad_acc,
-                            lr, beta1, beta2, eps, step, stream=None, splats=None):
+                            lr, beta1, beta2, eps, step, stream=None, splats=None, metric=None):
     """splats: the LgsSplats of the forward (optional; the colour clamp then
-    comes from their stored colours and the SH planes are read once)."""
+    comes from their stored colours and the SH planes are read once).
+    metric: a float32 tensor of n rows (optional) that receives the a8
+    densification metric as lgs_opacity_variance would write it."""
     L = load()
     arr = _lr_array(lr)
     _check(L.lgs_preprocess_bwd_adam(ctypes.byref(g), _ptr(m), _ptr(v), _ptr(map_),
                                      _ptr(d_num_visible), ctypes.byref(cam),
                                      ctypes.byref(splats) if splats is not None else None,
                                      _ptr(grad_acc), arr, beta1, beta2, eps, step,
-                                     _stream(stream)),
+                                     _ptr(metric), _stream(stream)),
            "lgs_preprocess_bwd_adam")
 
 

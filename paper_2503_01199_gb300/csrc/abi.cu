@@ -31,7 +31,7 @@ lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
                                const int32_t *d_V, const lgs_camera *cam, const float *rec,
                                float *gacc, const float *lr, float b1, float b2, float eps,
-                               int step, cudaStream_t s);
+                               int step, float *metric, cudaStream_t s);
 lgs_status round_planes(const float *src, int64_t src_stride, void *dst, int64_t dst_stride,
                         int n_planes, int64_t n, int dtype, cudaStream_t s);
 lgs_status adam_step(float *p, const float *grad, float *m, float *v, int64_t stride, int np,
@@ -399,7 +399,7 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
                                    const uint32_t *map, const int32_t *d_num_visible,
                                    const lgs_camera *cam, const lgs_splats *sp, float *grad_acc,
                                    const float *lr, float beta1, float beta2, float eps,
-                                   int32_t step, lgs_stream stream) {
+                                   int32_t step, float *metric, lgs_stream stream) {
     // 16-bit colour planes are accepted here as an extra output (the rounded
     // copy of the updated FP32 coefficients), with the splat records only
     if (bad_gaussians(g) || bad_camera(cam) || !m || !v || !grad_acc || !lr || step < 1 ||
@@ -408,7 +408,7 @@ lgs_status lgs_preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v,
         return LGS_ERR_INVALID_ARG;
     if (g->n == 0) return LGS_OK;
     return preprocess_bwd_adam(g, m, v, map, d_num_visible, cam, sp ? sp->rec : nullptr, grad_acc,
-                               lr, beta1, beta2, eps, step, as_stream(stream));
+                               lr, beta1, beta2, eps, step, metric, as_stream(stream));
 }
 
 lgs_status lgs_round_planes(const float *src, int64_t src_stride, void *dst, int64_t dst_stride,

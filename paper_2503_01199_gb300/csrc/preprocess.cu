@@ -650,6 +650,16 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// The densification metric of Sec. 3.3 (a8) from a gradient row: slots 9,
+// 10, 11 hold S, M and the fragment count C; C Var = S - M^2 / C (0 when
+// C = 0), the expression lgs_opacity_variance evaluates, so both give the
+// same bits. Lets the fused step write the metric from the row it reads.
+__device__ __forceinline__ float row_metric(const float *g16) {
+    const float S = g16[9], M = g16[10];
+    const uint32_t C = reinterpret_cast<const uint32_t *>(g16)[11];
+    return C ? S - M * M / (float)C : 0.f;
+}
+
 // A CTA runs part A for its chunk, then part B; CTAs in different phases
 // overlap part A's arithmetic with part B's memory traffic. Part B keeps
 // kStages coefficients' loads in flight through shared memory (cp.async),
@@ -662,7 +672,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
     int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
-    const float *__restrict__ gacc, AdamArgs a) {
+    const float *__restrict__ gacc, AdamArgs a, float *__restrict__ metric) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
     __shared__ float s_g[3][256], s_d[3][256];
     __shared__ int64_t s_row[256];
@@ -673,6 +683,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
         const int64_t j = c0 + tid;
         if (j < V) {
             const int64_t row = map ? map[j] : j;
+            if (metric) metric[row] = row_metric(gacc + 16 * j);
             GeomSink sink{P, Mo, Vo, stride, row, &a};
             float dir[3], grgb[3];
             backward<DEG>(K, P, stride, row, gacc + 16 * j, sink, dir, grgb);
@@ -751,7 +762,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_rec(
     float *__restrict__ P, float *__restrict__ Mo, float *__restrict__ Vo, int64_t stride,
     int64_t n, const uint32_t *__restrict__ map, const int32_t *d_V, Cam K,
     const float *__restrict__ gacc, const float *__restrict__ rec, AdamArgs a,
-    uint16_t *__restrict__ sh16, int sh_dtype) {
+    uint16_t *__restrict__ sh16, int sh_dtype, float *__restrict__ metric) {
     constexpr int KK = (DEG + 1) * (DEG + 1);
     __shared__ float s_g[3][256], s_d[3][256], s_c[4][256];  // s_c: centre gradient, 1 / dist
     __shared__ int64_t s_row[256];
@@ -763,6 +774,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_rec(
         const int64_t j = c0 + tid;
         if (j < V) {
             const int64_t row = map ? map[j] : j;
+            if (metric) metric[row] = row_metric(gacc + 16 * j);
             GeomSink sink{P, Mo, Vo, stride, row, &a};
             Fwd f;
             float gm[3] = {0.f, 0.f, 0.f}, grgb[3] = {0.f, 0.f, 0.f}, dir[3] = {0.f, 0.f, 0.f};
@@ -960,7 +972,7 @@ lgs_status preprocess_bwd(const lgs_gaussians *g, const uint32_t *map, const int
 lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const uint32_t *map,
                                const int32_t *d_V, const lgs_camera *cam, const float *rec,
                                float *gacc, const float *lr, float b1, float b2, float eps,
-                               int step, cudaStream_t s) {
+                               int step, float *metric, cudaStream_t s) {
     const Cam K = make_cam(cam, 16, 16);
     const AdamArgs a = make_adam(lr, LGS_NUM_PLANES(g->sh_degree), b1, b2, eps, step);
     const unsigned gf = grid_for(g->n, 256, 8);
@@ -970,18 +982,18 @@ lgs_status preprocess_bwd_adam(const lgs_gaussians *g, float *m, float *v, const
                              ? static_cast<uint16_t *>(const_cast<void *>(g->sh16)) : nullptr;
         const int st = g->sh_dtype;
         switch (g->sh_degree) {
-        case 0: k_bwd_adam_rec<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
-        case 1: k_bwd_adam_rec<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
-        case 2: k_bwd_adam_rec<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
-        default: k_bwd_adam_rec<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st); break;
+        case 0: k_bwd_adam_rec<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st, metric); break;
+        case 1: k_bwd_adam_rec<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st, metric); break;
+        case 2: k_bwd_adam_rec<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st, metric); break;
+        default: k_bwd_adam_rec<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, rec, a, sh16, st, metric); break;
         }
         return check_launch();
     }
     switch (g->sh_degree) {
-    case 0: k_bwd_adam_fused<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
-    case 1: k_bwd_adam_fused<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
-    case 2: k_bwd_adam_fused<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
-    default: k_bwd_adam_fused<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a); break;
+    case 0: k_bwd_adam_fused<0><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a, metric); break;
+    case 1: k_bwd_adam_fused<1><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a, metric); break;
+    case 2: k_bwd_adam_fused<2><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a, metric); break;
+    default: k_bwd_adam_fused<3><<<gf, 256, 0, s>>>(g->data, m, v, g->stride, g->n, map, d_V, K, gacc, a, metric); break;
     }
     return check_launch();
 }

@@ -210,14 +210,17 @@ class Trainer:
                          self.last, precision=self.cfg.precision)
         return cs
 
-    def backward(self, cs: B.LgsCamera, target: torch.Tensor, accumulate=False):
-        """a6..a8: loss gradient, backward rasterisation, variance metric."""
+    def backward(self, cs: B.LgsCamera, target: torch.Tensor, accumulate=False, metric=True):
+        """a6..a8: loss gradient, backward rasterisation, variance metric
+        (metric=False leaves a8 to the fused optimizer, which writes the
+        same values from the gradient rows it reads)."""
         tw, th = self.cfg.tile
         B.lgs_loss_l1(self.image, target, self.dLdI, self.loss)
         B.lgs_raster_bwd(self.splats, self.vals, self.ranges, cs, tw, th, self.finalT, self.last,
                          self.dLdI, self.gacc, accumulate=accumulate,
                          precision=self.cfg.precision)
-        B.lgs_opacity_variance(self.gacc, self._map(), self._dV(), self.n, self.metric)
+        if metric:
+            B.lgs_opacity_variance(self.gacc, self._map(), self._dV(), self.n, self.metric)
         if self.track_moments:
             B.lgs_moments_accumulate(self.gacc, self._map(), self._dV(), self.n, self.S_acc,
                                      self.M_acc, self.C_acc)
@@ -247,15 +250,16 @@ class Trainer:
         """Halves every activated opacity (Sec. 3.3)."""
         B.lgs_opacity_decay(self._g32())
 
-    def optimize(self, cs: B.LgsCamera, fused=True):
-        """a9 + a10: preprocess backward and Adam on the visible rows."""
+    def optimize(self, cs: B.LgsCamera, fused=True, metric=False):
+        """a9 + a10: preprocess backward and Adam on the visible rows
+        (fused, metric=True: also the a8 metric, in the same launch)."""
         self.step_count += 1
         c = self.cfg
         g = self.gaussians()
         if fused:
             B.lgs_preprocess_bwd_adam(g, self.m, self.v, self._map(), self._dV(), cs, self.gacc,
                                       self.lr, c.beta1, c.beta2, c.eps, self.step_count,
-                                      splats=self.splats)
+                                      splats=self.splats, metric=self.metric if metric else None)
         else:
             if self.sh16 is not None:
                 raise ValueError("a 16-bit colour copy is kept up to date by the fused optimizer only")
@@ -316,8 +320,8 @@ class Trainer:
             self.morton_reorder()
         cs = cam if isinstance(cam, B.LgsCamera) else B.camera_struct(cam)
         self.render(None, cs)
-        self.backward(cs, target)
-        self.optimize(cs, fused=fused)
+        self.backward(cs, target, metric=not fused)
+        self.optimize(cs, fused=fused, metric=fused)
         every = self.cfg.overflow_check_every
         if every and self.step_count % every == 0 and not torch.cuda.is_current_stream_capturing():
             self.check_overflow()

@@ -121,7 +121,7 @@ def test_capacity_and_grid_rules_are_checked_on_the_host():
     def fused(g_, sp_, gacc_=gacc, step=1, cam_=cam):
         return L.lgs_preprocess_bwd_adam(ctypes.byref(g_), m, v, rowmap, nvis, ctypes.byref(cam_),
                                          None if sp_ is None else ctypes.byref(sp_), gacc_, lr,
-                                         0.9, 0.999, 1e-15, step, None)
+                                         0.9, 0.999, 1e-15, step, None, None)
 
     small = B.LgsSplats(sp.rec, sp.depth, sp.radius, n - 1)
     assert fused(g, small) == bad                                    # records fewer than rows

@@ -171,7 +171,8 @@ def test_fused_backward_adam_map_layouts(layout):
     """The fused call reaches rows through the map in both of its passes:
     consecutive, scattered and unaligned runs of visible rows must all give
     the separate path's result, and rows outside the map must stay
-    byte-identical."""
+    byte-identical. The a8 metric it writes on request equals
+    lgs_opacity_variance's bit for bit, on the mapped rows only."""
     d = scenegen.uniform_box_scene(1000, 3, 9, 96, 96, focal=96.0)
     sc, cam = d["scene"], d["camera"]
     rng = np.random.default_rng(10)
@@ -184,7 +185,13 @@ def test_fused_backward_adam_map_layouts(layout):
     V = rows.size
     grads = np.zeros((1000, 16), np.float32)
     grads[:V, :9] = rng.standard_normal((V, 9)).astype(np.float32) * 1e-2
+    # S, M and the fragment count C (slots 9..11; some C = 0) for the a8
+    # metric the fused call may write
+    grads[:V, 9] = rng.uniform(0, 1e-3, V).astype(np.float32)
+    grads[:V, 10] = rng.standard_normal(V).astype(np.float32) * 1e-2
+    grads[:V, 11] = rng.integers(0, 40, V).astype(np.uint32).view(np.float32)
     lr = PL.lr_per_plane(3)
+    metrics = []
     m0 = rng.standard_normal((59, 1000)).astype(np.float32) * 1e-3
     v0 = rng.uniform(0, 1e-4, (59, 1000)).astype(np.float32)
     out = []
@@ -201,8 +208,10 @@ def test_fused_backward_adam_map_layouts(layout):
         mp = U.t(rows.astype(np.uint32).view(np.int32))
         dV = U.t(np.array([V], np.int32))
         gacc = U.t(grads)
+        metric = torch.full((1000,), -7.0, dtype=torch.float32, device="cuda")
         if mode == "fused":
-            B.lgs_preprocess_bwd_adam(g, m, v, mp, dV, cs, gacc, lr, 0.9, 0.999, 1e-15, 3)
+            B.lgs_preprocess_bwd_adam(g, m, v, mp, dV, cs, gacc, lr, 0.9, 0.999, 1e-15, 3,
+                                      metric=metric)
         elif mode == "fused_records":
             rec = torch.empty((1000, B.SPLAT_FLOATS), dtype=torch.float32, device="cuda")
             depth = torch.empty(1000, dtype=torch.float32, device="cuda")
@@ -210,15 +219,24 @@ def test_fused_backward_adam_map_layouts(layout):
             sp = B.splats_struct(rec, depth, radius)
             B.lgs_preprocess(g, mp, dV, cs, 16, 16, sp)
             B.lgs_preprocess_bwd_adam(g, m, v, mp, dV, cs, gacc, lr, 0.9, 0.999, 1e-15, 3,
-                                      splats=sp)
+                                      splats=sp, metric=metric)
         else:
             gp = torch.zeros_like(planes)
             B.lgs_preprocess_bwd(g, mp, dV, cs, gacc, gp)
             B.lgs_adam_step(planes, gp, m, v, planes.shape[0], lr, 0.9, 0.999, 1e-15, 3, mp, dV, n)
+            B.lgs_opacity_variance(gacc, mp, dV, n, metric)
         torch.cuda.synchronize()
+        metrics.append(metric.cpu().numpy())
         out.append((planes.cpu().numpy()[:, :n], m.cpu().numpy()[:, :n], v.cpu().numpy()[:, :n]))
     pa, ma, va = out[0]
     hidden = np.setdiff1d(np.arange(1000), rows)
+    # the metric of the fused call is lgs_opacity_variance's, bit for bit,
+    # on the mapped rows only
+    C = grads[:V, 11].view(np.uint32)
+    assert (C == 0).any() and (metrics[0][rows] != 0).any()
+    assert (metrics[0][hidden] == -7.0).all()
+    for mb in metrics[1:]:
+        np.testing.assert_array_equal(mb, metrics[0])
     for pb, mb, vb in out[1:]:
         np.testing.assert_array_equal(pb[:, hidden], pa[:, hidden])
         np.testing.assert_array_equal(mb[:, hidden], ma[:, hidden])
