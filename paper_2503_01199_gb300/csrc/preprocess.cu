@@ -683,19 +683,22 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_fused(
         const int64_t j = c0 + tid;
         if (j < V) {
             const int64_t row = map ? map[j] : j;
-            if (metric) metric[row] = row_metric(gacc + 16 * j);
-            GeomSink sink{P, Mo, Vo, stride, row, &a};
-            float dir[3], grgb[3];
-            backward<DEG>(K, P, stride, row, gacc + 16 * j, sink, dir, grgb);
+            s_row[tid] = -1;  // a row the debug build rejects is not updated
+            if (LGS_DCHECK(row < n, kSitePreMap)) {
+                if (metric) metric[row] = row_metric(gacc + 16 * j);
+                GeomSink sink{P, Mo, Vo, stride, row, &a};
+                float dir[3], grgb[3];
+                backward<DEG>(K, P, stride, row, gacc + 16 * j, sink, dir, grgb);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                s_g[c][tid] = grgb[c];
-                s_d[c][tid] = dir[c];
+                for (int c = 0; c < 3; ++c) {
+                    s_g[c][tid] = grgb[c];
+                    s_d[c][tid] = dir[c];
+                }
+                s_row[tid] = row;
             }
-            s_row[tid] = row;
         }
         __syncthreads();
-        if (j < V) {
+        if (j < V && s_row[tid] >= 0) {
             const int64_t row = s_row[tid];
             const float gr[3] = {s_g[0][tid], s_g[1][tid], s_g[2][tid]};
             const float dx = s_d[0][tid], dy = s_d[1][tid], dz = s_d[2][tid];
@@ -774,40 +777,43 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_rec(
         const int64_t j = c0 + tid;
         if (j < V) {
             const int64_t row = map ? map[j] : j;
-            if (metric) metric[row] = row_metric(gacc + 16 * j);
-            GeomSink sink{P, Mo, Vo, stride, row, &a};
-            Fwd f;
-            float gm[3] = {0.f, 0.f, 0.f}, grgb[3] = {0.f, 0.f, 0.f}, dir[3] = {0.f, 0.f, 0.f};
-            float dinv = 0.f;
-            if (geom_forward(K, P, stride, row, f)) {
-                const float *g16 = gacc + 16 * j;
-                geom_backward(K, f, g16, sink, gm);
-                const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
-                const float gcb = g16[8];
-                const float4 cr = reinterpret_cast<const float4 *>(rec + 12 * j)[1];
-                const float cb = rec[12 * j + 8];
-                grgb[0] = cr.z > 0.f ? gb.z : 0.f;
-                grgb[1] = cr.w > 0.f ? gb.w : 0.f;
-                grgb[2] = cb > 0.f ? gcb : 0.f;
-                dir[0] = f.dir[0];
-                dir[1] = f.dir[1];
-                dir[2] = f.dir[2];
-                dinv = f.dinv;
-            } else {
+            s_row[tid] = -1;  // a row the debug build rejects is not updated
+            if (LGS_DCHECK(row < n, kSitePreMap)) {
+                if (metric) metric[row] = row_metric(gacc + 16 * j);
+                GeomSink sink{P, Mo, Vo, stride, row, &a};
+                Fwd f;
+                float gm[3] = {0.f, 0.f, 0.f}, grgb[3] = {0.f, 0.f, 0.f}, dir[3] = {0.f, 0.f, 0.f};
+                float dinv = 0.f;
+                if (geom_forward(K, P, stride, row, f)) {
+                    const float *g16 = gacc + 16 * j;
+                    geom_backward(K, f, g16, sink, gm);
+                    const float4 gb = reinterpret_cast<const float4 *>(g16)[1];
+                    const float gcb = g16[8];
+                    const float4 cr = reinterpret_cast<const float4 *>(rec + 12 * j)[1];
+                    const float cb = rec[12 * j + 8];
+                    grgb[0] = cr.z > 0.f ? gb.z : 0.f;
+                    grgb[1] = cr.w > 0.f ? gb.w : 0.f;
+                    grgb[2] = cb > 0.f ? gcb : 0.f;
+                    dir[0] = f.dir[0];
+                    dir[1] = f.dir[1];
+                    dir[2] = f.dir[2];
+                    dinv = f.dinv;
+                } else {
 #pragma unroll
-                for (int k = 3; k < 11; ++k) sink(k, 0.0f);
-            }
+                    for (int k = 3; k < 11; ++k) sink(k, 0.0f);
+                }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                s_g[c][tid] = grgb[c];
-                s_d[c][tid] = dir[c];
-                s_c[c][tid] = gm[c];
+                for (int c = 0; c < 3; ++c) {
+                    s_g[c][tid] = grgb[c];
+                    s_d[c][tid] = dir[c];
+                    s_c[c][tid] = gm[c];
+                }
+                s_c[3][tid] = dinv;
+                s_row[tid] = row;
             }
-            s_c[3][tid] = dinv;
-            s_row[tid] = row;
         }
         __syncthreads();
-        if (j < V) {
+        if (j < V && s_row[tid] >= 0) {
             const int64_t row = s_row[tid];
             const float gr[3] = {s_g[0][tid], s_g[1][tid], s_g[2][tid]};
             const float dx = s_d[0][tid], dy = s_d[1][tid], dz = s_d[2][tid];
