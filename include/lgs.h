@@ -293,17 +293,19 @@ lgs_status lgs_set_wait_limit(uint32_t spins);
  * lists against the splat rows (lgs_splats.capacity) in the raster calls,
  * gradient rows against max_splats in the backward, the radix sort's
  * scatter positions against the key count, the Morton gather's source rows
- * and the compaction-map rows of the preprocess, its backward and the
- * plain Adam step against the row count. A failed check skips the access
- * and records its site and source line; the fused backward + Adam call,
- * the binning and the densification are not checked. lgs_debug_build()
+ * and the compaction-map rows of the preprocess, its backward, the fused
+ * backward + Adam and the plain Adam step against the row count, and the
+ * densification's source rows and moment rows. A failed check skips the
+ * access and records its site and source line; the binning writes only
+ * behind its capacity guards and is not checked. lgs_debug_build()
  * returns 1 in that build, 0 in the release build.
  * lgs_get_debug_error() synchronises the device; *code = (site << 32) |
  * line of the first failed check since the last query (0: none), cleared
  * on read; LGS_ERR_BOUNDS if one failed, else LGS_OK (always LGS_OK in the
  * release build, whose kernels carry no checks). Sites: 1 tile-list splat
  * index, 2 gradient row, 3 sort scatter, 4 gather row, 5 preprocess map
- * row, 6 Adam map row. */
+ * row (also of the fused backward + Adam), 6 Adam map row, 7 densification
+ * row. */
 int32_t lgs_debug_build(void);
 lgs_status lgs_get_debug_error(uint64_t *code);
 

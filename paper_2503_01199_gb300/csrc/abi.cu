@@ -251,7 +251,8 @@ lgs_status lgs_get_debug_error(uint64_t *code) {
         return LGS_ERR_CUDA;
     }
     lgs_status (*const readers[])(uint64_t *) = {debug_error_raster, debug_error_sort,
-                                                 debug_error_ccc, debug_error_preprocess};
+                                                 debug_error_ccc, debug_error_preprocess,
+                                                 debug_error_densify};
     for (auto rd : readers) {
         uint64_t c = 0;
         const lgs_status st = rd(&c);

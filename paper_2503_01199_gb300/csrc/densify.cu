@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_densify_apply(
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < kk;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = order[r], j = n + r;
+        if (!LGS_DCHECK(i < n, kSiteDensifyRow)) continue;
         if (selected) selected[r] = (uint32_t)i;
         float ls[3], s[3];
 #pragma unroll
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_accumulate(
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = map ? map[j] : j;
+        if (!LGS_DCHECK(row < max_rows, kSiteDensifyRow)) continue;
         const float4 t = reinterpret_cast<const float4 *>(gacc + 16 * j)[2];
         S[row] += t.y;
         M[row] += t.z;
@@ -187,5 +189,7 @@ lgs_status moments_metric(const float *S, const float *M, const uint32_t *C, int
     k_moments_metric<<<grid_for(n, kThreads), kThreads, 0, s>>>(S, M, C, n, metric);
     return check_launch();
 }
+
+DEBUG_TU(densify)
 
 }  // namespace lgs

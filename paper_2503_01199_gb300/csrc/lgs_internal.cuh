@@ -51,6 +51,7 @@ enum DebugSite : uint32_t {
     kSiteGatherPerm = 4,    // Morton gather source row < rows
     kSitePreMap = 5,        // preprocess compaction-map row < rows
     kSiteAdamMap = 6,       // backward / Adam compaction-map row < rows
+    kSiteDensifyRow = 7,    // densification source row / moments map row < rows
 };
 
 #ifdef LGS_DEBUG
@@ -85,6 +86,7 @@ lgs_status debug_error_raster(uint64_t *code);
 lgs_status debug_error_sort(uint64_t *code);
 lgs_status debug_error_ccc(uint64_t *code);
 lgs_status debug_error_preprocess(uint64_t *code);
+lgs_status debug_error_densify(uint64_t *code);
 
 // ---------------------------------------------------------------------------
 // device helpers
