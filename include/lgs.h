@@ -263,6 +263,17 @@ lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int6
                         uint32_t *tile_ranges, void *workspace, size_t workspace_bytes,
                         lgs_stream stream);
 
+/* The 64-bit sort keys of a finished binning, for callers that want them
+ * beside vals: keys[p] = (t << 32) | bits of depth[vals[p]] (the float's
+ * bits; depths are positive, so the bits order as the depths) for every pair
+ * p of every tile t < n_tiles, in tile_ranges' layout. Within a tile's
+ * range the keys do not decrease. sp: the splats the binning read (depth,
+ * capacity); vals, tile_ranges: its outputs (device); keys: device, one per
+ * pair. A splat index >= sp->capacity gets the key of an infinite depth.
+ * LGS_ERR_INVALID_ARG for a null pointer or n_tiles outside 1..65536. */
+lgs_status lgs_bin_keys(const lgs_splats *sp, const uint32_t *vals, const uint32_t *tile_ranges,
+                        int32_t n_tiles, uint64_t *keys, lgs_stream stream);
+
 /* Synchronises the device, returns LGS_ERR_CAPACITY and the largest pair
  * count seen if some lgs_bin_sort overflowed since the last query (and
  * clears the flag), else LGS_OK with *needed = 0. */

@@ -30,7 +30,7 @@ ENTRY_POINTS = (
     "lgs_version", "lgs_last_cuda_error", "lgs_kernel_launches", "lgs_morton_workspace_size", "lgs_morton_reorder",
     "lgs_ccc_workspace_size", "lgs_cluster_cull_compact", "lgs_cluster_cull_compact_noalloc",
     "lgs_compact_gather", "lgs_preprocess",
-    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_get_overflow", "lgs_get_wait_timeouts", "lgs_set_wait_limit",
+    "lgs_bin_sort_workspace_size", "lgs_bin_sort", "lgs_bin_keys", "lgs_get_overflow", "lgs_get_wait_timeouts", "lgs_set_wait_limit",
     "lgs_debug_build", "lgs_get_debug_error",
     "lgs_raster_fwd",
     "lgs_raster_fwd_batch", "lgs_raster_bwd_batch", "lgs_loss_l1", "lgs_raster_bwd",
@@ -136,6 +136,7 @@ def load(build_if_missing: bool = True):
         "lgs_densify_workspace_size": (sz, [i64]),
         "lgs_densify": (i32, [P, P, P, P, i64, f32, P, P, P, P, sz, P]),
         "lgs_opacity_decay": (i32, [P, P]),
+        "lgs_bin_keys": (i32, [P, P, P, i32, P, P]),
         "lgs_peak_ex2": (i32, [P, i32, i32, P]),
         "lgs_peak_ffma": (i32, [P, i32, i32, i32, P]),
         "lgs_peak_red": (i32, [P, i64, i32, i32, P]),
@@ -532,3 +533,11 @@ def lgs_peak_red(rows, n_rows: int, blocks: int, iters: int, stream=None) -> int
     _check(L.lgs_peak_red(_ptr(rows), int(n_rows), int(blocks), int(iters), _stream(stream)),
            "lgs_peak_red")
     return blocks * (PEAK_THREADS // 32) * 12 * iters
+
+
+def lgs_bin_keys(splats, vals, tile_ranges, keys, stream=None):
+    """keys (int64 tensor, one per pair) = tile << 32 | depth bits of each
+    pair of a finished binning (tile_ranges: [n_tiles, 2])."""
+    L = load()
+    _check(L.lgs_bin_keys(ctypes.byref(splats), _ptr(vals), _ptr(tile_ranges),
+                          int(tile_ranges.shape[0]), _ptr(keys), _stream(stream)), "lgs_bin_keys")

@@ -42,6 +42,8 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
                     int tw, int th, int cull, uint32_t *vals, int64_t cap, int64_t *d_P,
                     uint32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t s);
 lgs_status get_overflow(int64_t *needed);
+lgs_status bin_keys(const float *depth, const uint32_t *vals, const uint32_t *ranges, int ntiles,
+                    int64_t rows, uint64_t *keys, cudaStream_t s);
 lgs_status raster_fwd(const lgs_splats *sp, const uint32_t *vals, const uint32_t *ranges,
                       const lgs_camera *cam, int tw, int th, int precision, float *image,
                       float *finalT, int32_t *last, cudaStream_t s);
@@ -230,6 +232,15 @@ lgs_status lgs_bin_sort(const lgs_splats *sp, const int32_t *d_num_visible, int6
         return LGS_ERR_INVALID_ARG;
     return bin_sort(sp, d_num_visible, max_splats, cam, tile_w, tile_h, tile_cull, vals,
                     pair_capacity, d_num_pairs, tile_ranges, workspace, workspace_bytes,
+                    as_stream(stream));
+}
+
+lgs_status lgs_bin_keys(const lgs_splats *sp, const uint32_t *vals, const uint32_t *tile_ranges,
+                        int32_t n_tiles, uint64_t *keys, lgs_stream stream) {
+    if (!sp || !sp->depth || sp->capacity <= 0 || !vals || !tile_ranges || !keys ||
+        n_tiles <= 0 || n_tiles > 65536)
+        return LGS_ERR_INVALID_ARG;
+    return bin_keys(sp->depth, vals, tile_ranges, n_tiles, sp->capacity, keys,
                     as_stream(stream));
 }
 

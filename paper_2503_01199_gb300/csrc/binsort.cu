@@ -826,6 +826,33 @@ lgs_status bin_sort(const lgs_splats *sp, const int32_t *d_V, int64_t maxV, cons
     return check_launch();
 }
 
+namespace {
+
+// The 64-bit sort key (tile << 32 | depth bits) of every pair of a finished
+// binning, one CTA per tile over its range of vals. A pair whose splat
+// index is not below `rows` gets the key of a pair at infinite depth.
+__global__ void __launch_bounds__(kThreads) k_bin_keys(const float *__restrict__ depth,
+                                                      const uint32_t *__restrict__ vals,
+                                                      const uint32_t *__restrict__ ranges,
+                                                      int64_t rows, uint64_t *__restrict__ keys) {
+    const uint32_t t = blockIdx.x;
+    const uint32_t r0 = ranges[2 * t], r1 = ranges[2 * t + 1];
+    for (uint32_t p = r0 + threadIdx.x; p < r1; p += kThreads) {
+        const uint32_t v = vals[p];
+        const uint32_t d = (int64_t)v < rows ? __float_as_uint(depth[v]) : 0x7f800000u;
+        keys[p] = ((uint64_t)t << 32) | d;
+    }
+}
+
+}  // namespace
+
+lgs_status bin_keys(const float *depth, const uint32_t *vals, const uint32_t *ranges, int ntiles,
+                    int64_t rows, uint64_t *keys, cudaStream_t s) {
+    count_launch();
+    k_bin_keys<<<(unsigned)ntiles, kThreads, 0, s>>>(depth, vals, ranges, rows, keys);
+    return check_launch();
+}
+
 lgs_status bin_set_spin_limit(uint32_t spins) {
     if (cudaMemcpyToSymbol(g_bin_spin_limit, &spins, sizeof(spins)) != cudaSuccess) {
         set_cuda_error(cudaGetLastError());

@@ -52,6 +52,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert L.lgs_adam_step(None, None, None, None, 0, 0, None, 0.9, 0.999, 1e-15, 1, None, None, 0,
                            None) == B.LGS_ERR_INVALID_ARG
     assert L.lgs_bin_sort_workspace_size(1000, 100000, 64) > 100000 * 6
+    assert L.lgs_bin_keys(None, None, None, 0, None, None) == B.LGS_ERR_INVALID_ARG
     # unit-rate microbenchmarks: null buffers, sizes and counts out of range
     assert L.lgs_peak_ex2(None, 8, 1, None) == B.LGS_ERR_INVALID_ARG
     assert L.lgs_peak_ffma(None, 8, 1, 1, None) == B.LGS_ERR_INVALID_ARG

@@ -198,6 +198,33 @@ def test_bin_sort_bit_exact(orc, n, W, H, tile, cull):
     U.check_bins(orc, vals, ranges, P, s, W, H, tile, cull=cull)
 
 
+def test_bin_keys_of_the_tile_lists():
+    """lgs_bin_keys: every pair's 64-bit key is (tile << 32 | depth bits of
+    its splat), non-decreasing within each tile's range (the depth order
+    of the list); an empty binning writes nothing."""
+    import torch
+    from paper_2503_01199_gb300 import binding as B
+    cam = scenegen.pinhole_camera(200, 150, 200.0)
+    sp = U.random_splat_dict(3000, 31, 200, 150, max_radius=30)
+    g = U.gpu_raster(sp, cam)
+    dev, P = g["dev"], int(g["P"])
+    keys = torch.full((P + 1,), -1, dtype=torch.int64, device="cuda")
+    B.lgs_bin_keys(dev["splats"], dev["vals"], dev["ranges"], keys)
+    torch.cuda.synchronize()
+    k = keys.cpu().numpy().view(np.uint64)
+    assert k[P] == np.uint64(0xffffffffffffffff)               # nothing past the pairs
+    vals, ranges = g["vals"], g["ranges"].reshape(-1, 2)
+    depth_bits = sp["depth"].astype(np.float32).view(np.uint32).astype(np.uint64)
+    seen = 0
+    for t, (r0, r1) in enumerate(ranges):
+        seg = k[r0:r1]
+        assert (seg >> np.uint64(32) == np.uint64(t)).all()
+        assert (seg & np.uint64(0xffffffff) == depth_bits[vals[r0:r1]]).all()
+        assert (seg[1:] >= seg[:-1]).all()                     # unsigned: no np.diff
+        seen += r1 - r0
+    assert seen == P > 0
+
+
 @pytest.mark.parametrize("cull", [0, 1])
 def test_bin_sort_large_and_degenerate_splats(orc, cull):
     """Splats up to 600 px: groups of 32 splats with more tile rows than the
