@@ -9,12 +9,15 @@ sequence of liblgs calls (Sec. 3 pipeline):
   a6 L1 loss gradient                                     lgs_loss_l1
   a7 backward rasterisation + opacity-gradient moments    lgs_raster_bwd
   a8 densification metric C Var = S - M^2/C               lgs_opacity_variance
+                                                          (in the fused a9 + a10 call of a step)
   a9 preprocess backward + a10 sparse Adam                lgs_preprocess_bwd_adam
                                                           (or lgs_preprocess_bwd + lgs_adam_step)
 
 torch provides the device buffers and the stream; every step runs in the
 library's kernels. All calls are asynchronous and no count is read back, so
-a step can be captured in a CUDA graph.
+the a2-a8 sequence (and a step's work) can be captured in a CUDA graph; the
+Adam step count is a host argument, so a captured optimizer call would
+replay one fixed step count.
 
 Parameters and the two Adam moments live in one buffer of planes
 [3][P][stride] (params, m, v) so that the Morton re-sort permutes all of
